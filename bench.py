@@ -1,0 +1,290 @@
+#!/usr/bin/env python
+"""Benchmark: MEB solves/s of the ripALM hot path on one GB300 (or N replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload cube_m2e6_d100]
+
+A step is one full solve (Algorithm 1 with Algorithm 2, then the
+feasibility pass of Sec. 4.2) of the workload's synthetic instance:
+m = 2,000,000 balls in d = 100, centres U[-1,1]^d, radii U[0,0.05]
+(seed 1002).  Inputs (1.6 GB) are resident in HBM and larger than L2, so no
+flush is needed between steps.  Each solve is checked against the stored
+oracle radius (tests/golden/<workload>.json): a solve counts only if its
+radius relative error is <= 1e-8.
+
+Under torchrun (N > 1) every rank solves its own copy of the workload with no
+collective on the data path (weak scaling); the timed region is bracketed by
+barriers and the max over ranks is used.
+
+--impl reference times the CPU oracle as it stands on a bounded sample of the
+same workload (the first 100,000 balls, scaled by m / 100,000 to the
+workload's solves/s), on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MEB solves/s & p50/p99 latency at radius rel.err<=1e-8; per-iter HBM GB/s"
+UNIT = "solves/s"
+SAMPLE_M = 100_000
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _golden(name):
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", name + ".json")) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(C, R):
+    """The CPU oracle as it stands on the first SAMPLE_M balls; returns seconds."""
+    import oracle
+    ms = min(SAMPLE_M, C.shape[0])
+    t = time.perf_counter()
+    res = oracle.solve(C[:ms], R[:ms], tol=1e-10)
+    dt = time.perf_counter() - t
+    return dt, ms, res
+
+
+def run_reference(args, C, R, m, rank):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(C, R)
+    times = []
+    for _ in range(args.steps):
+        dt, ms, _ = oracle_sample(C, R)
+        times.append(dt * (m / ms))
+    tot = sum(times)
+    value = args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "m": m, "d": int(C.shape[1]), "tol": 1e-10},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"oracle solve of the first {SAMPLE_M} of {m} balls per step, "
+                                   f"time scaled by m/{SAMPLE_M}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cube_m2e6_d100")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_2605_31425_gb300 import workloads
+    C, R = workloads.workload(args.workload)
+    m, d = C.shape
+
+    if args.impl == "reference":
+        run_reference(args, C, R, m, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2605_31425_gb300 as meb
+    stream = torch.cuda.current_stream()
+    ctx = meb.Context(local, stream.cuda_stream)
+    dC = torch.from_numpy(C).cuda()
+    dR = torch.from_numpy(R).cuda()
+    torch.cuda.synchronize()
+
+    gold = _golden(args.workload)
+    r_ref = gold["r"] if gold and gold.get("input_sha256") == workloads.digest(C, R) else None
+
+    for _ in range(args.warmup):
+        res = meb.solve(dC, dR, ctx=ctx)
+
+    ctx.set_profiling(True)
+    ctx.reset_stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    radii = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            res = meb.solve(dC, dR, ctx=ctx)
+            ev[k][1].record(stream)
+            radii.append(res["r"])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    st = ctx.stats()
+    ctx.set_profiling(False)
+    lat = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(lat)
+    if dist:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    relerr = [abs(r - r_ref) / r_ref for r in radii] if r_ref else []
+    ok = sum(1 for e in relerr if e <= 1e-8) if r_ref else 0
+    value = world * ok / (tot_ms / 1e3) if r_ref else world * args.steps / (tot_ms / 1e3)
+
+    # roofline of the dominant kernel (the full pass): algorithmic bytes per launch
+    d4 = (d + 3) // 4
+    pass_launches = max(st["pass_launches"], 1)
+    avg_ms = st["pass_ms"] / pass_launches
+    rows64 = st["pass_fp64_rows"] / pass_launches
+    bytes_per_launch = m * (16 * d4 + 4 + 4) + rows64 * (8 * d + 8)
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    peak, peak_kind = _peaks()
+
+    # end to end: host (pinned) inputs through the public API, result back to host
+    pC = torch.from_numpy(C).pin_memory()
+    pR = torch.from_numpy(R).pin_memory()
+    hctx = meb.Context(local, stream.cuda_stream)
+    res_h = meb.solve(pC, pR, ctx=hctx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_ok = 0
+    for _ in range(args.e2e_steps):
+        res_h = meb.solve(pC, pR, ctx=hctx)
+        if r_ref is None or abs(res_h["r"] - r_ref) <= 1e-8 * r_ref:
+            e2e_ok += 1
+    e2e_s = time.perf_counter() - t0
+    e2e_val = world * e2e_ok / e2e_s
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        dt, ms, _ = oracle_sample(C, R)
+        cpu = {"value": 1.0 / (dt * m / ms), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one oracle solve of the first {ms} of {m} balls "
+                         f"({dt:.2f} s), time scaled by m/{ms}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "m": int(m), "d": int(d), "tol": 1e-10,
+                       "l2": "inputs (1.6 GB) larger than L2; no flush",
+                       "parallelism": f"replicas x{world}"},
+            "p50_ms": statistics.median(lat), "p99_ms": float(np.percentile(lat, 99)),
+            "max_relerr": max(relerr) if relerr else None, "solves_ok": ok,
+            "passes_per_solve": res["passes"], "ssn_per_solve": res["ssn_iters"],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_pass", "bytes_per_launch": bytes_per_launch,
+                         "avg_launch_ms": avg_ms, "peak_kind": peak_kind},
+            "e2e": {"value": e2e_val, "unit": UNIT,
+                    "h2d_bytes_per_step": int(C.nbytes + R.nbytes),
+                    "d2h_bytes_per_step": int(8 * d + 8 * res_h["n_active"])},
+            "gpu_launches": int(st["kernel_launches"]),
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+            "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

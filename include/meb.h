@@ -1,0 +1,145 @@
+/*
+ * meb.h -- C ABI of libmeb: the ripALM minimum-enclosing-ball hot path on one
+ * GB300 GPU (sm_103a).
+ *
+ * Problem (Sec. 1, eq. (MEB)): given m balls B(c_i, r_i) in R^d, find the
+ * centre c and the smallest radius r with ||c - c_i|| + r_i <= r for all i.
+ * Method: the SOCP form of Sec. 2 (one second-order-cone constraint
+ * (r - r_i, c - c_i) in Q_{d+1} per ball), solved by the relative-type
+ * inexact proximal augmented Lagrangian method (Algorithm 1, ripALM) with the
+ * semismooth Newton inner solver of Algorithm 2, and the a-posteriori
+ * feasibility pass of Sec. 4.2.
+ *
+ * Conventions for every entry point:
+ *  - Return 0 on success, a negative MEB_E* code otherwise; no exception
+ *    crosses the ABI.  meb_last_error() gives a one-line message.
+ *  - Arrays are FP64 unless stated: centres are m x d row-major, radii m.
+ *  - flags & MEB_PTR_DEVICE: every array argument is a device pointer on the
+ *    context's device; otherwise every array argument is a host pointer and
+ *    the library copies it in (and results out) on the context's stream.
+ *    Scalar outputs (psi, delta_max, argmax, counts, n_viol, info) are always
+ *    host pointers.
+ *  - The caller owns every buffer it passes; the library never keeps a
+ *    pointer past the call.  The context owns its device scratch (grown on
+ *    demand, freed by meb_destroy).
+ *  - A context is bound to one device and one stream; use one context per
+ *    host thread.  Calls return after the work on the stream is complete.
+ *  - Sizes: 1 <= m <= 2^31 - 257, 1 <= d <= 16384.
+ */
+#ifndef MEB_H
+#define MEB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MEB_OK 0
+#define MEB_EINVAL (-1)    /* bad size, NULL pointer, non-finite value, r_i < 0, tol <= 0 */
+#define MEB_ENOMEM (-2)    /* device allocation failed                                    */
+#define MEB_ECUDA (-3)     /* a CUDA call failed (message in meb_last_error)              */
+#define MEB_ENOTCONV (-4)  /* iteration cap reached; outputs hold the last iterate        */
+
+#define MEB_PTR_DEVICE 1u
+
+typedef struct meb_ctx meb_ctx;
+
+/* Parameters of Algorithms 1 and 2 on the scaled problem (data divided by the
+ * power of two s >= r0, r0 = max_i ||c0 - c_i|| + r_i at the mean centre c0). */
+typedef struct {
+    double tol;          /* KKT_max tolerance (Sec. 5), scaled problem; default 1e-10 */
+    double rho;          /* relative-error factor of Algorithm 1, [0,1); 0.5          */
+    double sigma0;       /* initial penalty; 10                                        */
+    double sigma_max;    /* cap on the penalty; 1e7                                    */
+    double sigma_growth; /* sigma *= growth when the primal residual stalls; 10        */
+    double sigma_ratio;  /* stall: residual > ratio * previous residual; 0.1           */
+    double tau;          /* proximal weight (constant); 1                              */
+    double armijo_mu;    /* Armijo sufficient-decrease constant; 1e-4                  */
+    double active_theta; /* active set: r - r_i - ||c - c_i|| <= theta r; 2e-6          */
+    int32_t max_outer;   /* 500 */
+    int32_t max_ssn;     /* 50  */
+    int32_t max_backtrack; /* 40 */
+    int32_t dense_max_d; /* dense Cholesky Newton solve when d <= this (<= 224); 224    */
+    int32_t max_cg;      /* CG iterations per Newton system (d > dense_max_d); 500     */
+    int32_t reserved[3];
+} meb_params;
+
+typedef struct {
+    double r;            /* returned radius: max_i(||c - c_i|| + r_i) at the returned c */
+    double r_alm;        /* ripALM's own radius variable                                */
+    double kkt[5];       /* KKT residuals of Sec. 5 at the last iterate, original units */
+    double kkt_max;      /* max of the five on the scaled problem (compared with tol)  */
+    double delta_max;    /* Delta_max = max_i(r_i + ||c - c_i||) - r_alm (Sec. 4.2)      */
+    double scale;        /* s                                                          */
+    int64_t n_active;    /* true size of the active set (may exceed active_cap)        */
+    int64_t fp64_rows;   /* ball rows evaluated in FP64 over all passes                */
+    int32_t outer_iters, ssn_iters, cg_iters, passes, backtracks;
+    int32_t status;      /* 0 converged, 1 iteration cap                               */
+} meb_info;
+
+/* Measurement counters of a context (no counterpart in the paper: they
+ * support the roofline report).  kernel_launches counts every kernel the
+ * context launched since meb_reset_stats; with profiling on, each full pass
+ * over the balls (the per-ball map of Algorithm 2, step 1) is bracketed by
+ * CUDA events on the context's stream and its device time summed here. */
+typedef struct {
+    int64_t kernel_launches;
+    int64_t pass_launches;   /* timed pass launches                      */
+    double pass_ms;          /* their summed device time, milliseconds   */
+    int64_t pass_balls;      /* balls they streamed (m per launch)       */
+    int64_t pass_fp64_rows;  /* rows they evaluated in FP64              */
+} meb_stats;
+
+/* Create a context on `device`, issuing work on `cuda_stream` (a cudaStream_t;
+ * NULL: the context creates and owns a non-blocking stream). */
+int meb_create(meb_ctx **out, int device, void *cuda_stream);
+void meb_destroy(meb_ctx *ctx);
+void meb_params_default(meb_params *p);
+const char *meb_last_error(const meb_ctx *ctx);
+
+/* Turn per-pass event timing on (1) or off (0); reset / read the counters. */
+int meb_set_profiling(meb_ctx *ctx, int on);
+int meb_reset_stats(meb_ctx *ctx);
+int meb_get_stats(meb_ctx *ctx, meb_stats *out);
+
+/* Solve eq. (MEB) (Algorithms 1 + 2, then the feasibility pass of Sec. 4.2).
+ * centers m x d, radii m; tol > 0 overrides params->tol (params may be NULL).
+ * Outputs: c_out[d]; active_idx[active_cap] ascending indices of
+ * {i : r - r_i - ||c - c_i|| <= theta r} (truncated at active_cap, which may be
+ * 0 with active_idx NULL); info (may be NULL).  m = 1 returns the ball itself. */
+int meb_solve(meb_ctx *ctx, const double *centers, const double *radii, int64_t m, int32_t d,
+              double tol, const meb_params *params, unsigned flags, double *c_out,
+              int64_t *active_idx, int64_t active_cap, meb_info *info);
+
+/* One evaluation of the prox-AL subproblem (Sec. 4, Algorithm 2 steps 1-2) at
+ * x = (r, c) (x[0] = r) with proximal centre xbar, multipliers U (m), V (m x d),
+ * penalty sigma > 0, proximal weight tau > 0, on the unscaled data:
+ *   psi   = r + sigma/2 sum ||Pi(z_i)||^2 - 1/(2 sigma) sum ||(u_i,v_i)||^2
+ *           + tau/(2 sigma) ||x - xbar||^2,
+ *   grad  = (1,0) - sum (u_i^+, v_i^+) + tau/sigma (x - xbar)        [d+1]
+ *   Uplus, Vplus = sigma Pi(z_i)                                   [m], [m x d]
+ *   Hq    = (tau/sigma I + sigma sum P_i) q   if q and Hq non-NULL  [d+1]
+ *   H     = tau/sigma I + sigma sum P_i      if H non-NULL         [(d+1)^2]
+ *   case_counts[3] = balls in cases Z (||b|| <= -a), I (||b|| <= a), M.
+ * Uplus and Vplus must both be given or both be NULL.                      */
+int meb_eval_alm(meb_ctx *ctx, const double *centers, const double *radii, int64_t m,
+                 int32_t d, const double *x, const double *xbar, const double *U,
+                 const double *V, double sigma, double tau, const double *q, unsigned flags,
+                 double *psi, double *grad, double *Uplus, double *Vplus, double *Hq, double *H,
+                 int64_t *case_counts);
+
+/* The a-posteriori feasibility pass of Sec. 4.2 at the ball (c, r):
+ *   delta_max = max_i (r_i + ||c - c_i|| - r), argmax = lowest maximising index,
+ *   viol_idx  = ascending { i : r_i + ||c - c_i|| - r > eps } (first viol_cap),
+ *   n_viol    = its true size.  viol_idx may be NULL with viol_cap 0.          */
+int meb_feas_check(meb_ctx *ctx, const double *centers, const double *radii, int64_t m,
+                   int32_t d, const double *c, double r, double eps, unsigned flags,
+                   double *delta_max, int64_t *argmax, int64_t *viol_idx, int64_t viol_cap,
+                   int64_t *n_viol);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MEB_H */

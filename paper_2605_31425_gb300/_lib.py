@@ -1,0 +1,294 @@
+"""Thin ctypes binding of libmeb (include/meb.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module converts numpy
+arrays (host path) or torch CUDA tensors (device path, ``MEB_PTR_DEVICE``) to
+pointers and sizes, and results back.  If the library cannot be built or
+loaded the calls raise; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MEB_OK, MEB_EINVAL, MEB_ENOMEM, MEB_ECUDA, MEB_ENOTCONV = 0, -1, -2, -3, -4
+MEB_PTR_DEVICE = 1
+
+_D = ct.POINTER(ct.c_double)
+_I64 = ct.POINTER(ct.c_int64)
+
+
+class MebParams(ct.Structure):
+    _fields_ = [
+        ("tol", ct.c_double), ("rho", ct.c_double), ("sigma0", ct.c_double),
+        ("sigma_max", ct.c_double), ("sigma_growth", ct.c_double), ("sigma_ratio", ct.c_double),
+        ("tau", ct.c_double), ("armijo_mu", ct.c_double), ("active_theta", ct.c_double),
+        ("max_outer", ct.c_int32), ("max_ssn", ct.c_int32), ("max_backtrack", ct.c_int32),
+        ("dense_max_d", ct.c_int32), ("max_cg", ct.c_int32), ("reserved", ct.c_int32 * 3),
+    ]
+
+
+class MebInfo(ct.Structure):
+    _fields_ = [
+        ("r", ct.c_double), ("r_alm", ct.c_double), ("kkt", ct.c_double * 5),
+        ("kkt_max", ct.c_double), ("delta_max", ct.c_double), ("scale", ct.c_double),
+        ("n_active", ct.c_int64), ("fp64_rows", ct.c_int64),
+        ("outer_iters", ct.c_int32), ("ssn_iters", ct.c_int32), ("cg_iters", ct.c_int32),
+        ("passes", ct.c_int32), ("backtracks", ct.c_int32), ("status", ct.c_int32),
+    ]
+
+
+class MebStats(ct.Structure):
+    _fields_ = [
+        ("kernel_launches", ct.c_int64), ("pass_launches", ct.c_int64), ("pass_ms", ct.c_double),
+        ("pass_balls", ct.c_int64), ("pass_fp64_rows", ct.c_int64),
+    ]
+
+
+class MebError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libmeb error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load():
+    """Build (if stale) and load libmeb.so; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            lib = ct.CDLL(path)
+            lib.meb_create.argtypes = [ct.POINTER(ct.c_void_p), ct.c_int, ct.c_void_p]
+            lib.meb_create.restype = ct.c_int
+            lib.meb_destroy.argtypes = [ct.c_void_p]
+            lib.meb_params_default.argtypes = [ct.POINTER(MebParams)]
+            lib.meb_last_error.argtypes = [ct.c_void_p]
+            lib.meb_last_error.restype = ct.c_char_p
+            lib.meb_solve.argtypes = [ct.c_void_p, _D, _D, ct.c_int64, ct.c_int32, ct.c_double,
+                                      ct.POINTER(MebParams), ct.c_uint, _D, _I64, ct.c_int64,
+                                      ct.POINTER(MebInfo)]
+            lib.meb_solve.restype = ct.c_int
+            lib.meb_eval_alm.argtypes = [ct.c_void_p, _D, _D, ct.c_int64, ct.c_int32, _D, _D, _D,
+                                         _D, ct.c_double, ct.c_double, _D, ct.c_uint, _D, _D, _D,
+                                         _D, _D, _D, _I64]
+            lib.meb_eval_alm.restype = ct.c_int
+            lib.meb_feas_check.argtypes = [ct.c_void_p, _D, _D, ct.c_int64, ct.c_int32, _D,
+                                           ct.c_double, ct.c_double, ct.c_uint, _D, _I64, _I64,
+                                           ct.c_int64, _I64]
+            lib.meb_feas_check.restype = ct.c_int
+            lib.meb_set_profiling.argtypes = [ct.c_void_p, ct.c_int]
+            lib.meb_reset_stats.argtypes = [ct.c_void_p]
+            lib.meb_get_stats.argtypes = [ct.c_void_p, ct.POINTER(MebStats)]
+            _lib = lib
+    return _lib
+
+
+def params_default() -> MebParams:
+    p = MebParams()
+    load().meb_params_default(ct.byref(p))
+    return p
+
+
+class Context:
+    """One libmeb context (device + stream).  ``stream`` is a raw cudaStream_t
+    handle (int) or None for a private stream."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self._lib = load()
+        h = ct.c_void_p()
+        rc = self._lib.meb_create(ct.byref(h), int(device), ct.c_void_p(stream) if stream else None)
+        if rc != MEB_OK:
+            raise MebError(rc, "meb_create failed")
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.meb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_profiling(self, on: bool):
+        self._check(self._lib.meb_set_profiling(self._h, 1 if on else 0))
+
+    def reset_stats(self):
+        self._check(self._lib.meb_reset_stats(self._h))
+
+    def stats(self) -> dict:
+        st = MebStats()
+        self._check(self._lib.meb_get_stats(self._h, ct.byref(st)))
+        return {k: getattr(st, k) for k, _ in MebStats._fields_}
+
+    def _check(self, rc: int, ok=(MEB_OK,)):
+        if rc not in ok:
+            raise MebError(rc, self._lib.meb_last_error(self._h).decode())
+        return rc
+
+
+_default_ctx = {}
+
+
+def default_context(device: int = 0, stream: int | None = None) -> Context:
+    key = (device, stream)
+    if key not in _default_ctx:
+        _default_ctx[key] = Context(device, stream)
+    return _default_ctx[key]
+
+
+# ---------------------------------------------------------------- marshalling
+def _is_torch_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _ptr(a):
+    """(pointer, keepalive) of a float64/int64 array: numpy (host) or torch CUDA."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr(), a
+    return a.ctypes.data, a
+
+
+def _as_d(p):
+    return ct.cast(p, _D) if p is not None else None
+
+
+def _as_i(p):
+    return ct.cast(p, _I64) if p is not None else None
+
+
+def _host_f64(a):
+    if hasattr(a, "data_ptr") and not getattr(a, "is_cuda", False):
+        # a torch CPU tensor (possibly pinned): keep it, pass its pointer
+        if not a.is_contiguous() or str(a.dtype) != "torch.float64":
+            raise ValueError("host tensors must be contiguous float64")
+        return a
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ctx_for(device_path: bool, ctx: Context | None) -> Context:
+    if ctx is not None:
+        return ctx
+    if device_path:
+        import torch
+        dev = torch.cuda.current_device()
+        return default_context(dev, torch.cuda.current_stream(dev).cuda_stream)
+    return default_context(0, None)
+
+
+def solve(centers, radii, tol: float = 0.0, params: MebParams | None = None,
+          active_cap: int | None = None, ctx: Context | None = None, allow_notconv=False):
+    """meb_solve.  numpy inputs: host path (results in numpy).  torch CUDA float64
+    tensors: device path (c is a CUDA tensor, active a CUDA int64 tensor)."""
+    dev = _is_torch_cuda(centers)
+    if dev:
+        import torch
+        m, d = centers.shape
+        c_out = torch.empty(d, dtype=torch.float64, device=centers.device)
+        cap = m if active_cap is None else active_cap
+        act = torch.empty(max(cap, 1), dtype=torch.int64, device=centers.device)
+        C, R = centers, radii
+    else:
+        C = _host_f64(centers)
+        if C.ndim == 1:
+            C = C.reshape(-1, 1)
+        R = _host_f64(radii)
+        m, d = C.shape
+        c_out = np.empty(d)
+        cap = m if active_cap is None else active_cap
+        act = np.empty(max(cap, 1), dtype=np.int64)
+    if R.shape[0] != m:
+        raise ValueError("radii must have m entries")
+    cx = _ctx_for(dev, ctx)
+    info = MebInfo()
+    pc, _k1 = _ptr(C)
+    pr, _k2 = _ptr(R)
+    po, _k3 = _ptr(c_out)
+    pa, _k4 = _ptr(act)
+    rc = cx._lib.meb_solve(cx._h, _as_d(pc), _as_d(pr), m, d, float(tol),
+                           ct.byref(params) if params is not None else None,
+                           MEB_PTR_DEVICE if dev else 0, _as_d(po), _as_i(pa), cap,
+                           ct.byref(info))
+    cx._check(rc, ok=(MEB_OK, MEB_ENOTCONV) if allow_notconv else (MEB_OK,))
+    na = int(info.n_active)
+    return dict(
+        r=info.r, r_alm=info.r_alm, c=c_out, active=act[:min(na, cap)], n_active=na,
+        kkt=list(info.kkt), kkt_max=info.kkt_max, delta_max=info.delta_max, scale=info.scale,
+        fp64_rows=int(info.fp64_rows), outer_iters=info.outer_iters, ssn_iters=info.ssn_iters,
+        cg_iters=info.cg_iters, passes=info.passes, backtracks=info.backtracks,
+        status=info.status, rc=rc,
+    )
+
+
+def eval_alm(centers, radii, x, xbar, U, V, sigma, tau, q=None, want_H=False,
+             ctx: Context | None = None):
+    """meb_eval_alm on host numpy arrays (or torch CUDA tensors)."""
+    dev = _is_torch_cuda(centers)
+    if dev:
+        import torch
+        m, d = centers.shape
+        mk = lambda *s: torch.empty(*s, dtype=torch.float64, device=centers.device)  # noqa: E731
+        C, R, X, XB, UU, VV, Q = centers, radii, x, xbar, U, V, q
+    else:
+        C = _host_f64(centers)
+        m, d = C.shape
+        R, X, XB = _host_f64(radii), _host_f64(x), _host_f64(xbar)
+        UU, VV = _host_f64(U), _host_f64(V)
+        Q = _host_f64(q) if q is not None else None
+        mk = lambda *s: np.empty(s)  # noqa: E731
+    grad = mk(d + 1)
+    Up = mk(m)
+    Vp = mk(m, d)
+    Hq = mk(d + 1) if q is not None else None
+    H = mk(d + 1, d + 1) if want_H else None
+    psi = ct.c_double()
+    counts = np.zeros(3, dtype=np.int64)
+    cx = _ctx_for(dev, ctx)
+    ptrs = [_ptr(a) for a in (C, R, X, XB, UU, VV, Q, grad, Up, Vp, Hq, H)]
+    p = [_as_d(t[0]) for t in ptrs]
+    rc = cx._lib.meb_eval_alm(cx._h, p[0], p[1], m, d, p[2], p[3], p[4], p[5], float(sigma),
+                              float(tau), p[6], MEB_PTR_DEVICE if dev else 0, ct.byref(psi),
+                              p[7], p[8], p[9], p[10], p[11], counts.ctypes.data_as(_I64))
+    cx._check(rc)
+    return dict(psi=psi.value, grad=grad, Uplus=Up, Vplus=Vp, Hq=Hq, H=H, counts=counts)
+
+
+def feas_check(centers, radii, c, r, eps, cap=None, ctx: Context | None = None):
+    """meb_feas_check: (delta_max, argmax, ascending violated indices, n_viol)."""
+    dev = _is_torch_cuda(centers)
+    if dev:
+        import torch
+        m, d = centers.shape
+        cap = m if cap is None else cap
+        viol = torch.empty(max(cap, 1), dtype=torch.int64, device=centers.device)
+        C, R, cc = centers, radii, c
+    else:
+        C = _host_f64(centers)
+        m, d = C.shape
+        R, cc = _host_f64(radii), _host_f64(c)
+        cap = m if cap is None else cap
+        viol = np.empty(max(cap, 1), dtype=np.int64)
+    cx = _ctx_for(dev, ctx)
+    dm = ct.c_double()
+    am = ct.c_int64()
+    nv = ct.c_int64()
+    (pc, _a), (pr, _b), (p3, _c), (pv, _d) = _ptr(C), _ptr(R), _ptr(cc), _ptr(viol)
+    rc = cx._lib.meb_feas_check(cx._h, _as_d(pc), _as_d(pr), m, d, _as_d(p3), float(r),
+                                float(eps), MEB_PTR_DEVICE if dev else 0, ct.byref(dm),
+                                ct.byref(am), _as_i(pv), cap, ct.byref(nv))
+    cx._check(rc)
+    return dm.value, am.value, viol[:min(nv.value, cap)], nv.value

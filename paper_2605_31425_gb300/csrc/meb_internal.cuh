@@ -1,0 +1,170 @@
+// Internal declarations shared by the kernels and the C-ABI layer of libmeb.
+//
+// All solver state lives in device memory (DevState plus the vectors it
+// points to); the kernels read and write it, and the host only launches and
+// reads back the small action/status fields.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace meb {
+
+constexpr int kPassThreads = 256;   // balls per pass block (one per thread)
+constexpr int kPassWarps = kPassThreads / 32;
+constexpr int kMaxDenseN = 225;     // dense Newton solve for d+1 <= 225 (packed FP64 in smem)
+constexpr int kSvecBlocks = 160;    // blocks of the support-row reduction
+constexpr int kSyrkTile = 32;
+constexpr int kSyrkRows = 32;       // support rows per SYRK block
+
+// ball case of the projection onto Q_{d+1}
+enum : int { CASE_Z = 0, CASE_I = 1, CASE_M = 2 };
+
+// controller actions
+enum : int {
+  ACT_NONE = 0,
+  ACT_NEWTON = 1,   // assemble H / run CG at the accepted point, then a trial pass
+  ACT_TRIAL = 2,    // a new trial point is set (backtrack); next is a pass
+  ACT_OUTER = 3,    // outer step: multiplier update, then a pass at x
+  ACT_DONE = 4,
+};
+
+// per-block partial record of the pass (doubles)
+enum : int {
+  P_PI2 = 0,   // sum ||Pi(z_i)||^2
+  P_SU,        // sum u_i^+
+  P_DUV2,      // sum ||(u,v)_i^+ - (u,v)_i||^2
+  P_UV2,       // sum ||(u,v)_i||^2 over the current multipliers
+  P_ZMAG,      // sum_{I,M} |a_i| + ||b_i||
+  P_KP,        // max primal distance to Q
+  P_KD,        // max dual distance to Q
+  P_KC,        // max complementarity
+  P_NI,        // count of case I
+  P_NM,        // count of case M
+  P_N64,       // rows evaluated in FP64
+  P_COUNT
+};
+
+struct DevState {
+  // problem
+  int64_t m, m_pad;
+  int d, d4, n1;
+  int dense;              // 1: dense Cholesky, 0: CG
+  double s, inv_s;        // power-of-two scale
+  // parameters (scaled problem)
+  double tol, rho, sigma_max, sigma_growth, sigma_ratio, tau, mu;
+  int max_outer, max_ssn, max_backtrack, max_cg;
+  // iteration state
+  double sigma, inv_sigma;
+  double psi, psi_mag, gmag;   // at the accepted point x
+  double gdx, eta;
+  double pinf_prev;
+  int outer, ssn_j, bt;
+  int tot_ssn, tot_passes, tot_bt, tot_cg;
+  int phase;                   // 0: pass evaluates x^k (outer start); 1: a line-search trial
+  int action, status;          // status: 0 running, 1 converged, 2 iteration cap
+  int sup_cur, nsup;           // current multiplier buffers and their size
+  int nS;                      // support (cases I, M) of the last evaluated point
+  int svec_nb, svec_rpb;       // blocks / rows per block of the support reduction
+  double sigma_prev;           // sigma of the finished outer step (multiplier update)
+  int64_t n64_total;
+  int chol_fail, eval_only;
+  double kkt[5], kkt_max;
+  double last[P_COUNT];        // reduced partials of the last pass
+  // trial point shadow for the FP32 screen
+  double rt_abs;               // trial radius, unscaled
+  float rq32, yn32;            // fl32(r_t / s), an upper bound on ||y32||
+  // CG scratch scalars
+  double cg_rz, cg_bn, cg_rtol;
+  int cg_it, cg_done;
+};
+
+// Device vectors of length n1 = d+1 (scaled units unless noted) and more.
+struct DevVecs {
+  double* x;      // accepted point
+  double* xt;     // trial point
+  double* xk;     // proximal centre x^k
+  double* ab;     // auxiliary (alpha, beta)
+  double* g;      // gradient at x
+  double* gt;     // gradient at the trial
+  double* dx;     // Newton direction
+  double* ct;     // trial centre, UNSCALED (c = s * xt[1:])
+  double* o;      // origin of the FP32 shadow, unscaled
+  float* y32;     // fl32((ct - o)/s), 4*d4 floats
+  double* sv;     // sum of v^+ (d)
+  double* sw;     // sum of w over case M (d)
+  double* st1;    // [0]: sum_M (1 + t)
+  // CG
+  double* cg_r; double* cg_z; double* cg_p; double* cg_ap; double* cg_diag;
+};
+
+struct Buffers {
+  int64_t launches;     // host-side count of kernels launched through these buffers
+  int64_t m_cap;
+  int d_cap;
+  int64_t nblk_cap;
+  // shadow
+  float4* X32;          // [d4][m_pad]
+  float* R32;           // [m_pad]
+  // multipliers (double buffered)
+  int* slot;            // [m]
+  int* sup_idx[2];      // [m]
+  double* sup_u[2];     // [m]
+  double* sup_v[2];     // [m*d]
+  // pass outputs
+  int* part_flag;       // [nblk]
+  double* part;         // [nblk][P_COUNT]
+  int* cand_cnt;        // [nblk]
+  int* cand_idx;        // [m_pad]
+  unsigned char* cand_case;
+  double* cand_a; double* cand_n; double* cand_u;
+  // support list of the last pass (ball order)
+  int* S_idx; unsigned char* S_case; double* S_a; double* S_n; double* S_u; double* S_t;
+  double* W;            // [m*d] w rows (case M) / b rows (case I)
+  double* svec_part;    // [kSvecBlocks][2d+1]
+  double* hpart;        // SYRK partials
+  int64_t hpart_cap;
+  double* H;            // [n1*n1] assembled Hessian (eval entry / CG diag)
+  double* hq;           // [n1] Hessian-vector product
+  double* colsum_part;  // mean-centre partials
+  double* e;            // [m] r_i + ||c - c_i|| of the last feasibility pass
+  double* feas_part;    // feasibility partials
+  int64_t* feas_ipart;
+  int* feas_cnt;        // [nblk]
+  int64_t* viol;        // [m] compacted indices
+  int64_t* list_tmp;    // [m_pad] per-tile lists before compaction
+  int64_t* count64;     // [4] device counters
+  double* wq;           // [m] w_k . q of the Hessian-vector product
+  DevState* st;
+  DevVecs vec;
+  double* vec_store;
+};
+
+// ---- launch wrappers (meb_kernels.cu) ----
+cudaError_t launch_colsum(const double* C, int64_t m, int d, double* part, double* out,
+                          cudaStream_t s);
+cudaError_t launch_feas(const double* C, const double* R, int64_t m, int d,
+                        const double* c, double r, double eps, int mode, double* e_out,
+                        Buffers& B, double* dmax_out, int64_t* argmax_out, int64_t* nviol_out,
+                        cudaStream_t s);
+cudaError_t launch_shadow(const double* C, const double* R, int64_t m, int d, int64_t m_pad,
+                          const double* o, double inv_s, float4* X32, float* R32, cudaStream_t s);
+cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m, int d,
+                        cudaStream_t s);
+cudaError_t launch_pass_post(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s);
+cudaError_t launch_tick_control(Buffers& B, int64_t m, int d, cudaStream_t s);
+cudaError_t launch_newton_dense(Buffers& B, int d, cudaStream_t s);
+cudaError_t launch_cg_setup(Buffers& B, int d, cudaStream_t s);
+cudaError_t launch_cg_iter(Buffers& B, int d, cudaStream_t s);
+cudaError_t launch_cg_finish(Buffers& B, int d, cudaStream_t s);
+cudaError_t launch_mult_update(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s);
+cudaError_t launch_state_init(Buffers& B, int d, cudaStream_t s);
+cudaError_t launch_support_from_dense(const double* U, const double* V, Buffers& B, int64_t m,
+                                      int d, cudaStream_t s);
+cudaError_t launch_eval_outputs(const double* C, Buffers& B, int64_t m, int d, const double* q,
+                                double* Uplus, double* Vplus, double* Hq, double* H,
+                                cudaStream_t s);
+cudaError_t launch_eval_prepare(Buffers& B, const double* x, const double* xbar, int d,
+                                cudaStream_t s);
+cudaError_t launch_final_point(Buffers& B, int d, double* c_out, double* r_alm, cudaStream_t s);
+
+}  // namespace meb
