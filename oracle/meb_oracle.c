@@ -33,12 +33,14 @@
  *     then Z, else M); I includes a = ||b|| = 0.
  *   - sigma_0 = 10, sigma_{k+1} = min(sigma_max, 10 sigma_k) when the
  *     primal residual max_i dist((r - r_i, c - c_i), Q) is above tol and
- *     did not fall below a tenth of its previous value; tau = 1 constant
+ *     did not fall below a tenth of its previous value; tau = 10 constant
  *     (Theorem 1 holds with nu_k = 0).
  *   - the inner loop also stops when ||grad|| is within 8 ulp of the scale
  *     of its own rounding error (nothing left to gain in FP64).
- *   - Armijo: mu = 1e-4, halving, at most max_backtrack halvings, with a
- *     rounding allowance of 64 ulp of the summed magnitude of Psi.
+ *   - Armijo: mu = 1e-4, at most max_backtrack reductions, a rounding
+ *     allowance of 64 ulp of the summed magnitude of Psi; each reduction
+ *     takes the minimiser of the quadratic through Psi(0), Psi'(0) and
+ *     Psi(eta), safeguarded to [eta/10, eta/2].
  *   - the returned radius is the max-type value max_i(||c - c_i|| + r_i)
  *     at the returned centre (the a-posteriori feasibility pass, Sec. 4.2).
  *   - active set A = { i : r - r_i - ||c - c_i|| <= theta * r }.
@@ -90,7 +92,7 @@ void orc_params_default(orc_params *p)
     p->sigma_max = 1e7;
     p->sigma_growth = 10.0;
     p->sigma_ratio = 0.1;
-    p->tau = 1.0;
+    p->tau = 10.0;
     p->armijo_mu = 1e-4;
     p->active_theta = 2e-6;
     p->max_outer = 500;
@@ -685,7 +687,15 @@ int orc_solve(int64_t m, int d, const double *C0, const double *R0,
                 double allow = 64.0 * 2.220446049250313e-16 * (mag > magt ? mag : magt);
                 if (psit <= psi + prm.armijo_mu * eta * gdx + allow) { ok = 1; break; }
                 if (bt == prm.max_backtrack) break;
-                eta *= 0.5;
+                {
+                    /* next step: minimiser of the quadratic through Psi(0),
+                     * Psi'(0) = g.dx and Psi(eta), kept in [eta/10, eta/2] */
+                    double den = 2.0 * (psit - psi - gdx * eta);
+                    double en = (den > 0.0) ? -gdx * eta * eta / den : 0.5 * eta;
+                    if (en < 0.1 * eta) en = 0.1 * eta;
+                    if (en > 0.5 * eta) en = 0.5 * eta;
+                    eta = en;
+                }
                 backtracks++;
             }
             /* accept the last trial (ok or not) */
