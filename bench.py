@@ -249,7 +249,7 @@ def main():
         if r_ref is None or abs(res_h["r"] - r_ref) <= 1e-8 * r_ref:
             e2e_ok += 1
     e2e_s = time.perf_counter() - t0
-    e2e_val = world * e2e_ok / e2e_s
+    e2e_val = world * e2e_ok / e2e_s if args.e2e_steps > 0 else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -54,7 +54,7 @@ typedef struct {
     double sigma_max;    /* cap on the penalty; 1e7                                    */
     double sigma_growth; /* sigma *= growth when the primal residual stalls; 10        */
     double sigma_ratio;  /* stall: residual > ratio * previous residual; 0.1           */
-    double tau;          /* proximal weight (constant); 1                              */
+    double tau;          /* proximal weight (constant); 10                             */
     double armijo_mu;    /* Armijo sufficient-decrease constant; 1e-4                  */
     double active_theta; /* active set: r - r_i - ||c - c_i|| <= theta r; 2e-6          */
     int32_t max_outer;   /* 500 */

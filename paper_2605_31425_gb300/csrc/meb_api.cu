@@ -15,10 +15,6 @@
 
 using namespace meb;
 
-namespace meb {
-__global__ void k_check_finite(const double* __restrict__ C, int64_t n, int* bad);
-__global__ void k_check_radii(const double* __restrict__ R, int64_t m, int* bad);
-}  // namespace meb
 
 struct meb_ctx {
   int device = 0;
@@ -65,8 +61,10 @@ static void free_buffers(meb_ctx* ctx) {
   Buffers& B = ctx->B;
   void* ptrs[] = {B.X32, B.R32, B.slot, B.sup_idx[0], B.sup_idx[1], B.sup_u[0], B.sup_u[1],
                   B.sup_v[0], B.sup_v[1], B.part_flag, B.part, B.cand_cnt, B.cand_idx,
+                  B.unc_cnt, B.unc_idx, B.unc_slot, B.vlb_part,
                   B.cand_case, B.cand_a, B.cand_n, B.cand_u, B.S_idx, B.S_case, B.S_a, B.S_n,
-                  B.S_u, B.S_t, B.W, B.svec_part, B.hpart, B.H, B.hq, B.colsum_part, B.e,
+                  B.S_u, B.S_t, B.W, B.svec_part, B.hpart, B.H, B.hq, B.colsum_part, B.fe_ub, B.fe_lb,
+                  B.fe_blb, B.fe_L, B.fq_y32,
                   B.feas_part, B.feas_ipart, B.feas_cnt, B.viol, B.list_tmp, B.count64, B.wq,
                   B.st, B.vec_store};
   for (void* p : ptrs)
@@ -111,14 +109,21 @@ static int ensure_buffers(meb_ctx* ctx, int64_t m, int d) {
     CK(dalloc(&B.sup_u[k], (size_t)m));
     CK(dalloc(&B.sup_v[k], (size_t)md));
   }
+  int tpb;
+  const int64_t npb = pass_blocks(m, &tpb);
+  const int64_t ncand = npb * tpb * 256;
   CK(dalloc(&B.part_flag, (size_t)nblk));
   CK(dalloc(&B.part, (size_t)nblk * P_COUNT));
   CK(dalloc(&B.cand_cnt, (size_t)nblk));
-  CK(dalloc(&B.cand_idx, (size_t)m_pad));
-  CK(dalloc(&B.cand_case, (size_t)m_pad));
-  CK(dalloc(&B.cand_a, (size_t)m_pad));
-  CK(dalloc(&B.cand_n, (size_t)m_pad));
-  CK(dalloc(&B.cand_u, (size_t)m_pad));
+  CK(dalloc(&B.unc_cnt, (size_t)nblk));
+  CK(dalloc(&B.vlb_part, (size_t)nblk));
+  CK(dalloc(&B.unc_idx, (size_t)ncand));
+  CK(dalloc(&B.unc_slot, (size_t)ncand));
+  CK(dalloc(&B.cand_idx, (size_t)ncand));
+  CK(dalloc(&B.cand_case, (size_t)ncand));
+  CK(dalloc(&B.cand_a, (size_t)ncand));
+  CK(dalloc(&B.cand_n, (size_t)ncand));
+  CK(dalloc(&B.cand_u, (size_t)ncand));
   CK(dalloc(&B.S_idx, (size_t)m));
   CK(dalloc(&B.S_case, (size_t)m));
   CK(dalloc(&B.S_a, (size_t)m));
@@ -130,8 +135,12 @@ static int ensure_buffers(meb_ctx* ctx, int64_t m, int d) {
   CK(dalloc(&B.hpart, (size_t)hp));
   CK(dalloc(&B.H, (size_t)(d + 1 <= kMaxDenseN ? n1 * n1 : 1)));
   CK(dalloc(&B.hq, (size_t)n1));
-  CK(dalloc(&B.colsum_part, (size_t)1024 * d));
-  CK(dalloc(&B.e, (size_t)m));
+  CK(dalloc(&B.colsum_part, (size_t)((m + 63) / 64) * d));
+  CK(dalloc(&B.fe_ub, (size_t)m));
+  CK(dalloc(&B.fe_lb, (size_t)m));
+  CK(dalloc(&B.fe_blb, (size_t)nblk));
+  CK(dalloc(&B.fe_L, 4));
+  CK(dalloc(&B.fq_y32, (size_t)4 * d4 + 4));
   CK(dalloc(&B.feas_part, (size_t)nblk + 8));
   CK(dalloc(&B.feas_ipart, (size_t)nblk + 8));
   CK(dalloc(&B.feas_cnt, (size_t)nblk + 8));
@@ -148,7 +157,8 @@ static int ensure_buffers(meb_ctx* ctx, int64_t m, int d) {
   double* p = B.vec_store;
   auto take = [&](double** q) { *q = p; p += stride; };
   take(&B.vec.x); take(&B.vec.xt); take(&B.vec.xk); take(&B.vec.ab); take(&B.vec.g);
-  take(&B.vec.gt); take(&B.vec.dx); take(&B.vec.ct); take(&B.vec.o); take(&B.vec.sv);
+  take(&B.vec.gt); take(&B.vec.dx); take(&B.vec.ct); take(&B.vec.o); take(&B.vec.c0);
+  take(&B.vec.sv);
   take(&B.vec.sw); take(&B.vec.st1); take(&B.vec.cg_r); take(&B.vec.cg_z); take(&B.vec.cg_p);
   take(&B.vec.cg_ap); take(&B.vec.cg_diag);
   B.vec.y32 = reinterpret_cast<float*>(p);
@@ -204,7 +214,7 @@ void meb_params_default(meb_params* p) {
   p->sigma_max = 1e7;
   p->sigma_growth = 10.0;
   p->sigma_ratio = 0.1;
-  p->tau = 1.0;
+  p->tau = 10.0;
   p->armijo_mu = 1e-4;
   p->active_theta = 2e-6;
   p->max_outer = 500;
@@ -292,21 +302,6 @@ static int check_sizes(meb_ctx* ctx, int64_t m, int32_t d) {
   return MEB_OK;
 }
 
-// Input validation on the device: all centres finite, radii finite and >= 0.
-static int validate_inputs(meb_ctx* ctx, const double* C, const double* R, int64_t m, int d) {
-  CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), ctx->stream));
-  const int64_t n = m * (int64_t)d;
-  int nb = (int)((n + 255) / 256);
-  if (nb > 4096) nb = 4096;
-  meb::k_check_finite<<<nb, 256, 0, ctx->stream>>>(C, n, ctx->d_flags);
-  int nb2 = (int)((m + 255) / 256);
-  if (nb2 > 4096) nb2 = 4096;
-  meb::k_check_radii<<<nb2, 256, 0, ctx->stream>>>(R, m, ctx->d_flags);
-  CK(cudaGetLastError());
-  ctx->B.launches += 2;
-  return MEB_OK;
-}
-
 static void host_state_defaults(DevState& S, int64_t m, int d, const meb_params& P, double s) {
   memset(&S, 0, sizeof(S));
   S.m = m;
@@ -370,15 +365,14 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   if (rc) return rc;
   rc = stage_in(ctx, POOL_R, radii, sizeof(double) * (size_t)m, flags, (const void**)&R);
   if (rc) return rc;
-  rc = validate_inputs(ctx, C, R, m, d);
-  if (rc) return rc;
+  B.C_in = C;
+  CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
   if (info) memset(info, 0, sizeof(*info));
 
-  // c0 = mean centre; r0 = max_i ||c0 - c_i|| + r_i (feasibility pass with r = 0)
-  CK(launch_colsum(C, m, d, B.colsum_part, B.vec.o, s));
-  B.launches += 2;
-  CK(launch_feas(C, R, m, d, B.vec.o, 0.0, INFINITY, 0, nullptr, B, ctx->d_scal,
-                 ctx->d_i64, ctx->d_i64 + 1, s));
+  // FP32 shadow (origin c_0) and the mean centre c0; r0 = max_i ||c0 - c_i|| + r_i
+  CK(launch_shadow(C, R, m, d, B, B.vec.o, B.vec.c0, ctx->d_flags, s));
+  CK(launch_feas_cert(C, R, m, d, B.vec.c0, 0.0, INFINITY, 2, 1, B, ctx->d_scal, ctx->d_i64,
+                      ctx->d_i64 + 1, s));
   CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -392,7 +386,7 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
 
   if (m == 1 || r0 == 0.0) {
     // one ball, or every ball the same point: the answer is that ball
-    CK(cudaMemcpyAsync(dcout, m == 1 ? C : B.vec.o, sizeof(double) * d,
+    CK(cudaMemcpyAsync(dcout, m == 1 ? C : B.vec.c0, sizeof(double) * d,
                        cudaMemcpyDeviceToDevice, s));
     if (!(flags & MEB_PTR_DEVICE))
       CK(cudaMemcpyAsync(c_out, dcout, sizeof(double) * d, cudaMemcpyDeviceToHost, s));
@@ -413,9 +407,6 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   frexp(r0, &ex);
   double sc = ldexp(1.0, ex);
   if (sc / 2.0 >= r0) sc /= 2.0;
-  const int64_t m_pad = ((m + 255) / 256) * 256;
-  CK(launch_shadow(C, R, m, d, m_pad, B.vec.o, 1.0 / sc, B.X32, B.R32, s));
-  B.launches += 1;
   CK(cudaMemsetAsync(B.slot, 0xff, sizeof(int) * (size_t)m, s));
   host_state_defaults(*ctx->h_st, m, d, P, sc);
   ctx->h_st->rt_abs = r0;   // initial radius; k_state_init scales it
@@ -430,7 +421,6 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
     if (ctx->profiling) CK(cudaEventRecord(ctx->ev[0], s));
     CK(launch_pass(C, R, B, m, d, s));
     if (ctx->profiling) CK(cudaEventRecord(ctx->ev[1], s));
-    CK(launch_pass_post(C, B, m, d, s));
     CK(launch_tick_control(B, m, d, s));
     rc = read_state(ctx);
     if (rc) return rc;
@@ -465,14 +455,14 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   // final point, radius lift (max-type value at c) and active set
   double* d_ralm = ctx->d_scal + 1;
   CK(launch_final_point(B, d, (double*)dcout, d_ralm, s));
-  CK(launch_feas(C, R, m, d, (const double*)dcout, 0.0, INFINITY, 0, nullptr, B, ctx->d_scal + 2,
-                 ctx->d_i64 + 2, ctx->d_i64 + 3, s));
+  CK(launch_feas_cert(C, R, m, d, (const double*)dcout, 0.0, INFINITY, 2, 1, B, ctx->d_scal + 2,
+                      ctx->d_i64 + 2, ctx->d_i64 + 3, s));
   CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const double r_alm = ctx->h_scal[1];
   const double r_out = ctx->h_scal[2];
-  CK(launch_feas(C, R, m, d, (const double*)dcout, r_out, P.active_theta * r_out, 1, nullptr, B,
-                 ctx->d_scal + 4, ctx->d_i64 + 4, ctx->d_i64 + 5, s));
+  CK(launch_feas_cert(C, R, m, d, (const double*)dcout, r_out, P.active_theta * r_out, 1, 0, B,
+                      nullptr, nullptr, ctx->d_i64 + 5, s));
   CK(cudaMemcpyAsync(ctx->h_scal + 8, ctx->d_i64 + 5, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   if (!(flags & MEB_PTR_DEVICE))
     CK(cudaMemcpyAsync(c_out, dcout, sizeof(double) * d, cudaMemcpyDeviceToHost, s));
@@ -539,13 +529,9 @@ extern "C" int meb_eval_alm(meb_ctx* ctx, const double* centers, const double* r
   if ((rc = stage_in(ctx, POOL_U, U, sizeof(double) * (size_t)m, flags, (const void**)&dU))) return rc;
   if ((rc = stage_in(ctx, POOL_V, V, sizeof(double) * (size_t)m * d, flags, (const void**)&dV))) return rc;
   if (q && (rc = stage_in(ctx, POOL_Q, q, n1b, flags, (const void**)&dq))) return rc;
-  rc = validate_inputs(ctx, C, R, m, d);
-  if (rc) return rc;
-
-  CK(launch_colsum(C, m, d, B.colsum_part, B.vec.o, s));
-  const int64_t m_pad = ((m + 255) / 256) * 256;
-  CK(launch_shadow(C, R, m, d, m_pad, B.vec.o, 1.0, B.X32, B.R32, s));
-  B.launches += 3 + 4 + 1 + 6;
+  B.C_in = C;
+  CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
+  CK(launch_shadow(C, R, m, d, B, B.vec.o, B.vec.c0, ctx->d_flags, s));
   CK(cudaMemsetAsync(B.slot, 0xff, sizeof(int) * (size_t)m, s));
   meb_params P;
   meb_params_default(&P);
@@ -558,7 +544,6 @@ extern "C" int meb_eval_alm(meb_ctx* ctx, const double* centers, const double* r
   CK(launch_support_from_dense(dU, dV, B, m, d, s));
   CK(launch_eval_prepare(B, dx, dxb, d, s));
   CK(launch_pass(C, R, B, m, d, s));
-  CK(launch_pass_post(C, B, m, d, s));
   CK(launch_tick_control(B, m, d, s));
   double *dUp = nullptr, *dVp = nullptr, *dHq = nullptr, *dH = nullptr;
   if (Uplus) {
@@ -620,9 +605,9 @@ extern "C" int meb_feas_check(meb_ctx* ctx, const double* centers, const double*
   if ((rc = stage_in(ctx, POOL_C, centers, sizeof(double) * (size_t)m * d, flags, (const void**)&C))) return rc;
   if ((rc = stage_in(ctx, POOL_R, radii, sizeof(double) * (size_t)m, flags, (const void**)&R))) return rc;
   if ((rc = stage_in(ctx, POOL_X, c, sizeof(double) * (size_t)d, flags, (const void**)&dc))) return rc;
-  rc = validate_inputs(ctx, C, R, m, d);
-  if (rc) return rc;
-  CK(launch_feas(C, R, m, d, dc, r, eps, 0, nullptr, B, ctx->d_scal, ctx->d_i64, ctx->d_i64 + 1, s));
+  CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
+  CK(launch_shadow(C, R, m, d, B, B.vec.o, B.vec.c0, ctx->d_flags, s));
+  CK(launch_feas_cert(C, R, m, d, dc, r, eps, 0, 1, B, ctx->d_scal, ctx->d_i64, ctx->d_i64 + 1, s));
   CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_i64, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(ctx->h_scal + 3, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -645,23 +630,3 @@ extern "C" int meb_feas_check(meb_ctx* ctx, const double* centers, const double*
   return MEB_OK;
 }
 
-namespace meb {
-// Finite check on the raw bits (exponent all ones = inf or NaN): integer ops only.
-__global__ void k_check_finite(const double* __restrict__ C, int64_t n, int* bad) {
-  const unsigned long long* u = reinterpret_cast<const unsigned long long*>(C);
-  int b = 0;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x)
-    b |= ((u[k] >> 52) & 0x7ff) == 0x7ff;
-  if (__syncthreads_or(b) && threadIdx.x == 0) atomicOr(bad, 1);
-}
-__global__ void k_check_radii(const double* __restrict__ R, int64_t m, int* bad) {
-  int b = 0;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const double r = R[k];
-    b |= !(r >= 0.0) || !isfinite(r);
-  }
-  if (__syncthreads_or(b) && threadIdx.x == 0) atomicOr(bad, 1);
-}
-}  // namespace meb

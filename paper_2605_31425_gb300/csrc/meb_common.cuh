@@ -1,0 +1,135 @@
+// Device helpers shared by the libmeb translation units: deterministic warp
+// and block reductions, the distance to the second-order cone, and the FP32
+// shadow conversion with its error bound.
+#pragma once
+#include <cuda_runtime.h>
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "meb_internal.cuh"
+
+namespace meb {
+
+#define MEB_FULLMASK 0xffffffffu
+
+__host__ __device__ static inline int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(MEB_FULLMASK, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(MEB_FULLMASK, v, o));
+  return v;
+}
+
+// Block-wide sum in a fixed tree order; every thread gets the result.
+template <int NT>
+__device__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0) {
+    t = lane < NT / 32 ? sh[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) sh[0] = t;
+  }
+  __syncthreads();
+  t = sh[0];
+  __syncthreads();
+  return t;
+}
+
+template <int NT>
+__device__ double block_max(double v, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0) {
+    t = lane < NT / 32 ? sh[lane] : -INFINITY;
+    t = warp_max(t);
+    if (lane == 0) sh[0] = t;
+  }
+  __syncthreads();
+  t = sh[0];
+  __syncthreads();
+  return t;
+}
+
+// Distance to Q of a point (a, b) with ||b|| = n (closed form of ||z - Pi(z)||).
+__device__ __forceinline__ double soc_dist_an(double a, double n) {
+  if (n <= a) return 0.0;
+  if (n <= -a) return sqrt(a * a + n * n);
+  return (n - a) * 0.70710678118654752440;
+}
+
+// FP64 -> FP32 by truncation of the mantissa, with integer operations only
+// (the conversion instruction runs on the FP64 pipe).  |result| <= |x| and
+// |x - result| < 2^-23 |x| for normal results; |x| < 2^-126 gives 0 (absolute
+// error < 2^-126); |x| >= 2^128 gives +-inf (never certified).
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ff) - 1023 + 127;
+  unsigned r;
+  if (e <= 0) r = sign;                         // zero, subnormal, underflow
+  else if (e >= 255) r = sign | 0x7f800000u;    // overflow, inf, NaN -> inf
+  else r = sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return __uint_as_float(r);
+}
+
+// Shadow rounding unit (truncation of an FP64 value that itself carries one
+// FP64 rounding): |x - x32| <= kShadowU |x32| per element.
+constexpr float kU32 = 5.9604645e-08f;     // 2^-24
+constexpr float kShadowU = 2.02f * 2.0f * kU32;
+
+// Certified bounds on D = ||x - y|| from the FP32 shadows x32, y32:
+//   S = sum (x32 - y32)^2, N = sum x32^2 (fmaf sums over k4 elements, k4 = 4 d4),
+//   yn >= ||y32||.  Each of the k4 difference/square/sum steps is round-to-
+//   nearest; the shadows are within kShadowU of the exact values.
+__device__ __forceinline__ float dist_ub(float S, float N, float yn, int k4) {
+  return (sqrtf(S) + kShadowU * (sqrtf(N) + yn)) * (1.0f + (float)(k4 + 16) * kU32) + 1e-30f;
+}
+__device__ __forceinline__ float dist_lb(float S, float N, float yn, int k4) {
+  const float v = (sqrtf(S) * (1.0f - (float)(k4 + 16) * kU32)) - kShadowU * (sqrtf(N) + yn) *
+                  (1.0f + (float)(k4 + 16) * kU32) - 1e-30f;
+  return v > 0.0f ? v : 0.0f;
+}
+
+// Trial point for the next pass: ct = s * xt[1:] (exact), rt = s * xt[0],
+// the query shadow y32 = trunc32(ct - o) with yn >= ||y32||, rq32 = fl32(rt).
+__device__ __forceinline__ void set_trial(DevState* st, const DevVecs& V, int d, double* sh) {
+  const double s = st->s;
+  const int d4 = (d + 3) / 4;
+  double q = 0.0;
+  for (int j = threadIdx.x; j < 4 * d4; j += blockDim.x) {
+    float y = 0.0f;
+    if (j < d) {
+      const double c = V.xt[1 + j] * s;
+      V.ct[j] = c;
+      y = f64_to_f32_trunc(c - V.o[j]);
+    }
+    V.y32[j] = y;
+    q += (double)y * (double)y;
+  }
+  q = block_sum<256>(q, sh);
+  if (threadIdx.x == 0) {
+    st->rt_abs = V.xt[0] * s;
+    st->rq32 = __double2float_rn(V.xt[0] * s);
+    st->yn32 = __double2float_ru(sqrt(q) * (1.0 + 1e-12));
+  }
+  __syncthreads();
+}
+
+}  // namespace meb

@@ -26,6 +26,8 @@ enum : int {
   ACT_TRIAL = 2,    // a new trial point is set (backtrack); next is a pass
   ACT_OUTER = 3,    // outer step: multiplier update, then a pass at x
   ACT_DONE = 4,
+  ACT_GRAD = 5,     // trial accepted (or first evaluation): reduce the support rows
+  ACT_TRIAL_EARLY = 6,  // trial rejected from the certified lower bound; next trial set
 };
 
 // per-block partial record of the pass (doubles)
@@ -68,11 +70,16 @@ struct DevState {
   double sigma_prev;           // sigma of the finished outer step (multiplier update)
   int64_t n64_total;
   int chol_fail, eval_only;
+  int accept_mode;             // 1: accepted, go to the stop test; 2: accepted, outer forced
+  int need_fp64_solve;         // FP32 inverse + refinement failed: FP64 Cholesky
+  int fp64_solves;             // count of FP64 Cholesky fallbacks
+  int early_rejects;           // trials rejected by the certified lower bound
+  double dx2_t;                // ||xt - xk||^2 of the last trial
   double kkt[5], kkt_max;
   double last[P_COUNT];        // reduced partials of the last pass
   // trial point shadow for the FP32 screen
   double rt_abs;               // trial radius, unscaled
-  float rq32, yn32;            // fl32(r_t / s), an upper bound on ||y32||
+  float rq32, yn32;            // fl32(r_t), an upper bound on ||y32||
   // CG scratch scalars
   double cg_rz, cg_bn, cg_rtol;
   int cg_it, cg_done;
@@ -88,8 +95,9 @@ struct DevVecs {
   double* gt;     // gradient at the trial
   double* dx;     // Newton direction
   double* ct;     // trial centre, UNSCALED (c = s * xt[1:])
-  double* o;      // origin of the FP32 shadow, unscaled
-  float* y32;     // fl32((ct - o)/s), 4*d4 floats
+  double* o;      // origin of the FP32 shadow (the first centre), unscaled
+  double* c0;     // initial centre (mean of the centres), unscaled
+  float* y32;     // trunc32(ct - o), 4*d4 floats
   double* sv;     // sum of v^+ (d)
   double* sw;     // sum of w over case M (d)
   double* st1;    // [0]: sum_M (1 + t)
@@ -99,6 +107,7 @@ struct DevVecs {
 
 struct Buffers {
   int64_t launches;     // host-side count of kernels launched through these buffers
+  const double* C_in;   // centres of the current call (device)
   int64_t m_cap;
   int d_cap;
   int64_t nblk_cap;
@@ -113,6 +122,10 @@ struct Buffers {
   // pass outputs
   int* part_flag;       // [nblk]
   double* part;         // [nblk][P_COUNT]
+  int* unc_cnt;         // [nblk] balls each pass block could not certify
+  int* unc_idx;         // [ncand] their indices (per-block segments)
+  int* unc_slot;        // [ncand] their multiplier slots (-1: none)
+  float* vlb_part;      // [nblk] lower-bound partials of the early rejection
   int* cand_cnt;        // [nblk]
   int* cand_idx;        // [m_pad]
   unsigned char* cand_case;
@@ -126,7 +139,11 @@ struct Buffers {
   double* H;            // [n1*n1] assembled Hessian (eval entry / CG diag)
   double* hq;           // [n1] Hessian-vector product
   double* colsum_part;  // mean-centre partials
-  double* e;            // [m] r_i + ||c - c_i|| of the last feasibility pass
+  float* fe_ub;         // [m] certified upper bound on r_i + ||c - c_i||
+  float* fe_lb;         // [m] certified lower bound
+  float* fe_blb;        // [nblk] block maxima of the lower bounds
+  float* fe_L;          // [4] max lower bound, query norm bound
+  float* fq_y32;        // [4*d4] query shadow of the feasibility pass
   double* feas_part;    // feasibility partials
   int64_t* feas_ipart;
   int* feas_cnt;        // [nblk]
@@ -139,18 +156,20 @@ struct Buffers {
   double* vec_store;
 };
 
-// ---- launch wrappers (meb_kernels.cu) ----
-cudaError_t launch_colsum(const double* C, int64_t m, int d, double* part, double* out,
-                          cudaStream_t s);
-cudaError_t launch_feas(const double* C, const double* R, int64_t m, int d,
-                        const double* c, double r, double eps, int mode, double* e_out,
-                        Buffers& B, double* dmax_out, int64_t* argmax_out, int64_t* nviol_out,
-                        cudaStream_t s);
-cudaError_t launch_shadow(const double* C, const double* R, int64_t m, int d, int64_t m_pad,
-                          const double* o, double inv_s, float4* X32, float* R32, cudaStream_t s);
+// ---- launch wrappers: streaming kernels (meb_pass.cu) ----
+int pass_blocks(int64_t m, int* tiles_per_block);
+cudaError_t launch_shadow(const double* C, const double* R, int64_t m, int d, Buffers& B,
+                          double* o, double* c0, int* bad, cudaStream_t s);
 cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m, int d,
                         cudaStream_t s);
-cudaError_t launch_pass_post(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s);
+cudaError_t launch_support_rows(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s);
+cudaError_t launch_feas_cert(const double* C, const double* R, int64_t m, int d, const double* c,
+                             double r, double eps, int mode, int want_max, Buffers& B,
+                             double* dmax_out, int64_t* argmax_out, int64_t* nviol_out,
+                             cudaStream_t s);
+cudaError_t launch_support_from_dense(const double* U, const double* V, Buffers& B, int64_t m,
+                                      int d, cudaStream_t s);
+// ---- launch wrappers: solver kernels (meb_solve.cu) ----
 cudaError_t launch_tick_control(Buffers& B, int64_t m, int d, cudaStream_t s);
 cudaError_t launch_newton_dense(Buffers& B, int d, cudaStream_t s);
 cudaError_t launch_cg_setup(Buffers& B, int d, cudaStream_t s);
@@ -158,8 +177,6 @@ cudaError_t launch_cg_iter(Buffers& B, int d, cudaStream_t s);
 cudaError_t launch_cg_finish(Buffers& B, int d, cudaStream_t s);
 cudaError_t launch_mult_update(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s);
 cudaError_t launch_state_init(Buffers& B, int d, cudaStream_t s);
-cudaError_t launch_support_from_dense(const double* U, const double* V, Buffers& B, int64_t m,
-                                      int d, cudaStream_t s);
 cudaError_t launch_eval_outputs(const double* C, Buffers& B, int64_t m, int d, const double* q,
                                 double* Uplus, double* Vplus, double* Hq, double* H,
                                 cudaStream_t s);

@@ -1,0 +1,1000 @@
+// libmeb streaming kernels: the FP32 shadow of the centres, the full pass of
+// Algorithm 2 (step 1 and the per-ball parts of step 2), the support-row
+// reduction, and the certified feasibility pass of Sec. 4.2.
+//
+// Notation (Sec. 2, Sec. 4): for ball i with centre c_i and radius r_i, at
+// x = (r, c) with multipliers (u_i, v_i),
+//   z_i = (a_i, b_i) = (r_i - r, c_i - c)/s + (u_i, v_i)/sigma,
+//   (u_i^+, v_i^+) = sigma * Pi_Q(z_i),
+// with the cases of the closed-form projection I: ||b|| <= a (Pi = z),
+// Z: ||b|| <= -a (Pi = 0), M: otherwise.  s is the power-of-two scale of the
+// problem; multiplying differences by 1/s is exact.
+//
+// GB300 design: FP64 runs at about 2 lanes/clk/SM on this part, so full
+// passes stream the FP32 shadow (ball-interleaved float4, 16*ceil(d/4) bytes
+// per ball) and certify, with the rigorous bound of meb_common.cuh, that a
+// ball with zero multipliers lies strictly inside the current ball (case Z:
+// it contributes exactly nothing).  Every other ball is evaluated in FP64
+// from its original row.  All reductions use fixed block-to-ball maps and
+// fixed-order trees, so results are deterministic.
+#include "meb_common.cuh"
+
+namespace meb {
+
+
+// ===========================================================================
+// Shadow: X32[g][i] = trunc32(c_i[4g..4g+3] - o) (0 beyond d),
+// R32[i] = trunc32(r_i); o = c_0 (the first centre).  One FP64 subtraction per
+// element; the conversion uses integer operations.  A block takes 64
+// consecutive balls: their rows (contiguous in memory) are read coalesced,
+// in chunks of 128 columns, and written transposed through shared memory.
+// The same sweep checks that every centre and radius is finite (and r_i >= 0)
+// and leaves block partials of the shadow column sums for the mean centre.
+constexpr int kShadowNT = 256;
+constexpr int kShadowBalls = 64;
+constexpr int kShadowCols = 128;
+
+__global__ void __launch_bounds__(kShadowNT) k_shadow(const double* __restrict__ C,
+                                                      const double* __restrict__ R, int64_t m,
+                                                      int d, int64_t m_pad,
+                                                      float4* __restrict__ X32,
+                                                      float* __restrict__ R32,
+                                                      double* __restrict__ colpart,
+                                                      int* __restrict__ bad) {
+  __shared__ float tile[kShadowBalls][kShadowCols + 1];
+  __shared__ double s_o[kShadowCols];
+  const int64_t i0 = (int64_t)blockIdx.x * kShadowBalls;
+  const int nb = (int)imin64(kShadowBalls, m - i0);
+  int badf = 0;
+  for (int j0 = 0; j0 < d; j0 += kShadowCols) {
+    const int nc = min(kShadowCols, d - j0);
+    for (int j = threadIdx.x; j < nc; j += kShadowNT) s_o[j] = C[j0 + j];
+    __syncthreads();
+    // coalesced read of rows i0 .. i0+nb-1, columns j0 .. j0+nc-1
+    for (int e = threadIdx.x; e < nb * nc; e += kShadowNT) {
+      const int r = e / nc, cc = e - r * nc;
+      const double v = C[(i0 + r) * (int64_t)d + j0 + cc];
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+      badf |= ((bits >> 52) & 0x7ff) == 0x7ff;
+      tile[r][cc] = f64_to_f32_trunc(v - s_o[cc]);
+    }
+    __syncthreads();
+    // transposed write: group g of 4 columns for 64 balls; column sums
+    const int ng = (nc + 3) / 4;
+    for (int e = threadIdx.x; e < ng * kShadowBalls; e += kShadowNT) {
+      const int g = e / kShadowBalls, r = e - g * kShadowBalls;
+      if (r < nb) {
+        float v[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) v[k] = (4 * g + k < nc) ? tile[r][4 * g + k] : 0.0f;
+        X32[(int64_t)(j0 / 4 + g) * m_pad + i0 + r] = make_float4(v[0], v[1], v[2], v[3]);
+      }
+    }
+    for (int cc = threadIdx.x; cc < nc; cc += kShadowNT) {
+      float t = 0.0f;   // FP32 within the block (the mean is only a starting point)
+      for (int r = 0; r < nb; r++) t += tile[r][cc];
+      colpart[(int64_t)blockIdx.x * d + j0 + cc] = (double)t;
+    }
+    __syncthreads();
+  }
+  for (int r = threadIdx.x; r < nb; r += kShadowNT) {
+    const double v = R[i0 + r];
+    badf |= !(v >= 0.0) || !isfinite(v);
+    R32[i0 + r] = f64_to_f32_trunc(v);
+  }
+  if (__syncthreads_or(badf) && threadIdx.x == 0) atomicOr(bad, 1);
+}
+
+// Mean centre c0 = c_0 + (1/m) sum_i x32_i: block j sums column j over the
+// block partials in a fixed tree order.
+__global__ void k_shadow_mean(const double* __restrict__ C, const double* __restrict__ colpart,
+                              int nb, int d, int64_t m, double* __restrict__ o,
+                              double* __restrict__ c0) {
+  __shared__ double sh[32];
+  const int j = blockIdx.x;
+  double t = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 256) t += colpart[(int64_t)b * d + j];
+  t = block_sum<256>(t, sh);
+  if (threadIdx.x == 0) {
+    o[j] = C[j];
+    c0[j] = C[j] + t / (double)m;
+  }
+}
+
+cudaError_t launch_shadow(const double* C, const double* R, int64_t m, int d, Buffers& B,
+                          double* o, double* c0, int* bad, cudaStream_t s) {
+  const int64_t m_pad = ((m + 255) / 256) * 256;
+  const int nb = (int)((m + kShadowBalls - 1) / kShadowBalls);
+  k_shadow<<<nb, kShadowNT, 0, s>>>(C, R, m, d, m_pad, B.X32, B.R32, B.colsum_part, bad);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_shadow_mean<<<d, 256, 0, s>>>(C, B.colsum_part, nb, d, m, o, c0);
+  B.launches += 2;
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// The pass, in two kernels over the same block -> tiles map (block b takes the
+// tiles [b*T, (b+1)*T) of 256 balls):
+//  k_screen : one ball per thread; FP32 certificate from the shadows; the
+//             balls it cannot certify (and the balls holding multipliers) are
+//             appended, in ball order, to block b's list.
+//  k_rows64 : block b evaluates its list in FP64 from the original rows, one
+//             warp per ball: projection, multiplier, the per-ball parts of Psi,
+//             grad, the stop test and KKT; block partials and the ordered
+//             candidates of the support (cases I, M).
+struct PassArgs {
+  const double* C;
+  const double* R;
+  int64_t m, m_pad;
+  int d, d4, tiles_per_block;
+  const float4* X32;
+  const float* R32;
+  const int* slot;
+  const int* sup_idx0; const int* sup_idx1;
+  const double* sup_u0; const double* sup_u1;
+  const double* sup_v0; const double* sup_v1;
+  DevState* st;
+  const double* ct;
+  const float* y32;
+  int* unc_cnt;
+  int* unc_idx;
+  int* unc_slot;
+  float* vlb_part;      // per block: sum of max(0, certified lower bound of the violation)^2
+  int* part_flag;
+  double* part;
+  int* cand_cnt;
+  int* cand_idx;
+  unsigned char* cand_case;
+  double* cand_a; double* cand_n; double* cand_u;
+};
+
+__global__ void __launch_bounds__(kPassThreads) k_screen(PassArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DevState* st = A.st;
+  if (st->status != 0 || st->action == ACT_DONE) return;
+  const int d4 = A.d4;
+  float4* s_y = reinterpret_cast<float4*>(smem_raw);
+  __shared__ int s_wc[kPassWarps];
+  __shared__ float s_v2[kPassWarps];
+  const float4* y4 = reinterpret_cast<const float4*>(A.y32);
+  for (int g = threadIdx.x; g < d4; g += kPassThreads) s_y[g] = y4[g];
+  const int cur = st->sup_cur;
+  const int nsup = st->nsup;
+  const int* sidx = cur ? A.sup_idx1 : A.sup_idx0;
+  const float rq = st->rq32, yn = st->yn32;
+  float v2sum = 0.0f;
+  const int k4 = 4 * d4;
+  __syncthreads();
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t ntiles = (A.m + kPassThreads - 1) / kPassThreads;
+  const int64_t t0 = (int64_t)blockIdx.x * A.tiles_per_block;
+  const int64_t t1 = imin64(ntiles, t0 + A.tiles_per_block);
+  const int64_t base = t0 * kPassThreads;
+  int count = 0;
+  for (int64_t tile = t0; tile < t1; tile++) {
+    const int64_t i = tile * kPassThreads + tid;
+    bool need = false;
+    int myslot = -1;
+    if (i < A.m) {
+      const int sl = A.slot[i];
+      if ((unsigned)sl < (unsigned)nsup && sidx[sl] == (int)i) myslot = sl;
+      if (myslot >= 0) {
+        need = true;
+      } else {
+        // certify ||c_i - c|| <= r - r_i from the shadows
+        const float4* xp = A.X32 + i;
+        float S0 = 0.f, S1 = 0.f, N0 = 0.f, N1 = 0.f;
+        int g = 0;
+        for (; g + 4 <= d4; g += 4) {
+          float4 xa[4];
+#pragma unroll
+          for (int q = 0; q < 4; q++) xa[q] = xp[(int64_t)(g + q) * A.m_pad];
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const float4 ya = s_y[g + q];
+            float t;
+            float& S = (q & 1) ? S1 : S0;
+            float& N = (q & 1) ? N1 : N0;
+            t = xa[q].x - ya.x; S = fmaf(t, t, S); N = fmaf(xa[q].x, xa[q].x, N);
+            t = xa[q].y - ya.y; S = fmaf(t, t, S); N = fmaf(xa[q].y, xa[q].y, N);
+            t = xa[q].z - ya.z; S = fmaf(t, t, S); N = fmaf(xa[q].z, xa[q].z, N);
+            t = xa[q].w - ya.w; S = fmaf(t, t, S); N = fmaf(xa[q].w, xa[q].w, N);
+          }
+        }
+        for (; g < d4; g++) {
+          const float4 xa = xp[(int64_t)g * A.m_pad];
+          const float4 ya = s_y[g];
+          float t;
+          t = xa.x - ya.x; S0 = fmaf(t, t, S0); N0 = fmaf(xa.x, xa.x, N0);
+          t = xa.y - ya.y; S0 = fmaf(t, t, S0); N0 = fmaf(xa.y, xa.y, N0);
+          t = xa.z - ya.z; S0 = fmaf(t, t, S0); N0 = fmaf(xa.z, xa.z, N0);
+          t = xa.w - ya.w; S0 = fmaf(t, t, S0); N0 = fmaf(xa.w, xa.w, N0);
+        }
+        const float r32 = A.R32[i];
+        const float ub = dist_ub(S0 + S1, N0 + N1, yn, k4);
+        const float lb = (rq - r32) - 6.0f * kU32 * (fabsf(rq) + fabsf(r32)) - 1e-30f;
+        need = !(ub <= lb);
+        if (need) {
+          // violation ||c_i - c|| + r_i - r >= D_lb + r32 - rq - margins; with zero
+          // multipliers ||Pi(z_i)||^2 >= max(0, violation / s)^2 / 2
+          const float dl = dist_lb(S0 + S1, N0 + N1, yn, k4);
+          const float v = (dl + r32 - rq) - 3.0f * kU32 * (dl + fabsf(r32) + fabsf(rq));
+          if (v > 0.0f) v2sum = fmaf(v, v, v2sum);
+        }
+      }
+    }
+    const unsigned msk = __ballot_sync(MEB_FULLMASK, need);
+    if (lane == 0) s_wc[w] = __popc(msk);
+    __syncthreads();
+    int off = 0, tot = 0;
+#pragma unroll
+    for (int k = 0; k < kPassWarps; k++) {
+      off += (k < w) ? s_wc[k] : 0;
+      tot += s_wc[k];
+    }
+    if (need) {
+      const int64_t o = base + count + off + __popc(msk & ((1u << lane) - 1u));
+      A.unc_idx[o] = (int)i;
+      A.unc_slot[o] = myslot;
+    }
+    count += tot;
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v2sum += __shfl_xor_sync(MEB_FULLMASK, v2sum, o);
+  if (lane == 0) s_v2[w] = v2sum;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.0f;
+    for (int k = 0; k < kPassWarps; k++) t += s_v2[k];
+    A.unc_cnt[blockIdx.x] = count;
+    A.vlb_part[blockIdx.x] = t;
+  }
+}
+
+// Early line-search rejection (one block): from the screen's certified lower
+// bound Psi_lb <= Psi(trial) (only balls with zero multipliers counted), a
+// trial with Psi_lb above the Armijo threshold is rejected without its FP64
+// rows; the next trial is set as in the controller.
+__global__ void __launch_bounds__(256) k_early(Buffers B, int d, int nb) {
+  DevState* st = B.st;
+  if (st->status != 0 || st->action == ACT_DONE || st->phase != 1 || st->eval_only) return;
+  __shared__ double sh[32];
+  __shared__ int s_rej;
+  const DevVecs& V = B.vec;
+  const int n1 = d + 1;
+  double t = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 256) t += (double)B.vlb_part[b];
+  t = block_sum<256>(t, sh);
+  double dx2 = 0.0;
+  for (int k = threadIdx.x; k < n1; k += 256) {
+    const double dk = V.xt[k] - V.xk[k];
+    dx2 += dk * dk;
+  }
+  dx2 = block_sum<256>(dx2, sh);
+  if (threadIdx.x == 0) {
+    const double sigma = st->sigma, tos = st->tau / sigma;
+    // FP32 sums of nonnegative terms: keep 1% for their rounding
+    const double pi2_lb = 0.99 * t * st->inv_s * st->inv_s * 0.5;
+    const double psi_lb = V.xt[0] + 0.5 * sigma * pi2_lb + 0.5 * tos * dx2;
+    const double mag = fabs(V.xt[0]) + 0.5 * sigma * pi2_lb + 0.5 * tos * dx2;
+    const double allow = 64.0 * DBL_EPSILON * fmax(st->psi_mag, mag);
+    const double thr = st->psi + st->mu * st->eta * st->gdx + allow;
+    int rej = 0;
+    if (psi_lb > thr && st->bt < st->max_backtrack) {
+      const double eta = st->eta;
+      const double den = 2.0 * (psi_lb - st->psi - st->gdx * eta);
+      double en = (den > 0.0) ? -st->gdx * eta * eta / den : 0.5 * eta;
+      en = fmin(fmax(en, 0.1 * eta), 0.5 * eta);
+      st->eta = en;
+      st->bt += 1;
+      st->tot_bt += 1;
+      st->tot_passes += 1;
+      st->early_rejects += 1;
+      st->last[P_N64] = 0.0;
+      st->action = ACT_TRIAL_EARLY;
+      rej = 1;
+    }
+    s_rej = rej;
+  }
+  __syncthreads();
+  if (s_rej) {
+    const double eta = st->eta;
+    for (int k = threadIdx.x; k < n1; k += 256) V.xt[k] = V.x[k] + eta * V.dx[k];
+    __syncthreads();
+    set_trial(st, V, d, sh);
+  }
+}
+
+__global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DevState* st = A.st;
+  if (st->status != 0 || st->action == ACT_DONE || st->action == ACT_TRIAL_EARLY) return;
+  const int n_b = A.unc_cnt[blockIdx.x];
+  if (n_b == 0) {
+    if (threadIdx.x == 0) {
+      A.part_flag[blockIdx.x] = 0;
+      A.cand_cnt[blockIdx.x] = 0;
+    }
+    return;
+  }
+  const int d = A.d;
+  double* s_ct = reinterpret_cast<double*>(smem_raw);   // d
+  __shared__ unsigned char s_cf[kPassThreads];
+  __shared__ unsigned char s_cc[kPassThreads];
+  __shared__ double s_ca[kPassThreads], s_cn[kPassThreads], s_cu[kPassThreads];
+  __shared__ int s_wc[kPassWarps];
+  __shared__ double s_wp[kPassWarps][P_COUNT];
+  for (int j = threadIdx.x; j < d; j += kPassThreads) s_ct[j] = A.ct[j];
+  const int cur = st->sup_cur;
+  const double* su = cur ? A.sup_u1 : A.sup_u0;
+  const double* sv = cur ? A.sup_v1 : A.sup_v0;
+  const double inv_s = st->inv_s, sigma = st->sigma, inv_sigma = st->inv_sigma;
+  const double rt = st->rt_abs;
+  __syncthreads();
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t base = (int64_t)blockIdx.x * A.tiles_per_block * kPassThreads;
+  double acc[P_COUNT];
+#pragma unroll
+  for (int k = 0; k < P_COUNT; k++) acc[k] = 0.0;
+  int ccount = 0;
+  for (int c0 = 0; c0 < n_b; c0 += kPassThreads) {
+    const int tot = min(kPassThreads, n_b - c0);
+    // warp w takes the 32 chunk entries 32w .. 32w+31; lane q ends with entry q's sums
+    const int e0 = 32 * w;
+    double mnn = 0.0, mpp = 0.0, mdv = 0.0, mvv = 0.0;
+    const int my = e0 + lane;
+    const bool valid = my < tot;
+    const int64_t myii = valid ? (int64_t)A.unc_idx[base + c0 + my] : 0;
+    const int mysl = valid ? A.unc_slot[base + c0 + my] : -1;
+    for (int q = 0; q < 32 && e0 + q < tot; q++) {
+      const int64_t ii = __shfl_sync(MEB_FULLMASK, myii, q);
+      const int sl = __shfl_sync(MEB_FULLMASK, mysl, q);
+      const double* crow = A.C + ii * (int64_t)d;
+      double nn = 0.0, pp = 0.0, dv = 0.0, vv = 0.0;
+      if (sl >= 0) {
+        const double* vrow = sv + (int64_t)sl * d;
+        for (int j = lane; j < d; j += 32) {
+          const double dl = (crow[j] - s_ct[j]) * inv_s;
+          const double v = vrow[j];
+          const double b = fma(v, inv_sigma, dl);
+          nn = fma(b, b, nn);
+          pp = fma(dl, dl, pp);
+          dv = fma(dl, v, dv);
+          vv = fma(v, v, vv);
+        }
+        nn = warp_sum(nn); pp = warp_sum(pp); dv = warp_sum(dv); vv = warp_sum(vv);
+      } else {
+        for (int j = lane; j < d; j += 32) {
+          const double dl = (crow[j] - s_ct[j]) * inv_s;
+          nn = fma(dl, dl, nn);
+        }
+        nn = warp_sum(nn);
+        pp = nn;
+      }
+      if (lane == q) { mnn = nn; mpp = pp; mdv = dv; mvv = vv; }
+    }
+    if (valid) {
+      const int sl = mysl;
+      const int64_t ii = myii;
+      const double nn = mnn, pp = mpp, dv = mdv, vv = mvv;
+      const double uo = (sl >= 0) ? su[sl] : 0.0;
+      const double a = fma(uo, inv_sigma, (A.R[ii] - rt) * inv_s);
+      const double n = sqrt(nn);
+      int cs;
+      double pa, f, pi2;
+      if (n <= a) { cs = CASE_I; pa = a; f = 1.0; pi2 = a * a + nn; }
+      else if (n <= -a) { cs = CASE_Z; pa = 0.0; f = 0.0; pi2 = 0.0; }
+      else { cs = CASE_M; pa = 0.5 * (a + n); f = pa / n; pi2 = 2.0 * pa * pa; }
+      const double up = sigma * pa;
+      // b.v = dl.v + ||v||^2/sigma;  ||v^+ - v||^2 = sigma^2 f^2 nn - 2 sigma f (b.v) + vv
+      const double bv = dv + vv * inv_sigma;
+      const double sf = sigma * f;
+      double dvv = sf * sf * nn - 2.0 * sf * bv + vv;
+      if (dvv < 0.0) dvv = 0.0;
+      acc[P_PI2] += pi2;
+      acc[P_SU] += up;
+      acc[P_DUV2] += (up - uo) * (up - uo) + dvv;
+      acc[P_UV2] += uo * uo + vv;
+      const double ap = (rt - A.R[ii]) * inv_s;   // (r - r_i)/s
+      acc[P_KP] = fmax(acc[P_KP], soc_dist_an(ap, sqrt(pp)));
+      acc[P_KD] = fmax(acc[P_KD], soc_dist_an(up, sf * n));
+      // (r - r_i) u^+ + (c - c_i).v^+ = ap u^+ - sigma f (dl.b), dl.b = pp + dv/sigma
+      acc[P_KC] = fmax(acc[P_KC], fabs(ap * up - sf * (pp + dv * inv_sigma)));
+      if (cs != CASE_Z) acc[P_ZMAG] += fabs(a) + n;
+      acc[P_NI] += (cs == CASE_I);
+      acc[P_NM] += (cs == CASE_M);
+      acc[P_N64] += 1.0;
+      s_cf[my] = (cs != CASE_Z);
+      s_cc[my] = (unsigned char)cs;
+      s_ca[my] = a;
+      s_cn[my] = n;
+      s_cu[my] = up;
+    }
+    __syncthreads();
+    // ordered compaction of the candidates (cases I, M) of this chunk
+    const bool cf = (tid < tot) && s_cf[tid];
+    const unsigned cm = __ballot_sync(MEB_FULLMASK, cf);
+    if (lane == 0) s_wc[w] = __popc(cm);
+    __syncthreads();
+    int cpos = 0, ctot = 0;
+#pragma unroll
+    for (int k = 0; k < kPassWarps; k++) {
+      cpos += (k < w) ? s_wc[k] : 0;
+      ctot += s_wc[k];
+    }
+    if (cf) {
+      const int64_t o = base + ccount + cpos + __popc(cm & ((1u << lane) - 1u));
+      A.cand_idx[o] = A.unc_idx[base + c0 + tid];
+      A.cand_case[o] = s_cc[tid];
+      A.cand_a[o] = s_ca[tid];
+      A.cand_n[o] = s_cn[tid];
+      A.cand_u[o] = s_cu[tid];
+    }
+    ccount += ctot;
+    __syncthreads();
+  }
+  // block partial: per-lane accumulators -> warp (fixed tree) -> warps in order
+#pragma unroll
+  for (int k = 0; k < P_COUNT; k++) {
+    const bool ismax = (k == P_KP || k == P_KD || k == P_KC);
+    acc[k] = ismax ? warp_max(acc[k]) : warp_sum(acc[k]);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < P_COUNT; k++) s_wp[w][k] = acc[k];
+  }
+  __syncthreads();
+  if (tid < P_COUNT) {
+    const bool ismax = (tid == P_KP || tid == P_KD || tid == P_KC);
+    double t = 0.0;
+    for (int k = 0; k < kPassWarps; k++) t = ismax ? fmax(t, s_wp[k][tid]) : t + s_wp[k][tid];
+    A.part[(int64_t)blockIdx.x * P_COUNT + tid] = t;
+  }
+  if (tid == 0) {
+    A.part_flag[blockIdx.x] = 1;
+    A.cand_cnt[blockIdx.x] = ccount;
+  }
+}
+
+int pass_blocks(int64_t m, int* tiles_per_block) {
+  const int64_t ntiles = (m + kPassThreads - 1) / kPassThreads;
+  const int64_t target = 152 * 6;
+  int64_t tpb = (ntiles + target - 1) / target;
+  if (tpb < 1) tpb = 1;
+  *tiles_per_block = (int)tpb;
+  return (int)((ntiles + tpb - 1) / tpb);
+}
+
+cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m, int d,
+                        cudaStream_t s) {
+  PassArgs A;
+  A.C = C; A.R = R; A.m = m;
+  const int d4 = (d + 3) / 4;
+  A.m_pad = ((m + 255) / 256) * 256;
+  A.d = d; A.d4 = d4;
+  const int nb = pass_blocks(m, &A.tiles_per_block);
+  A.X32 = B.X32; A.R32 = B.R32; A.slot = B.slot;
+  A.sup_idx0 = B.sup_idx[0]; A.sup_idx1 = B.sup_idx[1];
+  A.sup_u0 = B.sup_u[0]; A.sup_u1 = B.sup_u[1];
+  A.sup_v0 = B.sup_v[0]; A.sup_v1 = B.sup_v[1];
+  A.st = B.st; A.ct = B.vec.ct; A.y32 = B.vec.y32;
+  A.unc_cnt = B.unc_cnt; A.unc_idx = B.unc_idx; A.unc_slot = B.unc_slot;
+  A.vlb_part = B.vlb_part;
+  A.part_flag = B.part_flag; A.part = B.part;
+  A.cand_cnt = B.cand_cnt; A.cand_idx = B.cand_idx; A.cand_case = B.cand_case;
+  A.cand_a = B.cand_a; A.cand_n = B.cand_n; A.cand_u = B.cand_u;
+  const size_t sh1 = 16 * (size_t)d4;
+  cudaError_t e;
+  if (sh1 > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh1);
+    if (e != cudaSuccess) return e;
+  }
+  k_screen<<<nb, kPassThreads, sh1, s>>>(A);
+  k_early<<<1, 256, 0, s>>>(B, d, nb);
+  const size_t sh2 = 8 * (size_t)d;
+  if (sh2 > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_rows64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh2);
+    if (e != cudaSuccess) return e;
+  }
+  k_rows64<<<nb, kPassThreads, sh2, s>>>(A);
+  B.launches += 3;
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// Ordered gather of the pass candidates (block b's segment at b*T*256) into
+// the support list S.
+__global__ void k_compact_S(Buffers B, int nb, int64_t seg) {
+  DevState* st = B.st;
+  if (st->status != 0 || st->action != ACT_GRAD) return;
+  __shared__ long long sh[256];
+  __shared__ long long sc[256];
+  const int b0 = blockIdx.x * 256;
+  long long pre = 0;
+  for (int t = threadIdx.x; t < b0; t += 256) pre += B.cand_cnt[t];
+  sh[threadIdx.x] = pre;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  const long long base = sh[0];
+  __syncthreads();
+  const int t = b0 + threadIdx.x;
+  sc[threadIdx.x] = (t < nb) ? B.cand_cnt[t] : 0;
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {
+    long long v = threadIdx.x >= o ? sc[threadIdx.x - o] : 0;
+    __syncthreads();
+    sc[threadIdx.x] += v;
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = w; k < 256; k += 8) {
+    const int tt = b0 + k;
+    if (tt >= nb) break;
+    const long long n = B.cand_cnt[tt];
+    const long long s0 = base + sc[k] - n;
+    for (long long e = lane; e < n; e += 32) {
+      const int64_t src = (int64_t)tt * seg + e;
+      const int64_t dst = s0 + e;
+      B.S_idx[dst] = B.cand_idx[src];
+      B.S_case[dst] = B.cand_case[src];
+      B.S_a[dst] = B.cand_a[src];
+      B.S_n[dst] = B.cand_n[src];
+      B.S_u[dst] = B.cand_u[src];
+    }
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 255) st->nS = (int)(base + sc[255]);
+}
+
+// Support rows: b_k = (c_k - c)/s + v_k/sigma recomputed in FP64;
+//   sum v^+ = sigma f_k b_k (all S), sum w_k (case M), sum t_k w_k^2 (case M),
+//   sum (1 + t_k) (case M);  W rows w_k = b_k / n_k (M) or b_k (I).
+// Block b takes rows [b*rpb, (b+1)*rpb) in order; thread j owns columns j, j+256, ...
+__global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buffers B, int d) {
+  DevState* st = B.st;
+  if (st->status != 0 || st->action != ACT_GRAD) return;
+  const int nS = st->nS;
+  int rpb = (nS + kSvecBlocks - 1) / kSvecBlocks;
+  if (rpb < 8) rpb = 8;
+  const int nblk = (nS + rpb - 1) / rpb;
+  if (blockIdx.x == 0 && threadIdx.x == 0) { st->svec_nb = nblk; st->svec_rpb = rpb; }
+  if ((int)blockIdx.x >= nblk) return;
+  const int k0 = blockIdx.x * rpb, k1 = min(nS, k0 + rpb);
+  const int cur = st->sup_cur, nsup = st->nsup;
+  const int* sidx = cur ? B.sup_idx[1] : B.sup_idx[0];
+  const double* sv = cur ? B.sup_v[1] : B.sup_v[0];
+  const double inv_s = st->inv_s, sigma = st->sigma, inv_sigma = st->inv_sigma;
+  const double* ct = B.vec.ct;
+  double* out = B.svec_part + (int64_t)blockIdx.x * (3 * d + 1);
+  double s1t = 0.0;
+  for (int j0 = 0; j0 < d; j0 += 256) {
+    const int j = j0 + threadIdx.x;
+    double av = 0.0, aw = 0.0, atw = 0.0;
+    for (int k = k0; k < k1; k++) {
+      const int idx = B.S_idx[k];
+      const int cs = B.S_case[k];
+      const double a = B.S_a[k], n = B.S_n[k];
+      const int sl0 = B.slot[idx];
+      const int sl = ((unsigned)sl0 < (unsigned)nsup && sidx[sl0] == idx) ? sl0 : -1;
+      if (j0 == 0 && threadIdx.x == 0) {
+        const double t = (cs == CASE_M) ? a / n : 0.0;
+        B.S_t[k] = t;
+        if (cs == CASE_M) s1t += 1.0 + t;
+      }
+      if (j < d) {
+        double b = (C[(int64_t)idx * d + j] - ct[j]) * inv_s;
+        if (sl >= 0) b = fma(sv[(int64_t)sl * d + j], inv_sigma, b);
+        if (cs == CASE_I) {
+          av += sigma * b;
+          B.W[(int64_t)k * d + j] = b;
+        } else {
+          const double f = 0.5 * (a + n) / n;
+          const double wv = b / n;
+          const double t = a / n;
+          av += sigma * f * b;
+          aw += wv;
+          atw += t * wv * wv;
+          B.W[(int64_t)k * d + j] = wv;
+        }
+      }
+    }
+    if (j < d) {
+      out[j] = av;
+      out[d + j] = aw;
+      out[2 * d + j] = atw;
+    }
+  }
+  if (threadIdx.x == 0) out[3 * d] = s1t;
+}
+
+cudaError_t launch_support_rows(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s) {
+  int tpb;
+  const int nb = pass_blocks(m, &tpb);
+  k_compact_S<<<(nb + 255) / 256, 256, 0, s>>>(B, nb, (int64_t)tpb * kPassThreads);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_svec<<<kSvecBlocks, 256, 0, s>>>(C, B, d);
+  B.launches += 2;
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// Certified feasibility pass (Sec. 4.2).  For every ball, e_i = r_i + ||c - c_i||
+// (FP64, by definition) and
+//   mode 0: val_i = e_i - r;  max val (lowest index on ties), list {val_i > eps}
+//   mode 1: val_i = (r - r_i) - ||c - c_i|| (slack);  list {val_i <= eps}
+//   mode 2: the maximum of mode 0 only
+// Sweep A bounds e_i from the shadows (FP32, rigorous) and keeps the block
+// maxima of the lower bounds; sweep B evaluates in FP64 exactly the balls that
+// could be the maximum or whose list membership the bounds do not decide.
+constexpr int kFeasNT = 256;
+
+struct FeasArgs {
+  const double* C; const double* R;
+  int64_t m, m_pad;
+  int d, d4;
+  const float4* X32; const float* R32;
+  const double* c;      // query centre (unscaled)
+  const float* y32;     // trunc32(c - o), 4*d4 floats
+  const float* ynp;     // device: upper bound on ||y32||
+  double r, eps;
+  int mode;
+  int want_max;
+  float* eub;           // [m] upper bound on e_i
+  float* elb;           // [m] lower bound on e_i
+  float* blb;           // [nb] block max of the lower bounds
+  double* bmax; int64_t* barg; int* bcnt; int64_t* blist;
+  const float* L;       // device: max over blocks of blb
+};
+
+__global__ void __launch_bounds__(kFeasNT) k_feas_a(FeasArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* s_y = reinterpret_cast<float4*>(smem_raw);
+  __shared__ float s_m[kFeasNT / 32];
+  const float4* y4 = reinterpret_cast<const float4*>(A.y32);
+  for (int g = threadIdx.x; g < A.d4; g += kFeasNT) s_y[g] = y4[g];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * kFeasNT + threadIdx.x;
+  float lbv = -INFINITY;
+  if (i < A.m) {
+    const float4* xp = A.X32 + i;
+    float S = 0.f, N = 0.f;
+    for (int g = 0; g < A.d4; g++) {
+      const float4 xa = xp[(int64_t)g * A.m_pad];
+      const float4 ya = s_y[g];
+      float t;
+      t = xa.x - ya.x; S = fmaf(t, t, S); N = fmaf(xa.x, xa.x, N);
+      t = xa.y - ya.y; S = fmaf(t, t, S); N = fmaf(xa.y, xa.y, N);
+      t = xa.z - ya.z; S = fmaf(t, t, S); N = fmaf(xa.z, xa.z, N);
+      t = xa.w - ya.w; S = fmaf(t, t, S); N = fmaf(xa.w, xa.w, N);
+    }
+    const int k4 = 4 * A.d4;
+    const float yn = *A.ynp;
+    const float r32 = A.R32[i];   // r32 <= r_i <= r32 (1 + 2^-23)/(1 - 2^-23)
+    const float eu = (r32 * (1.0f + 5.0f * kU32) + dist_ub(S, N, yn, k4)) * (1.0f + 2.0f * kU32);
+    const float el = (r32 + dist_lb(S, N, yn, k4)) * (1.0f - 2.0f * kU32);
+    A.eub[i] = eu;
+    A.elb[i] = el;
+    lbv = el;
+  }
+  float t = lbv;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(MEB_FULLMASK, t, o));
+  if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = s_m[0];
+    for (int k = 1; k < kFeasNT / 32; k++) v = fmaxf(v, s_m[k]);
+    A.blb[blockIdx.x] = v;
+  }
+}
+
+__global__ void k_feas_L(const float* __restrict__ blb, int nb, float* __restrict__ L) {
+  __shared__ float sm[256];
+  float v = -INFINITY;
+  for (int b = threadIdx.x; b < nb; b += 256) v = fmaxf(v, blb[b]);
+  sm[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] = fmaxf(sm[threadIdx.x], sm[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *L = sm[0];
+}
+
+__global__ void __launch_bounds__(kFeasNT) k_feas_b(FeasArgs A) {
+  extern __shared__ double s_c[];
+  __shared__ int s_list[kFeasNT];
+  __shared__ unsigned char s_in[kFeasNT];     // list membership
+  __shared__ double s_v[kFeasNT];
+  __shared__ int64_t s_i[kFeasNT];
+  __shared__ int s_wc[kFeasNT / 32];
+  for (int j = threadIdx.x; j < A.d; j += kFeasNT) s_c[j] = A.c[j];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t i = (int64_t)blockIdx.x * kFeasNT + tid;
+  const double L = A.want_max ? (double)*A.L : INFINITY;
+  // decide from the bounds; 'need' = evaluate in FP64
+  bool need = false;
+  unsigned char in = 0;
+  if (i < A.m) {
+    const double eu = (double)A.eub[i], el = (double)A.elb[i];
+    const double ae = isinf(A.eps) ? 0.0 : fabs(A.eps);
+    const double tolr = 4.0 * DBL_EPSILON * (fabs(eu) + fabs(A.r) + ae);
+    if (A.want_max && eu >= L) need = true;
+    if (A.mode == 0) {
+      if (el - A.r > A.eps + tolr) in = 1;
+      else if (!(eu - A.r <= A.eps - tolr)) need = true;
+    } else if (A.mode == 1) {
+      // slack in [r - eu, r - el]
+      if ((A.r - el) <= A.eps - tolr) in = 1;
+      else if (!((A.r - eu) > A.eps + tolr)) need = true;
+    }   // mode 2: maximum only
+  }
+  s_in[tid] = in;
+  const unsigned msk = __ballot_sync(MEB_FULLMASK, need);
+  if (lane == 0) s_wc[w] = __popc(msk);
+  __syncthreads();
+  int off = 0, tot = 0;
+  for (int k = 0; k < kFeasNT / 32; k++) {
+    off += (k < w) ? s_wc[k] : 0;
+    tot += s_wc[k];
+  }
+  if (need) s_list[off + __popc(msk & ((1u << lane) - 1u))] = tid;
+  s_v[tid] = -INFINITY;
+  s_i[tid] = INT64_MAX;
+  __syncthreads();
+  // FP64 rows, warp per ball
+  for (int k = w; k < tot; k += kFeasNT / 32) {
+    const int loc = s_list[k];
+    const int64_t ii = (int64_t)blockIdx.x * kFeasNT + loc;
+    const double* row = A.C + ii * (int64_t)A.d;
+    double acc = 0.0;
+    for (int j = lane; j < A.d; j += 32) {
+      const double t = s_c[j] - row[j];
+      acc = fma(t, t, acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      const double n = sqrt(acc);
+      if (A.mode != 1) {
+        const double val = (A.R[ii] + n) - A.r;
+        s_in[loc] = (A.mode == 0) && (val > A.eps);
+        s_v[loc] = val;
+        s_i[loc] = ii;
+      } else {
+        const double val = (A.r - A.R[ii]) - n;
+        s_in[loc] = val <= A.eps;
+      }
+    }
+  }
+  __syncthreads();
+  // block max (lowest index on ties) among the FP64-evaluated balls
+  for (int o = kFeasNT / 2; o > 0; o >>= 1) {
+    if (tid < o) {
+      const double v2 = s_v[tid + o];
+      const int64_t i2 = s_i[tid + o];
+      if (v2 > s_v[tid] || (v2 == s_v[tid] && i2 < s_i[tid])) { s_v[tid] = v2; s_i[tid] = i2; }
+    }
+    __syncthreads();
+  }
+  // ordered list of members of this tile
+  const bool fl = (i < A.m) && s_in[tid];
+  const unsigned lm = __ballot_sync(MEB_FULLMASK, fl);
+  __syncthreads();
+  if (lane == 0) s_wc[w] = __popc(lm);
+  __syncthreads();
+  int loff = 0, ltot = 0;
+  for (int k = 0; k < kFeasNT / 32; k++) {
+    loff += (k < w) ? s_wc[k] : 0;
+    ltot += s_wc[k];
+  }
+  if (fl) A.blist[(int64_t)blockIdx.x * kFeasNT + loff + __popc(lm & ((1u << lane) - 1u))] = i;
+  if (tid == 0) {
+    A.bmax[blockIdx.x] = s_v[0];
+    A.barg[blockIdx.x] = s_i[0];
+    A.bcnt[blockIdx.x] = ltot;
+  }
+}
+
+// One block: max over blocks (lowest index on ties), total count.
+__global__ void k_feas_final(const double* __restrict__ bmax, const int64_t* __restrict__ barg,
+                             const int* __restrict__ bcnt, int nb, double* out_max,
+                             int64_t* out_arg, int64_t* out_cnt) {
+  __shared__ double sv[256];
+  __shared__ int64_t si[256];
+  __shared__ long long sc[256];
+  double best = -INFINITY;
+  int64_t bi = INT64_MAX;
+  long long cnt = 0;
+  for (int b = threadIdx.x; b < nb; b += 256) {
+    const double v = bmax[b];
+    const int64_t ix = barg[b];
+    if (v > best || (v == best && ix < bi)) { best = v; bi = ix; }
+    cnt += bcnt[b];
+  }
+  sv[threadIdx.x] = best; si[threadIdx.x] = bi; sc[threadIdx.x] = cnt;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double v2 = sv[threadIdx.x + o];
+      const int64_t i2 = si[threadIdx.x + o];
+      if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
+        sv[threadIdx.x] = v2; si[threadIdx.x] = i2;
+      }
+      sc[threadIdx.x] += sc[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (out_max) *out_max = sv[0];
+    if (out_arg) *out_arg = si[0];
+    if (out_cnt) *out_cnt = sc[0];
+  }
+}
+
+// Ordered gather of per-tile lists (tile t holds cnt[t] entries at t*T).
+__global__ void k_gather_lists(const int* __restrict__ cnt, const int64_t* __restrict__ lists,
+                               int nb, int T, int64_t* __restrict__ out, int64_t cap) {
+  __shared__ long long sh[256];
+  const int b0 = blockIdx.x * 256;
+  long long pre = 0;
+  for (int t = threadIdx.x; t < b0; t += 256) pre += cnt[t];
+  sh[threadIdx.x] = pre;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  const long long base = sh[0];
+  __syncthreads();
+  const int t = b0 + threadIdx.x;
+  const long long my = (t < nb) ? cnt[t] : 0;
+  sh[threadIdx.x] = my;
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {
+    const long long v = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += v;
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = w; k < 256; k += 8) {
+    const int tt = b0 + k;
+    if (tt >= nb) break;
+    const long long n = cnt[tt];
+    const long long st0 = base + sh[k] - n;
+    for (long long e = lane; e < n; e += 32) {
+      const long long pos = st0 + e;
+      if (pos < cap) out[pos] = lists[(int64_t)tt * T + e];
+    }
+  }
+}
+
+// Sum of per-tile counts into *out (one block).
+__global__ void k_count_sum(const int* __restrict__ cnt, int nb, int64_t* __restrict__ out) {
+  __shared__ long long sh[256];
+  long long v = 0;
+  for (int b = threadIdx.x; b < nb; b += 256) v += cnt[b];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// Query shadow for the feasibility pass: y32 = trunc32(c - o), yn >= ||y32||.
+__global__ void k_query_shadow(const double* __restrict__ c, const double* __restrict__ o, int d,
+                               float* __restrict__ y32, float* __restrict__ yn) {
+  __shared__ double sh[32];
+  const int d4 = (d + 3) / 4;
+  double q = 0.0;
+  for (int j = threadIdx.x; j < 4 * d4; j += blockDim.x) {
+    const float y = (j < d) ? f64_to_f32_trunc(c[j] - o[j]) : 0.0f;
+    y32[j] = y;
+    q += (double)y * (double)y;
+  }
+  q = block_sum<256>(q, sh);
+  if (threadIdx.x == 0) *yn = __double2float_ru(sqrt(q) * (1.0 + 1e-12));
+}
+
+cudaError_t launch_feas_cert(const double* C, const double* R, int64_t m, int d, const double* c,
+                             double r, double eps, int mode, int want_max, Buffers& B,
+                             double* dmax_out, int64_t* argmax_out, int64_t* nviol_out,
+                             cudaStream_t s) {
+  FeasArgs A;
+  A.C = C; A.R = R; A.m = m;
+  A.m_pad = ((m + 255) / 256) * 256;
+  A.d = d; A.d4 = (d + 3) / 4;
+  A.X32 = B.X32; A.R32 = B.R32;
+  A.c = c;
+  A.y32 = B.fq_y32;
+  A.r = r; A.eps = eps; A.mode = mode; A.want_max = want_max;
+  A.eub = B.fe_ub; A.elb = B.fe_lb; A.blb = B.fe_blb;
+  A.bmax = B.feas_part; A.barg = B.feas_ipart; A.bcnt = B.feas_cnt; A.blist = B.list_tmp;
+  A.L = B.fe_L;
+  A.ynp = B.fe_L + 1;
+  const int nb = (int)((m + kFeasNT - 1) / kFeasNT);
+  k_query_shadow<<<1, 256, 0, s>>>(c, B.vec.o, d, B.fq_y32, B.fe_L + 1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t sha = 16 * (size_t)A.d4;
+  if (sha > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_feas_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sha);
+    if (e != cudaSuccess) return e;
+  }
+  k_feas_a<<<nb, kFeasNT, sha, s>>>(A);
+  if (want_max) k_feas_L<<<1, 256, 0, s>>>(B.fe_blb, nb, B.fe_L);
+  const size_t shb = 8 * (size_t)d;
+  if (shb > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_feas_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
+    if (e != cudaSuccess) return e;
+  }
+  k_feas_b<<<nb, kFeasNT, shb, s>>>(A);
+  k_feas_final<<<1, 256, 0, s>>>(B.feas_part, B.feas_ipart, B.feas_cnt, nb, dmax_out, argmax_out,
+                                 nviol_out);
+  k_gather_lists<<<(nb + 255) / 256, 256, 0, s>>>(B.feas_cnt, B.list_tmp, nb, kFeasNT, B.viol, m);
+  B.launches += want_max ? 6 : 5;
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// Evaluation entry: support from dense (U, V) rows.
+__global__ void k_dense_flags(const double* __restrict__ U, const double* __restrict__ V,
+                              int64_t m, int d, int* __restrict__ cnt,
+                              int64_t* __restrict__ lists) {
+  __shared__ int s_wc[8];
+  const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  bool nz = false;
+  if (i < m) {
+    nz = U[i] != 0.0;
+    for (int j = 0; j < d && !nz; j++) nz = V[i * (int64_t)d + j] != 0.0;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned msk = __ballot_sync(MEB_FULLMASK, nz);
+  if (lane == 0) s_wc[w] = __popc(msk);
+  __syncthreads();
+  int off = 0, tot = 0;
+  for (int k = 0; k < 8; k++) { off += (k < w) ? s_wc[k] : 0; tot += s_wc[k]; }
+  if (nz) lists[(int64_t)blockIdx.x * 256 + off + __popc(msk & ((1u << lane) - 1u))] = i;
+  if (threadIdx.x == 0) cnt[blockIdx.x] = tot;
+}
+
+__global__ void k_dense_support(const double* __restrict__ U, const double* __restrict__ V,
+                                const int64_t* __restrict__ list, const int64_t* __restrict__ n,
+                                int d, Buffers B) {
+  const int64_t ns = *n;
+  const int lane = threadIdx.x & 31;
+  for (int64_t k = ((int64_t)blockIdx.x * 256 + threadIdx.x) >> 5; k < ns;
+       k += ((int64_t)gridDim.x * 256) >> 5) {
+    const int64_t i = list[k];
+    for (int j = lane; j < d; j += 32) B.sup_v[0][k * d + j] = V[i * (int64_t)d + j];
+    if (lane == 0) {
+      B.sup_idx[0][k] = (int)i;
+      B.sup_u[0][k] = U[i];
+      B.slot[i] = (int)k;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    B.st->sup_cur = 0;
+    B.st->nsup = (int)ns;
+  }
+}
+
+cudaError_t launch_support_from_dense(const double* U, const double* V, Buffers& B, int64_t m,
+                                      int d, cudaStream_t s) {
+  const int nb = (int)((m + 255) / 256);
+  k_dense_flags<<<nb, 256, 0, s>>>(U, V, m, d, B.feas_cnt, B.list_tmp);
+  k_gather_lists<<<(nb + 255) / 256, 256, 0, s>>>(B.feas_cnt, B.list_tmp, nb, 256, B.viol, m);
+  k_count_sum<<<1, 256, 0, s>>>(B.feas_cnt, nb, B.count64);
+  k_dense_support<<<304, 256, 0, s>>>(U, V, B.viol, B.count64, d, B);
+  B.launches += 4;
+  return cudaGetLastError();
+}
+
+}  // namespace meb

@@ -1,0 +1,1070 @@
+// libmeb solver kernels: the device-resident controller of Algorithms 1 and 2,
+// the Newton systems (dense and matrix-free), the multiplier update and the
+// evaluation-entry outputs, for sm_103a.
+//
+// Notation (Sec. 2, Sec. 4): at x = (r, c) with multipliers (u_i, v_i),
+// z_i = (r_i - r, c_i - c)/s + (u_i, v_i)/sigma and (u_i^+, v_i^+) = sigma Pi_Q(z_i).
+// The iterate lives on the scaled problem (data divided by the power of two
+// s); the streaming kernels read the unscaled input.  The controller kernels
+// run on one block; their vector work (length d + 1) is spread over it.
+#include <cuda_runtime.h>
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "meb_common.cuh"
+
+namespace meb {
+
+// ===========================================================================
+// Controller (one block): reduces the pass, forms grad and Psi, and takes the
+// decisions of Algorithms 1 and 2.  Vector work is spread over the block.
+
+// Outer update (Algorithm 1): (alpha,beta) -= sigma g, KKT_max, sigma rule.
+// Returns the action; thread 0 writes the state.
+__device__ void do_outer(DevState* st, const DevVecs& V, int d, double* sh) {
+  const int n1 = d + 1;
+  const double sigma = st->sigma;
+  for (int k = threadIdx.x; k < n1; k += blockDim.x) V.ab[k] -= sigma * V.g[k];
+  double q = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) q += V.sv[j] * V.sv[j];
+  q = block_sum<256>(q, sh);
+  __shared__ int s_act;
+  if (threadIdx.x == 0) {
+    st->kkt[0] = fabs(1.0 - st->last[P_SU]);
+    st->kkt[1] = sqrt(q);
+    st->kkt[2] = st->last[P_KP];
+    st->kkt[3] = st->last[P_KD];
+    st->kkt[4] = st->last[P_KC];
+    double km = 0.0;
+    for (int k = 0; k < 5; k++) km = fmax(km, st->kkt[k]);
+    st->kkt_max = km;
+    st->outer += 1;
+    int act;
+    if (km <= st->tol) { st->status = 1; act = ACT_DONE; }
+    else if (st->outer >= st->max_outer) { st->status = 2; act = ACT_DONE; }
+    else {
+      act = ACT_OUTER;
+      const double pinf = st->last[P_KP];
+      // the multiplier update uses the sigma of the finished outer step
+      st->sigma_prev = sigma;
+      if (pinf > st->tol && pinf > st->sigma_ratio * st->pinf_prev) {
+        double sg = sigma * st->sigma_growth;
+        if (sg > st->sigma_max) sg = st->sigma_max;
+        st->sigma = sg;
+        st->inv_sigma = 1.0 / sg;
+      }
+      st->pinf_prev = pinf;
+      st->phase = 0;
+    }
+    st->action = act;
+    s_act = act;
+  }
+  __syncthreads();
+  if (s_act == ACT_OUTER) {
+    for (int k = threadIdx.x; k < n1; k += blockDim.x) {
+      V.xk[k] = V.x[k];
+      V.xt[k] = V.x[k];
+    }
+    __syncthreads();
+    set_trial(st, V, d, sh);
+  }
+}
+
+// Controller, part A (one block): reduce the pass partials, form Psi at the
+// trial and take the line-search decision (Algorithm 2).  A rejected trial
+// sets the next trial directly; an accepted one (or the first evaluation of an
+// outer step) asks for the gradient: action ACT_GRAD.
+__global__ void __launch_bounds__(256) k_control_a(Buffers B, int d, int nb) {
+  DevState* st = B.st;
+  if (st->status != 0 || st->action == ACT_DONE) return;
+  if (st->action == ACT_TRIAL_EARLY) {   // decided by k_early; the next pass evaluates the new trial
+    if (threadIdx.x == 0) st->action = ACT_TRIAL;
+    return;
+  }
+  const DevVecs& V = B.vec;
+  const int n1 = d + 1;
+  __shared__ double sh[32];
+  __shared__ double s_last[P_COUNT];
+  __shared__ int s_next;
+  {
+    double acc[P_COUNT];
+#pragma unroll
+    for (int k = 0; k < P_COUNT; k++) acc[k] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 256) {
+      if (!B.part_flag[b]) continue;
+      const double* p = B.part + (int64_t)b * P_COUNT;
+#pragma unroll
+      for (int k = 0; k < P_COUNT; k++) {
+        const bool ismax = (k == P_KP || k == P_KD || k == P_KC);
+        acc[k] = ismax ? fmax(acc[k], p[k]) : acc[k] + p[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < P_COUNT; k++) {
+      const bool ismax = (k == P_KP || k == P_KD || k == P_KC);
+      const double r = ismax ? block_max<256>(acc[k], sh) : block_sum<256>(acc[k], sh);
+      if (threadIdx.x == 0) s_last[k] = r;
+    }
+  }
+  const double sigma = st->sigma, tos = st->tau / sigma;
+  double dx2 = 0.0;
+  for (int k = threadIdx.x; k < n1; k += 256) {
+    const double dk = V.xt[k] - V.xk[k];
+    dx2 += dk * dk;
+  }
+  dx2 = block_sum<256>(dx2, sh);
+  const double psi_t = V.xt[0] + 0.5 * sigma * s_last[P_PI2] + 0.5 * tos * dx2;
+  const double mag_t = fabs(V.xt[0]) + 0.5 * sigma * s_last[P_PI2] + 0.5 * tos * dx2;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < P_COUNT; k++) st->last[k] = s_last[k];
+    st->tot_passes += 1;
+    st->n64_total += (int64_t)s_last[P_N64];
+    st->dx2_t = dx2;
+    int nxt = 0;   // 0: gradient at the (accepted) trial; 1: backtrack
+    if (st->eval_only) {
+      st->psi = psi_t - s_last[P_UV2] / (2.0 * sigma);
+      st->accept_mode = 0;
+    } else if (st->phase == 1) {
+      const double allow = 64.0 * DBL_EPSILON * fmax(st->psi_mag, mag_t);
+      const bool ok = psi_t <= st->psi + st->mu * st->eta * st->gdx + allow;
+      if (ok || st->bt >= st->max_backtrack) {
+        st->psi = psi_t; st->psi_mag = mag_t;
+        st->ssn_j += 1;
+        st->tot_ssn += 1;
+        st->accept_mode = (!ok || st->ssn_j >= st->max_ssn) ? 2 : 1;   // 2: outer forced
+      } else {
+        // next step: minimiser of the quadratic through Psi(0), Psi'(0), Psi(eta),
+        // kept in [eta/10, eta/2]
+        const double eta = st->eta;
+        const double den = 2.0 * (psi_t - st->psi - st->gdx * eta);
+        double en = (den > 0.0) ? -st->gdx * eta * eta / den : 0.5 * eta;
+        en = fmin(fmax(en, 0.1 * eta), 0.5 * eta);
+        st->eta = en;
+        st->bt += 1;
+        st->tot_bt += 1;
+        nxt = 1;
+      }
+    } else {
+      st->psi = psi_t; st->psi_mag = mag_t;
+      st->ssn_j = 0;
+      st->accept_mode = 1;
+    }
+    st->action = nxt ? ACT_TRIAL : ACT_GRAD;
+    s_next = nxt;
+  }
+  __syncthreads();
+  if (s_next == 1) {
+    const double eta = st->eta;
+    for (int k = threadIdx.x; k < n1; k += 256) V.xt[k] = V.x[k] + eta * V.dx[k];
+    __syncthreads();
+    set_trial(st, V, d, sh);
+    if (threadIdx.x == 0) st->phase = 1;
+  }
+}
+
+// Controller, part B (one block, after the support rows were reduced): the
+// gradient at the accepted point, then the relative-type stopping condition
+// (Algorithm 1) and the next action.
+__global__ void __launch_bounds__(256) k_control_b(Buffers B, int d) {
+  DevState* st = B.st;
+  if (st->status != 0 || st->action != ACT_GRAD) return;
+  const DevVecs& V = B.vec;
+  const int n1 = d + 1;
+  __shared__ double sh[32];
+  const int snb = st->svec_nb;
+  for (int j = threadIdx.x; j < d; j += 256) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int k = 0; k < snb; k++) {
+      const double* p = B.svec_part + (int64_t)k * (3 * d + 1);
+      a += p[j];
+      b += p[d + j];
+      c += p[2 * d + j];
+    }
+    V.sv[j] = a;
+    V.sw[j] = b;
+    V.cg_diag[1 + j] = c;   // sum_M t w_j^2 (Jacobi preconditioner)
+  }
+  if (threadIdx.x == 0) {
+    double s1t = 0.0;
+    for (int k = 0; k < snb; k++) s1t += B.svec_part[(int64_t)k * (3 * d + 1) + 3 * d];
+    V.st1[0] = s1t;
+  }
+  __syncthreads();
+  const double sigma = st->sigma, tau = st->tau, tos = tau / sigma;
+  const double su = st->last[P_SU];
+  for (int k = threadIdx.x; k < n1; k += 256) {
+    const double dk = V.xt[k] - V.xk[k];
+    const double sk = (k == 0) ? su : V.sv[k - 1];
+    V.gt[k] = ((k == 0) ? 1.0 : 0.0) - sk + tos * dk;
+  }
+  __syncthreads();
+  if (st->eval_only) {
+    if (threadIdx.x == 0) { st->action = ACT_DONE; st->status = 1; }
+    return;
+  }
+  // accepted point: x <- xt, g <- gt
+  for (int k = threadIdx.x; k < n1; k += 256) {
+    V.x[k] = V.xt[k];
+    V.g[k] = V.gt[k];
+  }
+  if (threadIdx.x == 0) {
+    st->gmag = 1.0 + sigma * st->last[P_ZMAG] + tos * sqrt(st->dx2_t);
+    st->phase = 2;
+  }
+  __syncthreads();
+  if (st->accept_mode == 2) {
+    do_outer(st, V, d, sh);
+    return;
+  }
+  double la = 0.0, g2 = 0.0, dk2 = 0.0;
+  for (int k = threadIdx.x; k < n1; k += 256) {
+    la += (V.ab[k] - V.x[k]) * V.g[k];
+    g2 += V.g[k] * V.g[k];
+    const double t = V.x[k] - V.xk[k];
+    dk2 += t * t;
+  }
+  la = block_sum<256>(la, sh);
+  g2 = block_sum<256>(g2, sh);
+  dk2 = block_sum<256>(dk2, sh);
+  const double lhs = 2.0 * sigma * fabs(la) + sigma * sigma * g2;
+  const double rhs = st->rho * (st->last[P_DUV2] + tau * dk2);
+  const bool stop = (lhs <= rhs) || (sqrt(g2) <= 8.0 * DBL_EPSILON * st->gmag);
+  if (stop) {
+    do_outer(st, V, d, sh);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    st->action = ACT_NEWTON;
+    st->bt = 0;
+  }
+}
+
+cudaError_t launch_tick_control(Buffers& B, int64_t m, int d, cudaStream_t s) {
+  int tpb;
+  const int nb = pass_blocks(m, &tpb);
+  k_control_a<<<1, 256, 0, s>>>(B, d, nb);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_support_rows(B.C_in, B, m, d, s);
+  if (e != cudaSuccess) return e;
+  k_control_b<<<1, 256, 0, s>>>(B, d);
+  B.launches += 2;
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// Dense Newton system (d + 1 <= kMaxDenseN):
+//   H = tau/sigma I + sigma (n_I I + sum_M P_k),
+//   sum_M P_k = 1/2 [[n_M, sum w^T], [sum w, sum(1+t) I - sum t w w^T]].
+// k_syrk: partial tiles of sum_M t_k w_k w_k^T over row groups.
+constexpr int kSyrkGroups = 24;
+
+__global__ void __launch_bounds__(256) k_syrk(Buffers B, int d, int force) {
+  DevState* st = B.st;
+  if (!force && (st->status != 0 || st->action != ACT_NEWTON)) return;
+  const int nt = (d + kSyrkTile - 1) / kSyrkTile;
+  const int ntri = nt * (nt + 1) / 2;
+  const int tri = blockIdx.x, grp = blockIdx.y;
+  if (tri >= ntri) return;
+  // tile (ti >= tj) from the linear lower-triangle index
+  int ti = 0;
+  while ((ti + 1) * (ti + 2) / 2 <= tri) ti++;
+  const int tj = tri - ti * (ti + 1) / 2;
+  const int nS = st->nS;
+  const int rpg = (nS + kSyrkGroups - 1) / kSyrkGroups;
+  const int k0 = grp * rpg, k1 = min(nS, k0 + rpg);
+  __shared__ double sa[kSyrkRows][kSyrkTile + 1];
+  __shared__ double sb[kSyrkRows][kSyrkTile + 1];
+  __shared__ double stw[kSyrkRows];
+  // thread -> 4 outputs: rows (ty*4 .. ty*4+3)? use (r = tid/32 + 8q, c = tid%32)
+  const int cc = threadIdx.x & 31, r0 = threadIdx.x >> 5;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int kb = k0; kb < k1; kb += kSyrkRows) {
+    const int nr = min(kSyrkRows, k1 - kb);
+    for (int e = threadIdx.x; e < kSyrkRows * kSyrkTile; e += 256) {
+      const int rr = e / kSyrkTile, c2 = e % kSyrkTile;
+      double va = 0.0, vb = 0.0;
+      if (rr < nr) {
+        const int k = kb + rr;
+        const int ja = ti * kSyrkTile + c2, jb = tj * kSyrkTile + c2;
+        const bool m = B.S_case[k] == CASE_M;
+        if (m && ja < d) va = B.W[(int64_t)k * d + ja];
+        if (m && jb < d) vb = B.W[(int64_t)k * d + jb];
+      }
+      sa[rr][c2] = va;
+      sb[rr][c2] = vb;
+    }
+    if (threadIdx.x < kSyrkRows) {
+      const int k = kb + threadIdx.x;
+      stw[threadIdx.x] = (threadIdx.x < nr && B.S_case[k] == CASE_M) ? B.S_t[k] : 0.0;
+    }
+    __syncthreads();
+    for (int rr = 0; rr < nr; rr++) {
+      const double t = stw[rr];
+      const double bv = sb[rr][cc] * t;
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[q] = fma(sa[rr][r0 + 8 * q], bv, acc[q]);
+    }
+    __syncthreads();
+  }
+  double* out = B.hpart + ((int64_t)grp * ntri + tri) * (kSyrkTile * kSyrkTile);
+#pragma unroll
+  for (int q = 0; q < 4; q++) out[(r0 + 8 * q) * kSyrkTile + cc] = acc[q];
+}
+
+// Sum the group partials (in group order) into B.H's lower triangle block (rows/cols 1..d).
+__global__ void k_syrk_reduce(Buffers B, int d, int force) {
+  DevState* st = B.st;
+  if (!force && (st->status != 0 || st->action != ACT_NEWTON)) return;
+  const int nt = (d + kSyrkTile - 1) / kSyrkTile;
+  const int ntri = nt * (nt + 1) / 2;
+  const int64_t tot = (int64_t)ntri * kSyrkTile * kSyrkTile;
+  const int n1 = d + 1;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int tri = (int)(e / (kSyrkTile * kSyrkTile));
+    const int loc = (int)(e % (kSyrkTile * kSyrkTile));
+    int ti = 0;
+    while ((ti + 1) * (ti + 2) / 2 <= tri) ti++;
+    const int tj = tri - ti * (ti + 1) / 2;
+    const int j = ti * kSyrkTile + loc / kSyrkTile, l = tj * kSyrkTile + loc % kSyrkTile;
+    if (j >= d || l >= d || l > j) continue;
+    double s = 0.0;
+    for (int g = 0; g < kSyrkGroups; g++)
+      s += B.hpart[((int64_t)g * ntri + tri) * (kSyrkTile * kSyrkTile) + loc];
+    B.H[(int64_t)(1 + j) * n1 + (1 + l)] = s;
+  }
+}
+
+// One block: assemble H (packed lower, smem), Cholesky, solve H dx = -g,
+// then set the first line-search trial x + dx.
+__global__ void __launch_bounds__(256) k_newton_chol(Buffers B, int d) {
+  DevState* st = B.st;
+  if (st->status != 0 || st->action != ACT_NEWTON || !st->need_fp64_solve) return;
+  extern __shared__ double Lp[];   // packed lower: row i at i(i+1)/2
+  __shared__ double sh[32];
+  __shared__ int s_fail;
+  const DevVecs& V = B.vec;
+  const int n = d + 1;
+  const double sigma = st->sigma, tos = st->tau / sigma;
+  const double nI = st->last[P_NI], nM = st->last[P_NM];
+  const double s1t = V.st1[0];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  (void)tos; (void)nI; (void)nM; (void)s1t;
+  for (int i = wid; i < n; i += 8) {
+    const int64_t ri = (int64_t)i * (i + 1) / 2;
+    for (int l = lane; l <= i; l += 32) Lp[ri + l] = B.H[(int64_t)i * n + l];   // assembled H
+  }
+  if (threadIdx.x == 0) s_fail = 0;
+  __syncthreads();
+  // right-looking Cholesky on the packed lower triangle
+  for (int j = 0; j < n; j++) {
+    const int64_t jj = (int64_t)j * (j + 1) / 2 + j;
+    if (threadIdx.x == 0) {
+      const double p = Lp[jj];
+      if (!(p > 0.0)) s_fail = 1;
+      Lp[jj] = sqrt(fmax(p, DBL_MIN));
+    }
+    __syncthreads();
+    if (s_fail) break;
+    const double ljj = Lp[jj];
+    for (int i = j + 1 + threadIdx.x; i < n; i += 256) Lp[(int64_t)i * (i + 1) / 2 + j] /= ljj;
+    __syncthreads();
+    // trailing update: rows i > j, cols j < l <= i (warp per row)
+    for (int i = j + 1 + wid; i < n; i += 8) {
+      const int64_t ri = (int64_t)i * (i + 1) / 2;
+      const double lij = Lp[ri + j];
+      for (int l = j + 1 + lane; l <= i; l += 32)
+        Lp[ri + l] -= lij * Lp[(int64_t)l * (l + 1) / 2 + j];
+    }
+    __syncthreads();
+  }
+  if (s_fail) {
+    // Cholesky broke down: end the inner loop here (outer update at x)
+    if (threadIdx.x == 0) st->chol_fail += 1;
+    do_outer(st, V, d, sh);
+    return;
+  }
+  // forward / backward substitution (single warp; n <= 225)
+  double* y = V.dx;
+  if (threadIdx.x < 32) {
+    for (int i = 0; i < n; i++) {
+      const int64_t ri = (int64_t)i * (i + 1) / 2;
+      double t = 0.0;
+      for (int k = threadIdx.x; k < i; k += 32) t += Lp[ri + k] * y[k];
+      t = warp_sum(t);
+      if (threadIdx.x == 0) y[i] = (-V.g[i] - t) / Lp[ri + i];
+      __syncwarp();
+    }
+    for (int i = n - 1; i >= 0; i--) {
+      double t = 0.0;
+      for (int k = i + 1 + threadIdx.x; k < n; k += 32) t += Lp[(int64_t)k * (k + 1) / 2 + i] * y[k];
+      t = warp_sum(t);
+      if (threadIdx.x == 0) y[i] = (y[i] - t) / Lp[(int64_t)i * (i + 1) / 2 + i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  double gd = 0.0;
+  for (int k = threadIdx.x; k < n; k += 256) {
+    gd += V.g[k] * V.dx[k];
+    V.xt[k] = V.x[k] + V.dx[k];
+  }
+  gd = block_sum<256>(gd, sh);
+  if (threadIdx.x == 0) {
+    st->gdx = gd;
+    st->eta = 1.0;
+    st->phase = 1;
+    st->bt = 0;
+    st->action = ACT_TRIAL;
+  }
+  __syncthreads();
+  set_trial(st, V, d, sh);
+}
+
+// Full FP64 H (both triangles) in B.H from the SYRK block (lower triangle of
+// rows/cols 1..d) and the scalar / vector parts.
+__global__ void k_assemble_h(Buffers B, int d, int force) {
+  DevState* st = B.st;
+  if (!force && (st->status != 0 || st->action != ACT_NEWTON)) return;
+  const DevVecs& V = B.vec;
+  const int n = d + 1;
+  const double sigma = st->sigma, tos = st->tau / sigma;
+  const double nI = st->last[P_NI], nM = st->last[P_NM], s1t = V.st1[0];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), l = (int)(e % n);
+    if (l > i) continue;   // the thread of (i, l) writes both (i, l) and (l, i)
+    double h;
+    if (i == 0) h = tos + sigma * (nI + 0.5 * nM);
+    else if (l == 0) h = sigma * 0.5 * V.sw[i - 1];
+    else {
+      h = -0.5 * sigma * B.H[(int64_t)i * n + l];
+      if (i == l) h += tos + sigma * (nI + 0.5 * s1t);
+    }
+    B.H[(int64_t)i * n + l] = h;
+    B.H[(int64_t)l * n + i] = h;
+  }
+}
+
+// One block: FP32 Gauss-Jordan inverse of H (SPD, no pivoting needed), then
+// dx = -H^{-1} g refined in FP64: r = -g - H dx (FP64), dx += H32^{-1} r.
+// Sets need_fp64_solve when a pivot is not positive or the refinement does
+// not converge; otherwise sets up the first line-search trial.
+__global__ void __launch_bounds__(256) k_newton_gj(Buffers B, int d) {
+  DevState* st = B.st;
+  if (st->status != 0 || st->action != ACT_NEWTON) return;
+  extern __shared__ float A[];    // n x n, row-major
+  __shared__ double sh[32];
+  __shared__ int s_fail;
+  __shared__ float s_prow[kMaxDenseN];
+  __shared__ float s_rf[kMaxDenseN];
+  const DevVecs& V = B.vec;
+  const int n = d + 1;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int e = tid; e < n * n; e += 256) A[e] = (float)B.H[e];
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  for (int k = 0; k < n; k++) {
+    const float p = A[k * n + k];
+    if (!(p > 0.0f) || !isfinite(p)) { if (tid == 0) s_fail = 1; }
+    __syncthreads();
+    if (s_fail) break;
+    const float ip = 1.0f / p;
+    for (int j = tid; j < n; j += 256) {
+      const float v = (j == k) ? ip : A[k * n + j] * ip;
+      s_prow[j] = v;
+    }
+    __syncthreads();
+    for (int j = tid; j < n; j += 256) A[k * n + j] = s_prow[j];
+    // rows i != k: A[i][j] -= A[i][k] * prow[j]; A[i][k] = -A[i][k] * ip
+    for (int i = wid; i < n; i += 8) {
+      if (i == k) continue;
+      const float f = A[i * n + k];
+      __syncwarp();
+      for (int j = lane; j < n; j += 32) {
+        if (j == k) continue;
+        A[i * n + j] = fmaf(-f, s_prow[j], A[i * n + j]);
+      }
+      __syncwarp();
+      if (lane == 0) A[i * n + k] = -f * ip;
+    }
+    __syncthreads();
+  }
+  bool ok = !s_fail;
+  if (ok) {
+    // dx = A (-g), then refinement: r = -g - H dx (FP64), dx += A r (FP32).
+    // Thread i owns component i; A and H are read by columns (H symmetric,
+    // A ~ H^{-1} symmetric up to rounding), which coalesces.
+    double* x = V.dx;
+    for (int i = tid; i < n; i += 256) s_rf[i] = (float)(-V.g[i]);
+    __syncthreads();
+    double rn0 = 0.0;
+    for (int it = 0; it < 5; it++) {
+      double dn = 0.0, xn = 0.0;
+      for (int i = tid; i < n; i += 256) {
+        float t = 0.0f;
+        for (int j = 0; j < n; j++) t = fmaf(A[j * n + i], s_rf[j], t);
+        const double xi = (it == 0 ? 0.0 : x[i]) + (double)t;
+        x[i] = xi;
+        dn += (double)t * (double)t;
+        xn += xi * xi;
+      }
+      dn = block_sum<256>(dn, sh);
+      xn = block_sum<256>(xn, sh);
+      if (dn <= 1e-22 * xn) break;
+      double rn = 0.0;
+      for (int i = tid; i < n; i += 256) {
+        double t = -V.g[i];
+        for (int j = 0; j < n; j++) t = fma(-B.H[(int64_t)j * n + i], x[j], t);
+        s_rf[i] = (float)t;
+        rn += t * t;
+      }
+      rn = block_sum<256>(rn, sh);
+      if (it == 0) rn0 = rn;
+      else if (!(rn <= rn0)) { ok = false; break; }   // refinement diverges
+      if (it == 4) ok = rn <= 1e-16 * rn0;
+    }
+  }
+  if (!ok) {
+    if (tid == 0) st->need_fp64_solve = 1;
+    return;
+  }
+  double gd = 0.0;
+  for (int k = tid; k < n; k += 256) {
+    gd += V.g[k] * V.dx[k];
+    V.xt[k] = V.x[k] + V.dx[k];
+  }
+  gd = block_sum<256>(gd, sh);
+  if (tid == 0) {
+    st->need_fp64_solve = 0;
+    st->gdx = gd;
+    st->eta = 1.0;
+    st->phase = 1;
+    st->bt = 0;
+    st->action = ACT_TRIAL;
+  }
+  __syncthreads();
+  set_trial(st, V, d, sh);
+}
+
+// Register-blocked variant for n = d + 1 <= 112: a 16 x 16 thread grid, thread
+// (ty, tx) holding the 7 x 7 tile of rows ty + 16 a and columns tx + 16 b in
+// registers.  Each Gauss-Jordan step publishes the old pivot row and column
+// through shared memory and updates all 49 entries independently.
+constexpr int kGjTile = 7;
+constexpr int kGjRegN = 16 * kGjTile;
+
+__global__ void __launch_bounds__(256) k_newton_gj_reg(Buffers B, int d) {
+  DevState* st = B.st;
+  if (st->status != 0 || st->action != ACT_NEWTON) return;
+  __shared__ float s_row[kGjRegN], s_col[kGjRegN], s_b[kGjRegN];
+  __shared__ double sh[32];
+  __shared__ double s_x[kGjRegN];
+  const DevVecs& V = B.vec;
+  const int n = d + 1;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float a[kGjTile][kGjTile];
+#pragma unroll
+  for (int i = 0; i < kGjTile; i++)
+#pragma unroll
+    for (int j = 0; j < kGjTile; j++) {
+      const int row = ty + 16 * i, col = tx + 16 * j;
+      a[i][j] = (row < n && col < n) ? f64_to_f32_trunc(B.H[(int64_t)row * n + col]) : 0.0f;
+    }
+  __syncthreads();
+  bool fail = false;
+#pragma unroll
+  for (int kb = 0; kb < kGjTile; kb++) {
+    for (int kk = 0; kk < 16 && !fail; kk++) {
+      const int k = 16 * kb + kk;
+      if (k >= n) break;
+      if (ty == kk) {
+#pragma unroll
+        for (int j = 0; j < kGjTile; j++) s_row[tx + 16 * j] = a[kb][j];
+      }
+      if (tx == kk) {
+#pragma unroll
+        for (int i = 0; i < kGjTile; i++) s_col[ty + 16 * i] = a[i][kb];
+      }
+      __syncthreads();
+      const float p = s_row[k];
+      if (!(p > 0.0f) || !isfinite(p)) { fail = true; break; }
+      const float ip = 1.0f / p;
+      float rc[kGjTile], cr[kGjTile];
+#pragma unroll
+      for (int j = 0; j < kGjTile; j++) rc[j] = s_row[tx + 16 * j] * ip;
+#pragma unroll
+      for (int i = 0; i < kGjTile; i++) cr[i] = s_col[ty + 16 * i];
+#pragma unroll
+      for (int i = 0; i < kGjTile; i++)
+#pragma unroll
+        for (int j = 0; j < kGjTile; j++) a[i][j] = fmaf(-cr[i], rc[j], a[i][j]);
+      if (ty == kk) {   // pivot row: A[k][j] / p, and 1/p on the diagonal
+#pragma unroll
+        for (int j = 0; j < kGjTile; j++) a[kb][j] = (tx + 16 * j == k) ? ip : rc[j];
+      }
+      if (tx == kk) {   // pivot column: -A[i][k] / p off the diagonal
+#pragma unroll
+        for (int i = 0; i < kGjTile; i++)
+          if (ty + 16 * i != k) a[i][kb] = -cr[i] * ip;
+      }
+      __syncthreads();
+    }
+  }
+  bool ok = !fail;
+  if (ok) {
+    // dx = A (-g); refinement r = -g - H dx (FP64), dx += A r
+    for (int i = tid; i < kGjRegN; i += 256) {
+      s_b[i] = (i < n) ? (float)(-V.g[i]) : 0.0f;
+      s_x[i] = 0.0;
+    }
+    __syncthreads();
+    double rn0 = 0.0;
+    for (int it = 0; it < 4; it++) {
+      // y = A s_b : partial rows over this thread's columns, reduced over tx
+      double dn = 0.0, xn = 0.0;
+#pragma unroll
+      for (int i = 0; i < kGjTile; i++) {
+        float t = 0.0f;
+#pragma unroll
+        for (int j = 0; j < kGjTile; j++) t = fmaf(a[i][j], s_b[tx + 16 * j], t);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(MEB_FULLMASK, t, o);
+        const int row = ty + 16 * i;
+        if (tx == 0 && row < n) {
+          const double xi = s_x[row] + (double)t;
+          s_x[row] = xi;
+          dn += (double)t * (double)t;
+          xn += xi * xi;
+        }
+      }
+      dn = block_sum<256>(dn, sh);
+      xn = block_sum<256>(xn, sh);
+      if (dn <= 1e-22 * xn) break;
+      // r = -g - H x (FP64), rows reduced over tx
+      double rn = 0.0;
+#pragma unroll
+      for (int i = 0; i < kGjTile; i++) {
+        const int row = ty + 16 * i;
+        double t = 0.0;
+        if (row < n) {
+#pragma unroll
+          for (int j = 0; j < kGjTile; j++) {
+            const int col = tx + 16 * j;
+            if (col < n) t = fma(B.H[(int64_t)row * n + col], s_x[col], t);
+          }
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(MEB_FULLMASK, t, o);
+        if (tx == 0 && row < n) {
+          const double r = -V.g[row] - t;
+          s_b[row] = (float)r;
+          rn += r * r;
+        }
+      }
+      rn = block_sum<256>(rn, sh);
+      if (it == 0) rn0 = rn;
+      else if (!(rn <= rn0)) { ok = false; break; }
+      if (it == 3) ok = rn <= 1e-12 * rn0;
+    }
+  }
+  if (!ok) {
+    if (tid == 0) st->need_fp64_solve = 1;
+    return;
+  }
+  double gd = 0.0;
+  for (int k = tid; k < n; k += 256) {
+    V.dx[k] = s_x[k];
+    gd += V.g[k] * s_x[k];
+    V.xt[k] = V.x[k] + s_x[k];
+  }
+  gd = block_sum<256>(gd, sh);
+  if (tid == 0) {
+    st->need_fp64_solve = 0;
+    st->gdx = gd;
+    st->eta = 1.0;
+    st->phase = 1;
+    st->bt = 0;
+    st->action = ACT_TRIAL;
+  }
+  __syncthreads();
+  set_trial(st, V, d, sh);
+}
+
+cudaError_t launch_newton_dense(Buffers& B, int d, cudaStream_t s) {
+  const int nt = (d + kSyrkTile - 1) / kSyrkTile;
+  const int ntri = nt * (nt + 1) / 2;
+  k_syrk<<<dim3(ntri, kSyrkGroups), 256, 0, s>>>(B, d, 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_syrk_reduce<<<64, 256, 0, s>>>(B, d, 0);
+  const int n = d + 1;
+  k_assemble_h<<<(n * n + 255) / 256, 256, 0, s>>>(B, d, 0);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (n <= kGjRegN) {
+    k_newton_gj_reg<<<1, 256, 0, s>>>(B, d);
+  } else {
+    const size_t shg = sizeof(float) * (size_t)n * n;
+    if (shg > 48 * 1024) {
+      e = cudaFuncSetAttribute(k_newton_gj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shg);
+      if (e != cudaSuccess) return e;
+    }
+    k_newton_gj<<<1, 256, shg, s>>>(B, d);
+  }
+  // FP64 Cholesky only when the FP32 inverse could not be refined
+  const size_t sh = sizeof(double) * (size_t)n * (n + 1) / 2;
+  if (sh > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_newton_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (e != cudaSuccess) return e;
+  }
+  k_newton_chol<<<1, 256, sh, s>>>(B, d);
+  B.launches += 5;
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// Matrix-free Newton system (Sec. 4.1): CG with the Jacobi preconditioner,
+//   Hq = tau/sigma q + sigma (n_I q + sum_M P_k q),
+//   P_k q = 1/2 (q0 + w.q1 ; q0 w + (1+t) q1 - t w (w.q1)).
+// k_hvp_dot: wq_k = w_k . q1 (warp per row); k_hvp_acc: -1/2 sum_k t_k wq_k w_k
+// and 1/2 sum_k wq_k; hvp_finish adds the terms in q0 sum w and sum(1+t) q1.
+__global__ void __launch_bounds__(256) k_hvp_dot(Buffers B, int d, const double* __restrict__ q,
+                                                  double* __restrict__ wq, int force) {
+  DevState* st = B.st;
+  if (!force && (st->status != 0 || st->action != ACT_NEWTON || st->cg_done)) return;
+  const int nS = st->nS;
+  const int lane = threadIdx.x & 31;
+  for (int k = (blockIdx.x * 256 + threadIdx.x) >> 5; k < nS; k += (gridDim.x * 256) >> 5) {
+    double t = 0.0;
+    if (B.S_case[k] == CASE_M) {
+      const double* w = B.W + (int64_t)k * d;
+      for (int j = lane; j < d; j += 32) t = fma(w[j], q[1 + j], t);
+      t = warp_sum(t);
+    }
+    if (lane == 0) wq[k] = t;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_hvp_acc(Buffers B, int d, const double* __restrict__ q,
+                                                  const double* __restrict__ wq,
+                                                  double* __restrict__ part, int force) {
+  DevState* st = B.st;
+  if (!force && (st->status != 0 || st->action != ACT_NEWTON || st->cg_done)) return;
+  const int nS = st->nS;
+  const int rpb = (nS + gridDim.x - 1) / gridDim.x;
+  const int k0 = blockIdx.x * rpb, k1 = min(nS, k0 + rpb);
+  double* out = part + (int64_t)blockIdx.x * (d + 1);
+  double s0 = 0.0;
+  for (int j0 = 0; j0 < d; j0 += 256) {
+    const int j = j0 + threadIdx.x;
+    double acc = 0.0;
+    for (int k = k0; k < k1; k++) {
+      if (B.S_case[k] != CASE_M) continue;
+      const double coef = -0.5 * B.S_t[k] * wq[k];   // the q0 w part is 1/2 q0 sum w
+      if (j < d) acc = fma(coef, B.W[(int64_t)k * d + j], acc);
+      if (j0 == 0 && threadIdx.x == 0) s0 += 0.5 * wq[k];
+    }
+    if (j < d) out[1 + j] = acc;
+  }
+  if (threadIdx.x == 0) out[0] = s0;
+}
+
+// y = tau/sigma q + sigma (n_I q + 1/2 [n_M q0 + S0 ; q0 sum w + sum(1+t) q1] + acc)
+__device__ void hvp_finish(DevState* st, const DevVecs& V, int d, const double* q,
+                           const double* part, int nblk, double* y) {
+  const int n1 = d + 1;
+  const double sigma = st->sigma, tos = st->tau / sigma;
+  const double nI = st->last[P_NI], nM = st->last[P_NM], s1t = V.st1[0];
+  for (int k = threadIdx.x; k < n1; k += blockDim.x) {
+    double a = 0.0;
+    for (int b = 0; b < nblk; b++) a += part[(int64_t)b * n1 + k];
+    double pk;
+    if (k == 0) pk = nI * q[0] + 0.5 * nM * q[0] + a;
+    else pk = nI * q[k] + 0.5 * q[0] * V.sw[k - 1] + 0.5 * s1t * q[k] + a;
+    y[k] = tos * q[k] + sigma * pk;
+  }
+}
+
+constexpr int kHvpBlocks = 152;
+
+__global__ void __launch_bounds__(256) k_cg_setup(Buffers B, int d) {
+  DevState* st = B.st;
+  if (st->status != 0 || st->action != ACT_NEWTON) return;
+  __shared__ double sh[32];
+  const DevVecs& V = B.vec;
+  const int n1 = d + 1;
+  const double sigma = st->sigma, tos = st->tau / sigma;
+  const double nI = st->last[P_NI], nM = st->last[P_NM], s1t = V.st1[0];
+  double rz = 0.0, bn = 0.0;
+  for (int k = threadIdx.x; k < n1; k += 256) {
+    // diag(H): k = 0: tos + sigma (nI + nM/2); k > 0: tos + sigma (nI + (s1t - sum t w_k^2)/2)
+    const double dg = (k == 0) ? tos + sigma * (nI + 0.5 * nM)
+                               : tos + sigma * (nI + 0.5 * (s1t - V.cg_diag[k]));
+    V.cg_diag[k] = dg;   // overwrite in place (k > 0 held sum t w^2)
+    const double r = -V.g[k];
+    V.cg_r[k] = r;
+    V.dx[k] = 0.0;
+    const double z = r / dg;
+    V.cg_z[k] = z;
+    V.cg_p[k] = z;
+    rz += r * z;
+    bn += r * r;
+  }
+  rz = block_sum<256>(rz, sh);
+  bn = block_sum<256>(bn, sh);
+  if (threadIdx.x == 0) {
+    st->cg_rz = rz;
+    st->cg_bn = sqrt(bn);
+    double gn = sqrt(bn);
+    st->cg_rtol = gn < 0.01 ? sqrt(gn) : 0.1;
+    st->cg_it = 0;
+    st->cg_done = (bn == 0.0);
+  }
+}
+
+// One CG iteration after the HVP partials of p are in place.
+__global__ void __launch_bounds__(256) k_cg_update(Buffers B, int d, int nblk) {
+  DevState* st = B.st;
+  if (st->status != 0 || st->action != ACT_NEWTON || st->cg_done) return;
+  __shared__ double sh[32];
+  const DevVecs& V = B.vec;
+  const int n1 = d + 1;
+  hvp_finish(st, V, d, V.cg_p, B.hpart, nblk, V.cg_ap);
+  __syncthreads();
+  double pap = 0.0;
+  for (int k = threadIdx.x; k < n1; k += 256) pap += V.cg_p[k] * V.cg_ap[k];
+  pap = block_sum<256>(pap, sh);
+  const double alpha = st->cg_rz / pap;
+  double rr = 0.0, rz1 = 0.0;
+  for (int k = threadIdx.x; k < n1; k += 256) {
+    V.dx[k] += alpha * V.cg_p[k];
+    const double r = V.cg_r[k] - alpha * V.cg_ap[k];
+    V.cg_r[k] = r;
+    const double z = r / V.cg_diag[k];
+    V.cg_z[k] = z;
+    rr += r * r;
+    rz1 += r * z;
+  }
+  rr = block_sum<256>(rr, sh);
+  rz1 = block_sum<256>(rz1, sh);
+  const double beta = rz1 / st->cg_rz;
+  for (int k = threadIdx.x; k < n1; k += 256) V.cg_p[k] = V.cg_z[k] + beta * V.cg_p[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->cg_rz = rz1;
+    st->cg_it += 1;
+    st->tot_cg += 1;
+    if (sqrt(rr) <= st->cg_rtol * st->cg_bn || st->cg_it >= st->max_cg) st->cg_done = 1;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_cg_finish(Buffers B, int d) {
+  DevState* st = B.st;
+  if (st->status != 0 || st->action != ACT_NEWTON) return;
+  __shared__ double sh[32];
+  const DevVecs& V = B.vec;
+  const int n1 = d + 1;
+  double gd = 0.0;
+  for (int k = threadIdx.x; k < n1; k += 256) {
+    gd += V.g[k] * V.dx[k];
+    V.xt[k] = V.x[k] + V.dx[k];
+  }
+  gd = block_sum<256>(gd, sh);
+  if (threadIdx.x == 0) {
+    st->gdx = gd;
+    st->eta = 1.0;
+    st->phase = 1;
+    st->bt = 0;
+    st->action = ACT_TRIAL;
+  }
+  __syncthreads();
+  set_trial(st, V, d, sh);
+}
+
+cudaError_t launch_cg_setup(Buffers& B, int d, cudaStream_t s) {
+  k_cg_setup<<<1, 256, 0, s>>>(B, d);
+  B.launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_iter(Buffers& B, int d, cudaStream_t s) {
+  k_hvp_dot<<<kHvpBlocks * 4, 256, 0, s>>>(B, d, B.vec.cg_p, B.wq, 0);
+  k_hvp_acc<<<kHvpBlocks, 256, 0, s>>>(B, d, B.vec.cg_p, B.wq, B.hpart, 0);
+  k_cg_update<<<1, 256, 0, s>>>(B, d, kHvpBlocks);
+  B.launches += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_finish(Buffers& B, int d, cudaStream_t s) {
+  k_cg_finish<<<1, 256, 0, s>>>(B, d);
+  B.launches += 1;
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// Multiplier update (Algorithm 1): (u, v)^{k+1} = sigma_k Pi(z_k) on the
+// support of the accepted point, written to the other buffer; then the
+// ball->slot map and the buffer parity.
+__global__ void __launch_bounds__(256) k_mult_rows(const double* __restrict__ C, Buffers B,
+                                                   int d) {
+  DevState* st = B.st;
+  if (st->status != 0 || st->action != ACT_OUTER) return;
+  const int nS = st->nS;
+  const int cur = st->sup_cur, nxt = cur ^ 1, nsup = st->nsup;
+  const int* sidx = B.sup_idx[cur];
+  const double* sv = B.sup_v[cur];
+  double* nv = B.sup_v[nxt];
+  const double sigma = st->sigma_prev;   // sigma_k of the finished outer step
+  const double inv_sigma = 1.0 / sigma;
+  const double inv_s = st->inv_s;
+  const double* ct = B.vec.ct;        // == s * x (the accepted point)
+  const int lane = threadIdx.x & 31;
+  for (int k = (blockIdx.x * 256 + threadIdx.x) >> 5; k < nS; k += (gridDim.x * 256) >> 5) {
+    const int idx = B.S_idx[k];
+    const int sl0 = B.slot[idx];
+    const int sl = ((unsigned)sl0 < (unsigned)nsup && sidx[sl0] == idx) ? sl0 : -1;
+    const double a = B.S_a[k], n = B.S_n[k];
+    const double f = (B.S_case[k] == CASE_I) ? 1.0 : 0.5 * (a + n) / n;
+    for (int j = lane; j < d; j += 32) {
+      double b = (C[(int64_t)idx * d + j] - ct[j]) * inv_s;
+      if (sl >= 0) b = fma(sv[(int64_t)sl * d + j], inv_sigma, b);
+      nv[(int64_t)k * d + j] = sigma * f * b;
+    }
+    if (lane == 0) {
+      B.sup_idx[nxt][k] = idx;
+      B.sup_u[nxt][k] = B.S_u[k];
+    }
+  }
+}
+
+__global__ void k_mult_slots(Buffers B) {
+  DevState* st = B.st;
+  if (st->status != 0 || st->action != ACT_OUTER) return;
+  const int nS = st->nS;
+  const int nxt = st->sup_cur ^ 1;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nS; k += gridDim.x * blockDim.x)
+    B.slot[B.sup_idx[nxt][k]] = k;
+}
+
+__global__ void k_mult_flip(Buffers B) {
+  DevState* st = B.st;
+  if (st->status != 0 || st->action != ACT_OUTER) return;
+  st->sup_cur ^= 1;
+  st->nsup = st->nS;
+  st->action = ACT_NONE;
+}
+
+cudaError_t launch_mult_update(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s) {
+  (void)m;
+  k_mult_rows<<<304, 256, 0, s>>>(C, B, d);
+  k_mult_slots<<<152, 256, 0, s>>>(B);
+  k_mult_flip<<<1, 1, 0, s>>>(B);
+  B.launches += 3;
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// Solve initialisation (state fields set by the host beforehand): x = xt =
+// xk = ab = (r0, c0)/s, trial shadow.
+__global__ void k_state_init(Buffers B, int d) {
+  __shared__ double sh[32];
+  DevState* st = B.st;
+  const DevVecs& V = B.vec;
+  const double inv_s = st->inv_s;
+  for (int k = threadIdx.x; k <= d; k += blockDim.x) {
+    const double v = (k == 0) ? st->rt_abs * inv_s : V.c0[k - 1] * inv_s;
+    V.x[k] = v; V.xt[k] = v; V.xk[k] = v; V.ab[k] = v;
+    V.g[k] = 0.0; V.dx[k] = 0.0;
+  }
+  __syncthreads();
+  set_trial(st, V, d, sh);
+}
+
+cudaError_t launch_state_init(Buffers& B, int d, cudaStream_t s) {
+  k_state_init<<<1, 256, 0, s>>>(B, d);
+  B.launches += 1;
+  return cudaGetLastError();
+}
+
+// Evaluation entry: state for one pass at x with prox centre xbar, s = 1.
+__global__ void k_eval_prepare(Buffers B, const double* __restrict__ x,
+                               const double* __restrict__ xbar, int d) {
+  __shared__ double sh[32];
+  DevState* st = B.st;
+  const DevVecs& V = B.vec;
+  for (int k = threadIdx.x; k <= d; k += blockDim.x) {
+    V.x[k] = x[k]; V.xt[k] = x[k]; V.xk[k] = xbar[k]; V.ab[k] = x[k];
+  }
+  __syncthreads();
+  set_trial(st, V, d, sh);
+}
+
+cudaError_t launch_eval_prepare(Buffers& B, const double* x, const double* xbar, int d,
+                                cudaStream_t s) {
+  k_eval_prepare<<<1, 256, 0, s>>>(B, x, xbar, d);
+  return cudaGetLastError();
+}
+
+// Dense outputs of the evaluation: U+ (m), V+ (m x d) from the support list.
+__global__ void k_eval_scatter(Buffers B, int d, double* __restrict__ Up,
+                               double* __restrict__ Vp) {
+  DevState* st = B.st;
+  const int nS = st->nS;
+  const double sigma = st->sigma;
+  const int lane = threadIdx.x & 31;
+  for (int k = (blockIdx.x * 256 + threadIdx.x) >> 5; k < nS; k += (gridDim.x * 256) >> 5) {
+    const int64_t i = B.S_idx[k];
+    const bool isI = B.S_case[k] == CASE_I;
+    const double coef = isI ? sigma : B.S_u[k];   // v+ = sigma b (I) or u+ w (M)
+    for (int j = lane; j < d; j += 32) Vp[i * d + j] = coef * B.W[(int64_t)k * d + j];
+    if (lane == 0) Up[i] = B.S_u[k];
+  }
+}
+
+__global__ void k_eval_hq(Buffers B, int d, const double* __restrict__ q, double* __restrict__ y) {
+  hvp_finish(B.st, B.vec, d, q, B.hpart, kHvpBlocks, y);
+}
+
+cudaError_t launch_eval_outputs(const double* C, Buffers& B, int64_t m, int d, const double* q,
+                                double* Uplus, double* Vplus, double* Hq, double* H,
+                                cudaStream_t s) {
+  (void)C;
+  if (Uplus) cudaMemsetAsync(Uplus, 0, sizeof(double) * (size_t)m, s);
+  if (Vplus) cudaMemsetAsync(Vplus, 0, sizeof(double) * (size_t)m * d, s);
+  if (Uplus && Vplus) k_eval_scatter<<<304, 256, 0, s>>>(B, d, Uplus, Vplus);
+  if (Hq) {
+    k_hvp_dot<<<kHvpBlocks * 4, 256, 0, s>>>(B, d, q, B.wq, 1);
+    k_hvp_acc<<<kHvpBlocks, 256, 0, s>>>(B, d, q, B.wq, B.hpart, 1);
+    k_eval_hq<<<1, 256, 0, s>>>(B, d, q, Hq);
+  }
+  if (H) {
+    const int nt = (d + kSyrkTile - 1) / kSyrkTile;
+    const int ntri = nt * (nt + 1) / 2;
+    k_syrk<<<dim3(ntri, kSyrkGroups), 256, 0, s>>>(B, d, 1);
+    k_syrk_reduce<<<64, 256, 0, s>>>(B, d, 1);
+    const int64_t n2 = (int64_t)(d + 1) * (d + 1);
+    k_assemble_h<<<(int)imin64(1024, (n2 + 255) / 256), 256, 0, s>>>(B, d, 1);
+    cudaMemcpyAsync(H, B.H, sizeof(double) * (size_t)n2, cudaMemcpyDeviceToDevice, s);
+  }
+  return cudaGetLastError();
+}
+
+// Final centre and ALM radius (unscaled) from the accepted point.
+__global__ void k_final_point(Buffers B, int d, double* __restrict__ c_out,
+                              double* __restrict__ r_alm) {
+  DevState* st = B.st;
+  const double s = st->s;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) c_out[j] = B.vec.x[1 + j] * s;
+  if (threadIdx.x == 0) *r_alm = B.vec.x[0] * s;
+}
+
+cudaError_t launch_final_point(Buffers& B, int d, double* c_out, double* r_alm, cudaStream_t s) {
+  k_final_point<<<1, 256, 0, s>>>(B, d, c_out, r_alm);
+  B.launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace meb
