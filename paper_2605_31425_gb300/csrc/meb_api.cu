@@ -31,10 +31,28 @@ struct meb_ctx {
   double* d_scal = nullptr;     // device scalars
   int64_t* d_i64 = nullptr;     // device int64 scalars
   int profiling = 0;            // time every pass launch with CUDA events
+  // device-resident solve loop: a CUDA graph whose while-node runs controller
+  // ticks until the controller stops; rebuilt when the problem or buffers change
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t gm = 0;
+  int gd = 0;
+  int gmode = -1;
+  int gprof = -1;
+  cudaEvent_t gev[2 * 8] = {};
+  // tick loop: 0 = graph of kUnrollTicks ticks relaunched until the controller
+  // stops (default), 1 = host-driven ticks, 2 = graph with a while-node
+  int loop_mode = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   meb_stats stats{};
+  int prof_screens = 0;
   char err[512] = {0};
 };
+
+// kernels launched per controller tick of the device-resident loop
+static const int64_t kTickLaunches = 3 + 4 + 5 + 3;
+static const int kUnrollTicks = 8;
 
 enum { POOL_C, POOL_R, POOL_U, POOL_V, POOL_X, POOL_XB, POOL_Q, POOL_UP, POOL_VP, POOL_HQ,
        POOL_H, POOL_G, POOL_COUT, POOL_ACT, POOL_N };
@@ -110,7 +128,7 @@ static int ensure_buffers(meb_ctx* ctx, int64_t m, int d) {
     CK(dalloc(&B.sup_v[k], (size_t)md));
   }
   int tpb;
-  const int64_t npb = pass_blocks(m, &tpb);
+  const int64_t npb = pass_blocks(m, d, &tpb);
   const int64_t ncand = npb * tpb * 256;
   CK(dalloc(&B.part_flag, (size_t)nblk));
   CK(dalloc(&B.part, (size_t)nblk * P_COUNT));
@@ -236,6 +254,11 @@ int meb_create(meb_ctx** out, int device, void* cuda_stream) {
     e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
     ctx->own_stream = (e == cudaSuccess);
   }
+  {
+    const char* lm = getenv("MEB_TICK_LOOP");
+    if (lm && !strcmp(lm, "host")) ctx->loop_mode = 1;
+    if (lm && !strcmp(lm, "while")) ctx->loop_mode = 2;
+  }
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_st, sizeof(DevState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_scal, 64 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_flags, 16 * sizeof(int));
@@ -264,6 +287,10 @@ void meb_destroy(meb_ctx* ctx) {
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   for (int k = 0; k < 2; k++)
     if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  for (int k = 0; k < 16; k++)
+    if (ctx->gev[k]) cudaEventDestroy(ctx->gev[k]);
   delete ctx;
 }
 
@@ -334,6 +361,67 @@ static void host_state_defaults(DevState& S, int64_t m, int d, const meb_params&
 static int read_state(meb_ctx* ctx) {
   CK(cudaMemcpyAsync(ctx->h_st, ctx->B.st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  return MEB_OK;
+}
+
+// Build (or reuse) the graph: while (status == 0) { pass; controller; Newton
+// (dense); multiplier update; loop condition }.  Every kernel of the tick is
+// gated on the controller's action, so the tick is a fixed sequence.
+static int solve_graph(meb_ctx* ctx, const double* C, const double* R, int64_t m, int d) {
+  Buffers& B = ctx->B;
+  const int mode = ctx->loop_mode;
+  const int prof = ctx->profiling;
+  if (ctx->gexec && ctx->gkey[0] == C && ctx->gkey[1] == R && ctx->gkey[2] == B.st &&
+      ctx->gm == m && ctx->gd == d && ctx->gmode == mode && ctx->gprof == prof)
+    return MEB_OK;
+  if (prof && !ctx->gev[0])
+    for (int k = 0; k < 16; k++) CK(cudaEventCreate(&ctx->gev[k]));
+  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+  if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaSuccess;
+  if (mode == 2) {
+    CK(cudaGraphCreate(&ctx->graph, 0));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, ctx->graph, 1, cudaGraphCondAssignDefault));
+    // cudaGraphNodeParams holds a union without a default constructor: zeroed storage
+    alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+    memset(npbuf, 0, sizeof(npbuf));
+    cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(npbuf);
+    np->type = cudaGraphNodeTypeConditional;
+    np->conditional.handle = h;
+    np->conditional.type = cudaGraphCondTypeWhile;
+    np->conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, ctx->graph, nullptr, nullptr, 0, np));
+    cudaGraph_t body = np->conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    e = launch_pass(C, R, B, m, d, s);
+    if (e == cudaSuccess) e = launch_tick_control(B, m, d, s);
+    if (e == cudaSuccess) e = launch_newton_dense(B, d, s);
+    if (e == cudaSuccess) e = launch_mult_update(C, B, m, d, s);
+    if (e == cudaSuccess) e = launch_loop_cond(B, h, s);
+    cudaGraph_t got = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &got);
+    if (e != cudaSuccess) return fail(ctx, MEB_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    CK(e2);
+  } else {
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    for (int t = 0; t < kUnrollTicks && e == cudaSuccess; t++) {
+      // profiling: CUDA events around every k_screen of the batch (event nodes)
+      e = prof ? launch_pass(C, R, B, m, d, s, ctx->gev[2 * t], ctx->gev[2 * t + 1], t)
+               : launch_pass(C, R, B, m, d, s);
+      if (e == cudaSuccess) e = launch_tick_control(B, m, d, s);
+      if (e == cudaSuccess) e = launch_newton_dense(B, d, s);
+      if (e == cudaSuccess) e = launch_mult_update(C, B, m, d, s);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(s, &ctx->graph);
+    if (e != cudaSuccess) return fail(ctx, MEB_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    CK(e2);
+  }
+  CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
+  ctx->gkey[0] = C; ctx->gkey[1] = R; ctx->gkey[2] = B.st;
+  ctx->gm = m; ctx->gd = d; ctx->gmode = mode; ctx->gprof = prof;
   return MEB_OK;
 }
 
@@ -413,42 +501,83 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   CK(cudaMemcpyAsync(B.st, ctx->h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
   CK(launch_state_init(B, d, s));
   const bool dense = ctx->h_st->dense;
+  ctx->prof_screens = 0;
 
   const int64_t max_ticks =
       (int64_t)P.max_outer * (P.max_ssn + 2) * (P.max_backtrack + 2) + 16;
-  int64_t ticks = 0;
-  for (;;) {
-    if (ctx->profiling) CK(cudaEventRecord(ctx->ev[0], s));
-    CK(launch_pass(C, R, B, m, d, s));
-    if (ctx->profiling) CK(cudaEventRecord(ctx->ev[1], s));
-    CK(launch_tick_control(B, m, d, s));
-    rc = read_state(ctx);
+  if (dense && ctx->loop_mode != 1 && !(ctx->profiling && ctx->loop_mode == 2)) {
+    // device-resident ticks: graph launches, one status read per kUnrollTicks ticks
+    rc = solve_graph(ctx, C, R, m, d);
     if (rc) return rc;
-    if (ctx->profiling) {
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
-      ctx->stats.pass_ms += ms;
-      ctx->stats.pass_launches += 1;
-      ctx->stats.pass_balls += m;
-      ctx->stats.pass_fp64_rows += (int64_t)ctx->h_st->last[P_N64];
-    }
-    if (ctx->h_st->status != 0) break;
-    if (ctx->h_st->action == ACT_NEWTON) {
-      if (dense) {
-        CK(launch_newton_dense(B, d, s));
-      } else {
-        CK(launch_cg_setup(B, d, s));
-        for (int round = 0; round <= P.max_cg / 4 + 1; round++) {
-          for (int k = 0; k < 4; k++) CK(launch_cg_iter(B, d, s));
-          rc = read_state(ctx);
-          if (rc) return rc;
-          if (ctx->h_st->cg_done || ctx->h_st->status != 0 || ctx->h_st->action != ACT_NEWTON) break;
+    const int64_t before = B.launches;
+    if (ctx->loop_mode == 2) {
+      ctx->h_st->max_ticks = max_ticks < 20000 ? max_ticks : 20000;
+      CK(cudaMemcpyAsync(&B.st->max_ticks, &ctx->h_st->max_ticks, sizeof(int64_t),
+                         cudaMemcpyHostToDevice, s));
+      CK(cudaGraphLaunch(ctx->gexec, s));
+      rc = read_state(ctx);
+      if (rc) return rc;
+      B.launches = before + ctx->h_st->ticks * (kTickLaunches + 1);
+      if (ctx->h_st->status == 3) return fail(ctx, MEB_ECUDA, "controller did not terminate");
+    } else {
+      int64_t ticks = 0;
+      for (;;) {
+        if (ctx->profiling)
+          CK(cudaMemsetAsync(B.st->screen_log, 0, sizeof(B.st->screen_log), s));
+        CK(cudaGraphLaunch(ctx->gexec, s));
+        ticks += kUnrollTicks;
+        rc = read_state(ctx);
+        if (rc) return rc;
+        if (ctx->profiling) {
+          for (int t = 0; t < kUnrollTicks; t++) {
+            if (!ctx->h_st->screen_log[t]) continue;
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ctx->gev[2 * t], ctx->gev[2 * t + 1]));
+            ctx->stats.pass_ms += ms;
+            ctx->stats.pass_launches += 1;
+            ctx->stats.pass_balls += m;
+          }
         }
-        CK(launch_cg_finish(B, d, s));
+        if (ctx->h_st->status != 0) break;
+        if (ticks > max_ticks) return fail(ctx, MEB_ECUDA, "controller did not terminate");
       }
+      B.launches = before + ticks * kTickLaunches;
     }
-    CK(launch_mult_update(C, B, m, d, s));
-    if (++ticks > max_ticks) return fail(ctx, MEB_ECUDA, "controller did not terminate");
+  } else {
+    int64_t ticks = 0;
+    for (;;) {
+      CK(launch_pass(C, R, B, m, d, s, ctx->profiling ? ctx->ev[0] : nullptr,
+                     ctx->profiling ? ctx->ev[1] : nullptr));
+      CK(launch_tick_control(B, m, d, s));
+      rc = read_state(ctx);
+      if (rc) return rc;
+      if (ctx->profiling && ctx->h_st->screens > ctx->prof_screens) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+        ctx->stats.pass_ms += ms;
+        ctx->stats.pass_launches += 1;
+        ctx->stats.pass_balls += m;
+        ctx->stats.pass_fp64_rows += (int64_t)ctx->h_st->last[P_N64];
+      }
+      ctx->prof_screens = ctx->h_st->screens;
+      if (ctx->h_st->status != 0) break;
+      if (ctx->h_st->action == ACT_NEWTON) {
+        if (dense) {
+          CK(launch_newton_dense(B, d, s));
+        } else {
+          CK(launch_cg_setup(B, d, s));
+          for (int round = 0; round <= P.max_cg / 4 + 1; round++) {
+            for (int k = 0; k < 4; k++) CK(launch_cg_iter(B, d, s));
+            rc = read_state(ctx);
+            if (rc) return rc;
+            if (ctx->h_st->cg_done || ctx->h_st->status != 0 || ctx->h_st->action != ACT_NEWTON) break;
+          }
+          CK(launch_cg_finish(B, d, s));
+        }
+      }
+      CK(launch_mult_update(C, B, m, d, s));
+      if (++ticks > max_ticks) return fail(ctx, MEB_ECUDA, "controller did not terminate");
+    }
   }
   const DevState S = *ctx->h_st;
 

@@ -74,6 +74,10 @@ struct DevState {
   int need_fp64_solve;         // FP32 inverse + refinement failed: FP64 Cholesky
   int fp64_solves;             // count of FP64 Cholesky fallbacks
   int early_rejects;           // trials rejected by the certified lower bound
+  int reuse_lists;             // next pass: same point, new multipliers (skip the screen)
+  int64_t ticks, max_ticks;    // controller ticks of the device-resident loop and their cap
+  int screen_log[8];           // profiling: tick t of a graph batch ran a full screen
+  int screens;                 // full FP32 screens run
   double dx2_t;                // ||xt - xk||^2 of the last trial
   double kkt[5], kkt_max;
   double last[P_COUNT];        // reduced partials of the last pass
@@ -157,11 +161,12 @@ struct Buffers {
 };
 
 // ---- launch wrappers: streaming kernels (meb_pass.cu) ----
-int pass_blocks(int64_t m, int* tiles_per_block);
+int pass_blocks(int64_t m, int d, int* tiles_per_block);
 cudaError_t launch_shadow(const double* C, const double* R, int64_t m, int d, Buffers& B,
                           double* o, double* c0, int* bad, cudaStream_t s);
 cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m, int d,
-                        cudaStream_t s);
+                        cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
+                        int log_slot = -1);
 cudaError_t launch_support_rows(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s);
 cudaError_t launch_feas_cert(const double* C, const double* R, int64_t m, int d, const double* c,
                              double r, double eps, int mode, int want_max, Buffers& B,
@@ -183,5 +188,6 @@ cudaError_t launch_eval_outputs(const double* C, Buffers& B, int64_t m, int d, c
 cudaError_t launch_eval_prepare(Buffers& B, const double* x, const double* xbar, int d,
                                 cudaStream_t s);
 cudaError_t launch_final_point(Buffers& B, int d, double* c_out, double* r_alm, cudaStream_t s);
+cudaError_t launch_loop_cond(Buffers& B, cudaGraphConditionalHandle h, cudaStream_t s);
 
 }  // namespace meb

@@ -128,6 +128,7 @@ struct PassArgs {
   const double* R;
   int64_t m, m_pad;
   int d, d4, tiles_per_block;
+  int log_slot;
   const float4* X32;
   const float* R32;
   const int* slot;
@@ -152,7 +153,12 @@ struct PassArgs {
 __global__ void __launch_bounds__(kPassThreads) k_screen(PassArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DevState* st = A.st;
-  if (st->status != 0 || st->action == ACT_DONE) return;
+  // reuse_lists: the point is the one of the last screen and only the
+  // multipliers changed; its certificates (zero-multiplier balls strictly
+  // inside) still hold, and its lists contain every ball that had or gets a
+  // multiplier.  Only k_rows64 runs again.
+  if (st->status != 0 || st->action == ACT_DONE || st->reuse_lists) return;
+  if (A.log_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0) st->screen_log[A.log_slot] = 1;
   const int d4 = A.d4;
   float4* s_y = reinterpret_cast<float4*>(smem_raw);
   __shared__ int s_wc[kPassWarps];
@@ -236,7 +242,6 @@ __global__ void __launch_bounds__(kPassThreads) k_screen(PassArgs A) {
     if (need) {
       const int64_t o = base + count + off + __popc(msk & ((1u << lane) - 1u));
       A.unc_idx[o] = (int)i;
-      A.unc_slot[o] = myslot;
     }
     count += tot;
     __syncthreads();
@@ -328,6 +333,8 @@ __global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A) {
   __shared__ double s_wp[kPassWarps][P_COUNT];
   for (int j = threadIdx.x; j < d; j += kPassThreads) s_ct[j] = A.ct[j];
   const int cur = st->sup_cur;
+  const int nsup = st->nsup;
+  const int* sidx = cur ? A.sup_idx1 : A.sup_idx0;
   const double* su = cur ? A.sup_u1 : A.sup_u0;
   const double* sv = cur ? A.sup_v1 : A.sup_v0;
   const double inv_s = st->inv_s, sigma = st->sigma, inv_sigma = st->inv_sigma;
@@ -347,7 +354,11 @@ __global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A) {
     const int my = e0 + lane;
     const bool valid = my < tot;
     const int64_t myii = valid ? (int64_t)A.unc_idx[base + c0 + my] : 0;
-    const int mysl = valid ? A.unc_slot[base + c0 + my] : -1;
+    int mysl = -1;
+    if (valid) {
+      const int sl0 = A.slot[myii];
+      if ((unsigned)sl0 < (unsigned)nsup && sidx[sl0] == (int)myii) mysl = sl0;
+    }
     for (int q = 0; q < 32 && e0 + q < tot; q++) {
       const int64_t ii = __shfl_sync(MEB_FULLMASK, myii, q);
       const int sl = __shfl_sync(MEB_FULLMASK, mysl, q);
@@ -458,9 +469,26 @@ __global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A) {
   }
 }
 
-int pass_blocks(int64_t m, int* tiles_per_block) {
+// Resident k_screen blocks on this GPU for a given dynamic shared memory size
+// (one wave of blocks), cached per size.
+static int screen_resident_blocks(int d4) {
+  static int cached_d4 = -1, cached = 0;
+  if (cached_d4 != d4) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_screen, kPassThreads, 16 * (size_t)d4);
+    if (per < 1) per = 1;
+    if (sms < 1) sms = 1;
+    cached = sms * per;
+    cached_d4 = d4;
+  }
+  return cached;
+}
+
+int pass_blocks(int64_t m, int d, int* tiles_per_block) {
   const int64_t ntiles = (m + kPassThreads - 1) / kPassThreads;
-  const int64_t target = 152 * 6;
+  const int64_t target = screen_resident_blocks((d + 3) / 4);
   int64_t tpb = (ntiles + target - 1) / target;
   if (tpb < 1) tpb = 1;
   *tiles_per_block = (int)tpb;
@@ -468,13 +496,14 @@ int pass_blocks(int64_t m, int* tiles_per_block) {
 }
 
 cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m, int d,
-                        cudaStream_t s) {
+                        cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int log_slot) {
   PassArgs A;
+  A.log_slot = log_slot;
   A.C = C; A.R = R; A.m = m;
   const int d4 = (d + 3) / 4;
   A.m_pad = ((m + 255) / 256) * 256;
   A.d = d; A.d4 = d4;
-  const int nb = pass_blocks(m, &A.tiles_per_block);
+  const int nb = pass_blocks(m, d, &A.tiles_per_block);
   A.X32 = B.X32; A.R32 = B.R32; A.slot = B.slot;
   A.sup_idx0 = B.sup_idx[0]; A.sup_idx1 = B.sup_idx[1];
   A.sup_u0 = B.sup_u[0]; A.sup_u1 = B.sup_u[1];
@@ -491,7 +520,14 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
     e = cudaFuncSetAttribute(k_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh1);
     if (e != cudaSuccess) return e;
   }
+  // cudaEventRecordExternal: inside a stream capture the records become event
+  // nodes of the graph, so the events carry device times of every launch
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (ev0 || ev1) cudaStreamIsCapturing(s, &cap);
+  const unsigned evf = (cap == cudaStreamCaptureStatusActive) ? cudaEventRecordExternal : 0u;
+  if (ev0) cudaEventRecordWithFlags(ev0, s, evf);
   k_screen<<<nb, kPassThreads, sh1, s>>>(A);
+  if (ev1) cudaEventRecordWithFlags(ev1, s, evf);
   k_early<<<1, 256, 0, s>>>(B, d, nb);
   const size_t sh2 = 8 * (size_t)d;
   if (sh2 > 48 * 1024) {
@@ -613,7 +649,7 @@ __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buff
 
 cudaError_t launch_support_rows(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s) {
   int tpb;
-  const int nb = pass_blocks(m, &tpb);
+  const int nb = pass_blocks(m, d, &tpb);
   k_compact_S<<<(nb + 255) / 256, 256, 0, s>>>(B, nb, (int64_t)tpb * kPassThreads);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -56,6 +56,7 @@ __device__ void do_outer(DevState* st, const DevVecs& V, int d, double* sh) {
       }
       st->pinf_prev = pinf;
       st->phase = 0;
+      st->reuse_lists = 1;
     }
     st->action = act;
     s_act = act;
@@ -118,6 +119,8 @@ __global__ void __launch_bounds__(256) k_control_a(Buffers B, int d, int nb) {
   const double mag_t = fabs(V.xt[0]) + 0.5 * sigma * s_last[P_PI2] + 0.5 * tos * dx2;
   if (threadIdx.x == 0) {
     for (int k = 0; k < P_COUNT; k++) st->last[k] = s_last[k];
+    if (!st->reuse_lists) st->screens += 1;
+    st->reuse_lists = 0;
     st->tot_passes += 1;
     st->n64_total += (int64_t)s_last[P_N64];
     st->dx2_t = dx2;
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(256) k_control_b(Buffers B, int d) {
 
 cudaError_t launch_tick_control(Buffers& B, int64_t m, int d, cudaStream_t s) {
   int tpb;
-  const int nb = pass_blocks(m, &tpb);
+  const int nb = pass_blocks(m, d, &tpb);
   k_control_a<<<1, 256, 0, s>>>(B, d, nb);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1059,6 +1062,22 @@ __global__ void k_final_point(Buffers B, int d, double* __restrict__ c_out,
   const double s = st->s;
   for (int j = threadIdx.x; j < d; j += blockDim.x) c_out[j] = B.vec.x[1 + j] * s;
   if (threadIdx.x == 0) *r_alm = B.vec.x[0] * s;
+}
+
+// Loop condition of the device-resident solve (CUDA graph while-node): one
+// more tick while the controller runs; a tick cap ends a loop that does not
+// terminate with status 3.
+__global__ void k_loop_cond(Buffers B, cudaGraphConditionalHandle h) {
+  DevState* st = B.st;
+  st->ticks += 1;
+  if (st->status == 0 && st->ticks >= st->max_ticks) st->status = 3;
+  cudaGraphSetConditional(h, st->status == 0 ? 1u : 0u);
+}
+
+cudaError_t launch_loop_cond(Buffers& B, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_loop_cond<<<1, 1, 0, s>>>(B, h);
+  B.launches += 1;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_final_point(Buffers& B, int d, double* c_out, double* r_alm, cudaStream_t s) {

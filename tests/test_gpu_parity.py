@@ -194,3 +194,32 @@ def test_device_pointer_path():
     assert g["r"] == h["r"]
     assert np.array_equal(g["c"].cpu().numpy(), h["c"])
     assert np.array_equal(g["active"].cpu().numpy(), h["active"])
+
+
+def test_tick_loops_agree(monkeypatch):
+    """The graph-batched tick loop (default), the host-driven loop and the
+    while-node graph run the same kernels in the same order: bit-identical."""
+    C, R = workloads.cube(30_000, 40, 17, 0.05)
+    ctxs = {}
+    for mode in ("default", "host", "while"):
+        if mode == "default":
+            monkeypatch.delenv("MEB_TICK_LOOP", raising=False)
+        else:
+            monkeypatch.setenv("MEB_TICK_LOOP", mode)
+        ctxs[mode] = meb.Context(0)
+    monkeypatch.delenv("MEB_TICK_LOOP", raising=False)
+    res = {k: meb.solve(C, R, ctx=c) for k, c in ctxs.items()}
+    g = res["default"]
+    for k in ("host", "while"):
+        h = res[k]
+        assert g["r"] == h["r"] and np.array_equal(g["c"], h["c"]), k
+        assert g["passes"] == h["passes"] and g["ssn_iters"] == h["ssn_iters"], k
+        assert np.array_equal(g["active"], h["active"]), k
+    ctx = ctxs["default"]
+    ctx.set_profiling(True)          # event nodes in the graph: same results
+    p = meb.solve(C, R, ctx=ctx)
+    ctx.set_profiling(False)
+    assert p["r"] == g["r"] and np.array_equal(p["c"], g["c"])
+    assert ctx.stats()["pass_launches"] > 0
+    g2 = meb.solve(C, R, ctx=ctx)    # graph reused
+    assert g2["r"] == g["r"] and np.array_equal(g2["c"], g["c"])
