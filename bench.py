@@ -117,6 +117,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate(dist, tot_ms: float, ok: int, device=None):
+    """Whole-job throughput over ranks: (sum of correct solves) / (max time).
+    Ranks share no data on the path; only these two scalars are reduced."""
+    if dist is None:
+        return ok / (tot_ms / 1e3), tot_ms, ok
+    import torch
+    t = torch.tensor([tot_ms], dtype=torch.float64, device=device)
+    n = torch.tensor([ok], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(n.item()) / (float(t.item()) / 1e3), float(t.item()), int(n.item())
+
+
 def oracle_sample(C, R):
     """The CPU oracle as it stands on the first SAMPLE_M balls; returns seconds."""
     import oracle
@@ -220,14 +233,9 @@ def main():
     st = ctx.stats()
     ctx.set_profiling(False)
     lat = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(lat)
-    if dist:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
     relerr = [abs(r - r_ref) / r_ref for r in radii] if r_ref else []
-    ok = sum(1 for e in relerr if e <= 1e-8) if r_ref else 0
-    value = world * ok / (tot_ms / 1e3) if r_ref else world * args.steps / (tot_ms / 1e3)
+    ok = sum(1 for e in relerr if e <= 1e-8) if r_ref else args.steps
+    value, tot_ms, ok_all = aggregate(dist, sum(lat), ok, device="cuda")
 
     # roofline of the dominant kernel, k_screen (the full FP32 pass over all
     # balls): algorithmic bytes per launch / mean event-timed launch duration
@@ -269,7 +277,7 @@ def main():
                        "l2": "inputs (1.6 GB) larger than L2; no flush",
                        "parallelism": f"replicas x{world}"},
             "p50_ms": statistics.median(lat), "p99_ms": float(np.percentile(lat, 99)),
-            "max_relerr": max(relerr) if relerr else None, "solves_ok": ok,
+            "max_relerr": max(relerr) if relerr else None, "solves_ok": ok_all,
             "passes_per_solve": res["passes"], "ssn_per_solve": res["ssn_iters"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
