@@ -138,6 +138,26 @@ int meb_feas_check(meb_ctx *ctx, const double *centers, const double *radii, int
                    double *delta_max, int64_t *argmax, int64_t *viol_idx, int64_t viol_cap,
                    int64_t *n_viol);
 
+/* Allocation-free variant of meb_feas_check (the paper has no counterpart: it
+ * exists for callers that cannot call cudaMalloc, such as engines whose device
+ * memory belongs to their own pool or to another framework's caching
+ * allocator, and loops that forbid allocation once running).  Same results as
+ * meb_feas_check, computed in FP64 from the rows.  No context: the work runs on
+ * `cuda_stream` (NULL: the legacy default stream) of the current device, and the
+ * call returns after it completes.  centers (m x d), radii (m), c (d) and
+ * viol_idx (viol_cap entries, may be NULL with viol_cap 0) are DEVICE pointers on
+ * the current device; delta_max, argmax and n_viol are host pointers.
+ * Scratch: a fixed static device array (about 33 KB per GPU that loads the
+ * library, held until exit); the call allocates and frees nothing.  The first
+ * call on a device caches the array's device address (cudaGetSymbolAddress):
+ * make it before any stream capture on that device.  All calls share the array:
+ * calls that overlap on the GPU (several streams or host threads) race.
+ * Limits: 1 <= m <= 2^31 - 1, 1 <= d <= 4096; larger sizes return MEB_EINVAL. */
+int meb_feas_check_noalloc(const double *centers, const double *radii, int64_t m, int32_t d,
+                           const double *c, double r, double eps, void *cuda_stream,
+                           double *delta_max, int64_t *argmax, int64_t *viol_idx,
+                           int64_t viol_cap, int64_t *n_viol);
+
 #ifdef __cplusplus
 }
 #endif

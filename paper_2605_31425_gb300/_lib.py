@@ -83,6 +83,10 @@ def load():
                                            ct.c_double, ct.c_double, ct.c_uint, _D, _I64, _I64,
                                            ct.c_int64, _I64]
             lib.meb_feas_check.restype = ct.c_int
+            lib.meb_feas_check_noalloc.argtypes = [_D, _D, ct.c_int64, ct.c_int32, _D, ct.c_double,
+                                                   ct.c_double, ct.c_void_p, _D, _I64, _I64,
+                                                   ct.c_int64, _I64]
+            lib.meb_feas_check_noalloc.restype = ct.c_int
             lib.meb_set_profiling.argtypes = [ct.c_void_p, ct.c_int]
             lib.meb_reset_stats.argtypes = [ct.c_void_p]
             lib.meb_get_stats.argtypes = [ct.c_void_p, ct.POINTER(MebStats)]
@@ -292,3 +296,23 @@ def feas_check(centers, radii, c, r, eps, cap=None, ctx: Context | None = None):
                                 ct.byref(am), _as_i(pv), cap, ct.byref(nv))
     cx._check(rc)
     return dm.value, am.value, viol[:min(nv.value, cap)], nv.value
+
+
+def feas_check_noalloc(centers, radii, c, r, eps, viol, stream: int | None = None):
+    """meb_feas_check_noalloc: the allocation-free feasibility check, for callers
+    that cannot call cudaMalloc.  centers, radii, c and viol (int64, its length
+    is the cap) are torch CUDA tensors on the current device; no context, no
+    allocation inside the library.  Returns (delta_max, argmax, n_viol)."""
+    lib = load()
+    m, d = centers.shape
+    dm = ct.c_double()
+    am = ct.c_int64()
+    nv = ct.c_int64()
+    rc = lib.meb_feas_check_noalloc(_as_d(centers.data_ptr()), _as_d(radii.data_ptr()), m, d,
+                                    _as_d(c.data_ptr()), float(r), float(eps),
+                                    ct.c_void_p(stream) if stream else None, ct.byref(dm),
+                                    ct.byref(am), _as_i(viol.data_ptr()), int(viol.numel()),
+                                    ct.byref(nv))
+    if rc != MEB_OK:
+        raise MebError(rc, "meb_feas_check_noalloc failed")
+    return dm.value, am.value, nv.value

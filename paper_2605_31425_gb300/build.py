@@ -1,6 +1,6 @@
 """Build libmeb.so (the CUDA hot path) in-tree with nvcc for sm_103a.
 
-Three translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 ``paper_2605_31425_gb300/_build/libmeb.so``; rebuilt only when a source is
 newer than the library.
 """
@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmeb.so")
-SOURCES = ["meb_pass.cu", "meb_solve.cu", "meb_api.cu"]
+SOURCES = ["meb_pass.cu", "meb_solve.cu", "meb_api.cu", "meb_noalloc.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 
