@@ -51,7 +51,7 @@ struct meb_ctx {
 };
 
 // kernels launched per controller tick of the device-resident loop
-static const int64_t kTickLaunches = 3 + 4 + 5 + 3;
+static const int64_t kTickLaunches = 2 + 2 + 4 + 2;
 static const int kUnrollTicks = 8;
 
 enum { POOL_C, POOL_R, POOL_U, POOL_V, POOL_X, POOL_XB, POOL_Q, POOL_UP, POOL_VP, POOL_HQ,

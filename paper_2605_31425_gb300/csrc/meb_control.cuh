@@ -1,0 +1,304 @@
+// The controller of Algorithms 1 and 2 as block-level device functions.  Each
+// runs in the last block of the kernel that produced its inputs (the block
+// that takes the last ticket after every block has fenced its writes), so the
+// decisions need no kernel launch of their own.  Vector work (length d + 1)
+// is spread over the block's 256 threads.
+#pragma once
+#include "meb_common.cuh"
+
+namespace meb {
+
+// Last-block-done: every thread fences its writes, then thread 0 takes a
+// ticket; the block holding the last ticket returns true (after an acquire
+// fence) and resets the counter for the next launch.
+__device__ __forceinline__ bool last_block_ticket(unsigned int* ctr) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int t = atomicAdd(ctr, 1u);
+    s_last = (t == gridDim.x - 1);
+    if (s_last) *ctr = 0u;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+// Outer update (Algorithm 1): (alpha,beta) -= sigma g, KKT_max, sigma rule.
+// Returns the action; thread 0 writes the state.
+__device__ __forceinline__ void do_outer(DevState* st, const DevVecs& V, int d, double* sh) {
+  const int n1 = d + 1;
+  const double sigma = st->sigma;
+  for (int k = threadIdx.x; k < n1; k += blockDim.x) V.ab[k] -= sigma * V.g[k];
+  double q = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) q += V.sv[j] * V.sv[j];
+  q = block_sum<256>(q, sh);
+  __shared__ int s_act;
+  if (threadIdx.x == 0) {
+    st->kkt[0] = fabs(1.0 - st->last[P_SU]);
+    st->kkt[1] = sqrt(q);
+    st->kkt[2] = st->last[P_KP];
+    st->kkt[3] = st->last[P_KD];
+    st->kkt[4] = st->last[P_KC];
+    double km = 0.0;
+    for (int k = 0; k < 5; k++) km = fmax(km, st->kkt[k]);
+    st->kkt_max = km;
+    st->outer += 1;
+    int act;
+    if (km <= st->tol) { st->status = 1; act = ACT_DONE; }
+    else if (st->outer >= st->max_outer) { st->status = 2; act = ACT_DONE; }
+    else {
+      act = ACT_OUTER;
+      const double pinf = st->last[P_KP];
+      // the multiplier update uses the sigma of the finished outer step
+      st->sigma_prev = sigma;
+      if (pinf > st->tol && pinf > st->sigma_ratio * st->pinf_prev) {
+        double sg = sigma * st->sigma_growth;
+        if (sg > st->sigma_max) sg = st->sigma_max;
+        st->sigma = sg;
+        st->inv_sigma = 1.0 / sg;
+      }
+      st->pinf_prev = pinf;
+      st->phase = 0;
+      st->reuse_lists = 1;
+    }
+    st->action = act;
+    s_act = act;
+  }
+  __syncthreads();
+  if (s_act == ACT_OUTER) {
+    for (int k = threadIdx.x; k < n1; k += blockDim.x) {
+      V.xk[k] = V.x[k];
+      V.xt[k] = V.x[k];
+    }
+    __syncthreads();
+    set_trial(st, V, d, sh);
+  }
+}
+
+// Early line-search rejection (the last block of k_screen): from the screen's certified lower
+// bound Psi_lb <= Psi(trial) (only balls with zero multipliers counted), a
+// trial with Psi_lb above the Armijo threshold is rejected without its FP64
+// rows; the next trial is set as in the controller.
+__device__ __forceinline__ void early_body(const Buffers& B, int d, int nb) {
+  DevState* st = B.st;
+  if (st->phase != 1 || st->eval_only) {
+    if (threadIdx.x == 0 && st->action == ACT_TRIAL_EARLY) st->action = ACT_TRIAL;
+    return;
+  }
+  __shared__ double sh[32];
+  __shared__ int s_rej;
+  const DevVecs& V = B.vec;
+  const int n1 = d + 1;
+  double t = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 256) t += (double)B.vlb_part[b];
+  t = block_sum<256>(t, sh);
+  double dx2 = 0.0;
+  for (int k = threadIdx.x; k < n1; k += 256) {
+    const double dk = V.xt[k] - V.xk[k];
+    dx2 += dk * dk;
+  }
+  dx2 = block_sum<256>(dx2, sh);
+  if (threadIdx.x == 0) {
+    const double sigma = st->sigma, tos = st->tau / sigma;
+    // FP32 sums of nonnegative terms: keep 1% for their rounding
+    const double pi2_lb = 0.99 * t * st->inv_s * st->inv_s * 0.5;
+    const double psi_lb = V.xt[0] + 0.5 * sigma * pi2_lb + 0.5 * tos * dx2;
+    const double mag = fabs(V.xt[0]) + 0.5 * sigma * pi2_lb + 0.5 * tos * dx2;
+    const double allow = 64.0 * DBL_EPSILON * fmax(st->psi_mag, mag);
+    const double thr = st->psi + st->mu * st->eta * st->gdx + allow;
+    int rej = 0;
+    if (psi_lb > thr && st->bt < st->max_backtrack) {
+      const double eta = st->eta;
+      const double den = 2.0 * (psi_lb - st->psi - st->gdx * eta);
+      double en = (den > 0.0) ? -st->gdx * eta * eta / den : 0.5 * eta;
+      en = fmin(fmax(en, 0.1 * eta), 0.5 * eta);
+      st->eta = en;
+      st->bt += 1;
+      st->tot_bt += 1;
+      st->tot_passes += 1;
+      st->early_rejects += 1;
+      st->last[P_N64] = 0.0;
+      st->action = ACT_TRIAL_EARLY;
+      rej = 1;
+    } else if (st->action == ACT_TRIAL_EARLY) {
+      st->action = ACT_TRIAL;   // the trial set by the previous early rejection is evaluated
+    }
+    s_rej = rej;
+  }
+  __syncthreads();
+  if (s_rej) {
+    const double eta = st->eta;
+    for (int k = threadIdx.x; k < n1; k += 256) V.xt[k] = V.x[k] + eta * V.dx[k];
+    __syncthreads();
+    set_trial(st, V, d, sh);
+  }
+}
+
+// Controller, part A (the last block of k_rows64): reduce the pass partials,
+// form Psi at the trial and take the line-search decision (Algorithm 2).  A rejected trial
+// sets the next trial directly; an accepted one (or the first evaluation of an
+// outer step) asks for the gradient: action ACT_GRAD.
+__device__ __forceinline__ void control_a_body(const Buffers& B, int d, int nb) {
+  DevState* st = B.st;
+  const DevVecs& V = B.vec;
+  const int n1 = d + 1;
+  __shared__ double sh[32];
+  __shared__ double s_last[P_COUNT];
+  __shared__ int s_next;
+  {
+    double acc[P_COUNT];
+#pragma unroll
+    for (int k = 0; k < P_COUNT; k++) acc[k] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 256) {
+      if (!B.part_flag[b]) continue;
+      const double* p = B.part + (int64_t)b * P_COUNT;
+#pragma unroll
+      for (int k = 0; k < P_COUNT; k++) {
+        const bool ismax = (k == P_KP || k == P_KD || k == P_KC);
+        acc[k] = ismax ? fmax(acc[k], p[k]) : acc[k] + p[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < P_COUNT; k++) {
+      const bool ismax = (k == P_KP || k == P_KD || k == P_KC);
+      const double r = ismax ? block_max<256>(acc[k], sh) : block_sum<256>(acc[k], sh);
+      if (threadIdx.x == 0) s_last[k] = r;
+    }
+  }
+  const double sigma = st->sigma, tos = st->tau / sigma;
+  double dx2 = 0.0;
+  for (int k = threadIdx.x; k < n1; k += 256) {
+    const double dk = V.xt[k] - V.xk[k];
+    dx2 += dk * dk;
+  }
+  dx2 = block_sum<256>(dx2, sh);
+  const double psi_t = V.xt[0] + 0.5 * sigma * s_last[P_PI2] + 0.5 * tos * dx2;
+  const double mag_t = fabs(V.xt[0]) + 0.5 * sigma * s_last[P_PI2] + 0.5 * tos * dx2;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < P_COUNT; k++) st->last[k] = s_last[k];
+    if (!st->reuse_lists) st->screens += 1;
+    st->reuse_lists = 0;
+    st->tot_passes += 1;
+    st->n64_total += (int64_t)s_last[P_N64];
+    st->dx2_t = dx2;
+    int nxt = 0;   // 0: gradient at the (accepted) trial; 1: backtrack
+    if (st->eval_only) {
+      st->psi = psi_t - s_last[P_UV2] / (2.0 * sigma);
+      st->accept_mode = 0;
+    } else if (st->phase == 1) {
+      const double allow = 64.0 * DBL_EPSILON * fmax(st->psi_mag, mag_t);
+      const bool ok = psi_t <= st->psi + st->mu * st->eta * st->gdx + allow;
+      if (ok || st->bt >= st->max_backtrack) {
+        st->psi = psi_t; st->psi_mag = mag_t;
+        st->ssn_j += 1;
+        st->tot_ssn += 1;
+        st->accept_mode = (!ok || st->ssn_j >= st->max_ssn) ? 2 : 1;   // 2: outer forced
+      } else {
+        // next step: minimiser of the quadratic through Psi(0), Psi'(0), Psi(eta),
+        // kept in [eta/10, eta/2]
+        const double eta = st->eta;
+        const double den = 2.0 * (psi_t - st->psi - st->gdx * eta);
+        double en = (den > 0.0) ? -st->gdx * eta * eta / den : 0.5 * eta;
+        en = fmin(fmax(en, 0.1 * eta), 0.5 * eta);
+        st->eta = en;
+        st->bt += 1;
+        st->tot_bt += 1;
+        nxt = 1;
+      }
+    } else {
+      st->psi = psi_t; st->psi_mag = mag_t;
+      st->ssn_j = 0;
+      st->accept_mode = 1;
+    }
+    st->action = nxt ? ACT_TRIAL : ACT_GRAD;
+    s_next = nxt;
+  }
+  __syncthreads();
+  if (s_next == 1) {
+    const double eta = st->eta;
+    for (int k = threadIdx.x; k < n1; k += 256) V.xt[k] = V.x[k] + eta * V.dx[k];
+    __syncthreads();
+    set_trial(st, V, d, sh);
+    if (threadIdx.x == 0) st->phase = 1;
+  }
+}
+
+// Controller, part B (the last block of k_svec, after the support rows were
+// reduced): the gradient at the accepted point, then the relative-type stopping condition
+// (Algorithm 1) and the next action.
+__device__ __forceinline__ void control_b_body(const Buffers& B, int d) {
+  DevState* st = B.st;
+  const DevVecs& V = B.vec;
+  const int n1 = d + 1;
+  __shared__ double sh[32];
+  const int snb = st->svec_nb;
+  for (int j = threadIdx.x; j < d; j += 256) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int k = 0; k < snb; k++) {
+      const double* p = B.svec_part + (int64_t)k * (3 * d + 1);
+      a += p[j];
+      b += p[d + j];
+      c += p[2 * d + j];
+    }
+    V.sv[j] = a;
+    V.sw[j] = b;
+    V.cg_diag[1 + j] = c;   // sum_M t w_j^2 (Jacobi preconditioner)
+  }
+  if (threadIdx.x == 0) {
+    double s1t = 0.0;
+    for (int k = 0; k < snb; k++) s1t += B.svec_part[(int64_t)k * (3 * d + 1) + 3 * d];
+    V.st1[0] = s1t;
+  }
+  __syncthreads();
+  const double sigma = st->sigma, tau = st->tau, tos = tau / sigma;
+  const double su = st->last[P_SU];
+  for (int k = threadIdx.x; k < n1; k += 256) {
+    const double dk = V.xt[k] - V.xk[k];
+    const double sk = (k == 0) ? su : V.sv[k - 1];
+    V.gt[k] = ((k == 0) ? 1.0 : 0.0) - sk + tos * dk;
+  }
+  __syncthreads();
+  if (st->eval_only) {
+    if (threadIdx.x == 0) { st->action = ACT_DONE; st->status = 1; }
+    return;
+  }
+  // accepted point: x <- xt, g <- gt
+  for (int k = threadIdx.x; k < n1; k += 256) {
+    V.x[k] = V.xt[k];
+    V.g[k] = V.gt[k];
+  }
+  if (threadIdx.x == 0) {
+    st->gmag = 1.0 + sigma * st->last[P_ZMAG] + tos * sqrt(st->dx2_t);
+    st->phase = 2;
+  }
+  __syncthreads();
+  if (st->accept_mode == 2) {
+    do_outer(st, V, d, sh);
+    return;
+  }
+  double la = 0.0, g2 = 0.0, dk2 = 0.0;
+  for (int k = threadIdx.x; k < n1; k += 256) {
+    la += (V.ab[k] - V.x[k]) * V.g[k];
+    g2 += V.g[k] * V.g[k];
+    const double t = V.x[k] - V.xk[k];
+    dk2 += t * t;
+  }
+  la = block_sum<256>(la, sh);
+  g2 = block_sum<256>(g2, sh);
+  dk2 = block_sum<256>(dk2, sh);
+  const double lhs = 2.0 * sigma * fabs(la) + sigma * sigma * g2;
+  const double rhs = st->rho * (st->last[P_DUV2] + tau * dk2);
+  const bool stop = (lhs <= rhs) || (sqrt(g2) <= 8.0 * DBL_EPSILON * st->gmag);
+  if (stop) {
+    do_outer(st, V, d, sh);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    st->action = ACT_NEWTON;
+    st->bt = 0;
+  }
+}
+
+}  // namespace meb

@@ -77,6 +77,7 @@ struct DevState {
   int reuse_lists;             // next pass: same point, new multipliers (skip the screen)
   int64_t ticks, max_ticks;    // controller ticks of the device-resident loop and their cap
   int screen_log[8];           // profiling: tick t of a graph batch ran a full screen
+  unsigned int ctr_screen, ctr_rows, ctr_svec, ctr_slots;   // last-block-done tickets
   int screens;                 // full FP32 screens run
   double dx2_t;                // ||xt - xk||^2 of the last trial
   double kkt[5], kkt_max;

@@ -17,7 +17,7 @@
 // it contributes exactly nothing).  Every other ball is evaluated in FP64
 // from its original row.  All reductions use fixed block-to-ball maps and
 // fixed-order trees, so results are deterministic.
-#include "meb_common.cuh"
+#include "meb_control.cuh"
 
 namespace meb {
 
@@ -150,7 +150,7 @@ struct PassArgs {
   double* cand_a; double* cand_n; double* cand_u;
 };
 
-__global__ void __launch_bounds__(kPassThreads) k_screen(PassArgs A) {
+__global__ void __launch_bounds__(kPassThreads) k_screen(PassArgs A, Buffers B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DevState* st = A.st;
   // reuse_lists: the point is the one of the last screen and only the
@@ -256,63 +256,10 @@ __global__ void __launch_bounds__(kPassThreads) k_screen(PassArgs A) {
     A.unc_cnt[blockIdx.x] = count;
     A.vlb_part[blockIdx.x] = t;
   }
+  if (last_block_ticket(&st->ctr_screen)) early_body(B, A.d, gridDim.x);
 }
 
-// Early line-search rejection (one block): from the screen's certified lower
-// bound Psi_lb <= Psi(trial) (only balls with zero multipliers counted), a
-// trial with Psi_lb above the Armijo threshold is rejected without its FP64
-// rows; the next trial is set as in the controller.
-__global__ void __launch_bounds__(256) k_early(Buffers B, int d, int nb) {
-  DevState* st = B.st;
-  if (st->status != 0 || st->action == ACT_DONE || st->phase != 1 || st->eval_only) return;
-  __shared__ double sh[32];
-  __shared__ int s_rej;
-  const DevVecs& V = B.vec;
-  const int n1 = d + 1;
-  double t = 0.0;
-  for (int b = threadIdx.x; b < nb; b += 256) t += (double)B.vlb_part[b];
-  t = block_sum<256>(t, sh);
-  double dx2 = 0.0;
-  for (int k = threadIdx.x; k < n1; k += 256) {
-    const double dk = V.xt[k] - V.xk[k];
-    dx2 += dk * dk;
-  }
-  dx2 = block_sum<256>(dx2, sh);
-  if (threadIdx.x == 0) {
-    const double sigma = st->sigma, tos = st->tau / sigma;
-    // FP32 sums of nonnegative terms: keep 1% for their rounding
-    const double pi2_lb = 0.99 * t * st->inv_s * st->inv_s * 0.5;
-    const double psi_lb = V.xt[0] + 0.5 * sigma * pi2_lb + 0.5 * tos * dx2;
-    const double mag = fabs(V.xt[0]) + 0.5 * sigma * pi2_lb + 0.5 * tos * dx2;
-    const double allow = 64.0 * DBL_EPSILON * fmax(st->psi_mag, mag);
-    const double thr = st->psi + st->mu * st->eta * st->gdx + allow;
-    int rej = 0;
-    if (psi_lb > thr && st->bt < st->max_backtrack) {
-      const double eta = st->eta;
-      const double den = 2.0 * (psi_lb - st->psi - st->gdx * eta);
-      double en = (den > 0.0) ? -st->gdx * eta * eta / den : 0.5 * eta;
-      en = fmin(fmax(en, 0.1 * eta), 0.5 * eta);
-      st->eta = en;
-      st->bt += 1;
-      st->tot_bt += 1;
-      st->tot_passes += 1;
-      st->early_rejects += 1;
-      st->last[P_N64] = 0.0;
-      st->action = ACT_TRIAL_EARLY;
-      rej = 1;
-    }
-    s_rej = rej;
-  }
-  __syncthreads();
-  if (s_rej) {
-    const double eta = st->eta;
-    for (int k = threadIdx.x; k < n1; k += 256) V.xt[k] = V.x[k] + eta * V.dx[k];
-    __syncthreads();
-    set_trial(st, V, d, sh);
-  }
-}
-
-__global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A) {
+__global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A, Buffers B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DevState* st = A.st;
   if (st->status != 0 || st->action == ACT_DONE || st->action == ACT_TRIAL_EARLY) return;
@@ -322,6 +269,7 @@ __global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A) {
       A.part_flag[blockIdx.x] = 0;
       A.cand_cnt[blockIdx.x] = 0;
     }
+    if (last_block_ticket(&st->ctr_rows)) control_a_body(B, A.d, gridDim.x);
     return;
   }
   const int d = A.d;
@@ -467,6 +415,7 @@ __global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A) {
     A.part_flag[blockIdx.x] = 1;
     A.cand_cnt[blockIdx.x] = ccount;
   }
+  if (last_block_ticket(&st->ctr_rows)) control_a_body(B, A.d, gridDim.x);
 }
 
 // Resident k_screen blocks on this GPU for a given dynamic shared memory size
@@ -526,16 +475,15 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
   if (ev0 || ev1) cudaStreamIsCapturing(s, &cap);
   const unsigned evf = (cap == cudaStreamCaptureStatusActive) ? cudaEventRecordExternal : 0u;
   if (ev0) cudaEventRecordWithFlags(ev0, s, evf);
-  k_screen<<<nb, kPassThreads, sh1, s>>>(A);
+  k_screen<<<nb, kPassThreads, sh1, s>>>(A, B);
   if (ev1) cudaEventRecordWithFlags(ev1, s, evf);
-  k_early<<<1, 256, 0, s>>>(B, d, nb);
   const size_t sh2 = 8 * (size_t)d;
   if (sh2 > 48 * 1024) {
     e = cudaFuncSetAttribute(k_rows64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh2);
     if (e != cudaSuccess) return e;
   }
-  k_rows64<<<nb, kPassThreads, sh2, s>>>(A);
-  B.launches += 3;
+  k_rows64<<<nb, kPassThreads, sh2, s>>>(A, B);
+  B.launches += 2;
   return cudaGetLastError();
 }
 
@@ -598,7 +546,10 @@ __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buff
   if (rpb < 8) rpb = 8;
   const int nblk = (nS + rpb - 1) / rpb;
   if (blockIdx.x == 0 && threadIdx.x == 0) { st->svec_nb = nblk; st->svec_rpb = rpb; }
-  if ((int)blockIdx.x >= nblk) return;
+  if ((int)blockIdx.x >= nblk) {
+    if (last_block_ticket(&st->ctr_svec)) control_b_body(B, d);
+    return;
+  }
   const int k0 = blockIdx.x * rpb, k1 = min(nS, k0 + rpb);
   const int cur = st->sup_cur, nsup = st->nsup;
   const int* sidx = cur ? B.sup_idx[1] : B.sup_idx[0];
@@ -645,6 +596,7 @@ __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buff
     }
   }
   if (threadIdx.x == 0) out[3 * d] = s1t;
+  if (last_block_ticket(&st->ctr_svec)) control_b_body(B, d);
 }
 
 cudaError_t launch_support_rows(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s) {

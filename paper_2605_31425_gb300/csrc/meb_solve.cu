@@ -12,7 +12,7 @@
 #include <math.h>
 #include <stdint.h>
 
-#include "meb_common.cuh"
+#include "meb_control.cuh"
 
 namespace meb {
 
@@ -20,240 +20,10 @@ namespace meb {
 // Controller (one block): reduces the pass, forms grad and Psi, and takes the
 // decisions of Algorithms 1 and 2.  Vector work is spread over the block.
 
-// Outer update (Algorithm 1): (alpha,beta) -= sigma g, KKT_max, sigma rule.
-// Returns the action; thread 0 writes the state.
-__device__ void do_outer(DevState* st, const DevVecs& V, int d, double* sh) {
-  const int n1 = d + 1;
-  const double sigma = st->sigma;
-  for (int k = threadIdx.x; k < n1; k += blockDim.x) V.ab[k] -= sigma * V.g[k];
-  double q = 0.0;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) q += V.sv[j] * V.sv[j];
-  q = block_sum<256>(q, sh);
-  __shared__ int s_act;
-  if (threadIdx.x == 0) {
-    st->kkt[0] = fabs(1.0 - st->last[P_SU]);
-    st->kkt[1] = sqrt(q);
-    st->kkt[2] = st->last[P_KP];
-    st->kkt[3] = st->last[P_KD];
-    st->kkt[4] = st->last[P_KC];
-    double km = 0.0;
-    for (int k = 0; k < 5; k++) km = fmax(km, st->kkt[k]);
-    st->kkt_max = km;
-    st->outer += 1;
-    int act;
-    if (km <= st->tol) { st->status = 1; act = ACT_DONE; }
-    else if (st->outer >= st->max_outer) { st->status = 2; act = ACT_DONE; }
-    else {
-      act = ACT_OUTER;
-      const double pinf = st->last[P_KP];
-      // the multiplier update uses the sigma of the finished outer step
-      st->sigma_prev = sigma;
-      if (pinf > st->tol && pinf > st->sigma_ratio * st->pinf_prev) {
-        double sg = sigma * st->sigma_growth;
-        if (sg > st->sigma_max) sg = st->sigma_max;
-        st->sigma = sg;
-        st->inv_sigma = 1.0 / sg;
-      }
-      st->pinf_prev = pinf;
-      st->phase = 0;
-      st->reuse_lists = 1;
-    }
-    st->action = act;
-    s_act = act;
-  }
-  __syncthreads();
-  if (s_act == ACT_OUTER) {
-    for (int k = threadIdx.x; k < n1; k += blockDim.x) {
-      V.xk[k] = V.x[k];
-      V.xt[k] = V.x[k];
-    }
-    __syncthreads();
-    set_trial(st, V, d, sh);
-  }
-}
-
-// Controller, part A (one block): reduce the pass partials, form Psi at the
-// trial and take the line-search decision (Algorithm 2).  A rejected trial
-// sets the next trial directly; an accepted one (or the first evaluation of an
-// outer step) asks for the gradient: action ACT_GRAD.
-__global__ void __launch_bounds__(256) k_control_a(Buffers B, int d, int nb) {
-  DevState* st = B.st;
-  if (st->status != 0 || st->action == ACT_DONE) return;
-  if (st->action == ACT_TRIAL_EARLY) {   // decided by k_early; the next pass evaluates the new trial
-    if (threadIdx.x == 0) st->action = ACT_TRIAL;
-    return;
-  }
-  const DevVecs& V = B.vec;
-  const int n1 = d + 1;
-  __shared__ double sh[32];
-  __shared__ double s_last[P_COUNT];
-  __shared__ int s_next;
-  {
-    double acc[P_COUNT];
-#pragma unroll
-    for (int k = 0; k < P_COUNT; k++) acc[k] = 0.0;
-    for (int b = threadIdx.x; b < nb; b += 256) {
-      if (!B.part_flag[b]) continue;
-      const double* p = B.part + (int64_t)b * P_COUNT;
-#pragma unroll
-      for (int k = 0; k < P_COUNT; k++) {
-        const bool ismax = (k == P_KP || k == P_KD || k == P_KC);
-        acc[k] = ismax ? fmax(acc[k], p[k]) : acc[k] + p[k];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < P_COUNT; k++) {
-      const bool ismax = (k == P_KP || k == P_KD || k == P_KC);
-      const double r = ismax ? block_max<256>(acc[k], sh) : block_sum<256>(acc[k], sh);
-      if (threadIdx.x == 0) s_last[k] = r;
-    }
-  }
-  const double sigma = st->sigma, tos = st->tau / sigma;
-  double dx2 = 0.0;
-  for (int k = threadIdx.x; k < n1; k += 256) {
-    const double dk = V.xt[k] - V.xk[k];
-    dx2 += dk * dk;
-  }
-  dx2 = block_sum<256>(dx2, sh);
-  const double psi_t = V.xt[0] + 0.5 * sigma * s_last[P_PI2] + 0.5 * tos * dx2;
-  const double mag_t = fabs(V.xt[0]) + 0.5 * sigma * s_last[P_PI2] + 0.5 * tos * dx2;
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < P_COUNT; k++) st->last[k] = s_last[k];
-    if (!st->reuse_lists) st->screens += 1;
-    st->reuse_lists = 0;
-    st->tot_passes += 1;
-    st->n64_total += (int64_t)s_last[P_N64];
-    st->dx2_t = dx2;
-    int nxt = 0;   // 0: gradient at the (accepted) trial; 1: backtrack
-    if (st->eval_only) {
-      st->psi = psi_t - s_last[P_UV2] / (2.0 * sigma);
-      st->accept_mode = 0;
-    } else if (st->phase == 1) {
-      const double allow = 64.0 * DBL_EPSILON * fmax(st->psi_mag, mag_t);
-      const bool ok = psi_t <= st->psi + st->mu * st->eta * st->gdx + allow;
-      if (ok || st->bt >= st->max_backtrack) {
-        st->psi = psi_t; st->psi_mag = mag_t;
-        st->ssn_j += 1;
-        st->tot_ssn += 1;
-        st->accept_mode = (!ok || st->ssn_j >= st->max_ssn) ? 2 : 1;   // 2: outer forced
-      } else {
-        // next step: minimiser of the quadratic through Psi(0), Psi'(0), Psi(eta),
-        // kept in [eta/10, eta/2]
-        const double eta = st->eta;
-        const double den = 2.0 * (psi_t - st->psi - st->gdx * eta);
-        double en = (den > 0.0) ? -st->gdx * eta * eta / den : 0.5 * eta;
-        en = fmin(fmax(en, 0.1 * eta), 0.5 * eta);
-        st->eta = en;
-        st->bt += 1;
-        st->tot_bt += 1;
-        nxt = 1;
-      }
-    } else {
-      st->psi = psi_t; st->psi_mag = mag_t;
-      st->ssn_j = 0;
-      st->accept_mode = 1;
-    }
-    st->action = nxt ? ACT_TRIAL : ACT_GRAD;
-    s_next = nxt;
-  }
-  __syncthreads();
-  if (s_next == 1) {
-    const double eta = st->eta;
-    for (int k = threadIdx.x; k < n1; k += 256) V.xt[k] = V.x[k] + eta * V.dx[k];
-    __syncthreads();
-    set_trial(st, V, d, sh);
-    if (threadIdx.x == 0) st->phase = 1;
-  }
-}
-
-// Controller, part B (one block, after the support rows were reduced): the
-// gradient at the accepted point, then the relative-type stopping condition
-// (Algorithm 1) and the next action.
-__global__ void __launch_bounds__(256) k_control_b(Buffers B, int d) {
-  DevState* st = B.st;
-  if (st->status != 0 || st->action != ACT_GRAD) return;
-  const DevVecs& V = B.vec;
-  const int n1 = d + 1;
-  __shared__ double sh[32];
-  const int snb = st->svec_nb;
-  for (int j = threadIdx.x; j < d; j += 256) {
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int k = 0; k < snb; k++) {
-      const double* p = B.svec_part + (int64_t)k * (3 * d + 1);
-      a += p[j];
-      b += p[d + j];
-      c += p[2 * d + j];
-    }
-    V.sv[j] = a;
-    V.sw[j] = b;
-    V.cg_diag[1 + j] = c;   // sum_M t w_j^2 (Jacobi preconditioner)
-  }
-  if (threadIdx.x == 0) {
-    double s1t = 0.0;
-    for (int k = 0; k < snb; k++) s1t += B.svec_part[(int64_t)k * (3 * d + 1) + 3 * d];
-    V.st1[0] = s1t;
-  }
-  __syncthreads();
-  const double sigma = st->sigma, tau = st->tau, tos = tau / sigma;
-  const double su = st->last[P_SU];
-  for (int k = threadIdx.x; k < n1; k += 256) {
-    const double dk = V.xt[k] - V.xk[k];
-    const double sk = (k == 0) ? su : V.sv[k - 1];
-    V.gt[k] = ((k == 0) ? 1.0 : 0.0) - sk + tos * dk;
-  }
-  __syncthreads();
-  if (st->eval_only) {
-    if (threadIdx.x == 0) { st->action = ACT_DONE; st->status = 1; }
-    return;
-  }
-  // accepted point: x <- xt, g <- gt
-  for (int k = threadIdx.x; k < n1; k += 256) {
-    V.x[k] = V.xt[k];
-    V.g[k] = V.gt[k];
-  }
-  if (threadIdx.x == 0) {
-    st->gmag = 1.0 + sigma * st->last[P_ZMAG] + tos * sqrt(st->dx2_t);
-    st->phase = 2;
-  }
-  __syncthreads();
-  if (st->accept_mode == 2) {
-    do_outer(st, V, d, sh);
-    return;
-  }
-  double la = 0.0, g2 = 0.0, dk2 = 0.0;
-  for (int k = threadIdx.x; k < n1; k += 256) {
-    la += (V.ab[k] - V.x[k]) * V.g[k];
-    g2 += V.g[k] * V.g[k];
-    const double t = V.x[k] - V.xk[k];
-    dk2 += t * t;
-  }
-  la = block_sum<256>(la, sh);
-  g2 = block_sum<256>(g2, sh);
-  dk2 = block_sum<256>(dk2, sh);
-  const double lhs = 2.0 * sigma * fabs(la) + sigma * sigma * g2;
-  const double rhs = st->rho * (st->last[P_DUV2] + tau * dk2);
-  const bool stop = (lhs <= rhs) || (sqrt(g2) <= 8.0 * DBL_EPSILON * st->gmag);
-  if (stop) {
-    do_outer(st, V, d, sh);
-    return;
-  }
-  if (threadIdx.x == 0) {
-    st->action = ACT_NEWTON;
-    st->bt = 0;
-  }
-}
-
 cudaError_t launch_tick_control(Buffers& B, int64_t m, int d, cudaStream_t s) {
-  int tpb;
-  const int nb = pass_blocks(m, d, &tpb);
-  k_control_a<<<1, 256, 0, s>>>(B, d, nb);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  e = launch_support_rows(B.C_in, B, m, d, s);
-  if (e != cudaSuccess) return e;
-  k_control_b<<<1, 256, 0, s>>>(B, d);
-  B.launches += 2;
-  return cudaGetLastError();
+  // the line-search controller runs in the last block of k_rows64 and the
+  // stop-test controller in the last block of k_svec (meb_control.cuh)
+  return launch_support_rows(B.C_in, B, m, d, s);
 }
 
 // ===========================================================================
@@ -320,23 +90,36 @@ __global__ void __launch_bounds__(256) k_syrk(Buffers B, int d, int force) {
 __global__ void k_syrk_reduce(Buffers B, int d, int force) {
   DevState* st = B.st;
   if (!force && (st->status != 0 || st->action != ACT_NEWTON)) return;
+  // H = tau/sigma I + sigma (n_I I + 1/2 [[n_M, sum w^T], [sum w, sum(1+t) I - SY]]),
+  // SY = sum_M t w w^T from the group partials (summed in group order)
+  const DevVecs& V = B.vec;
   const int nt = (d + kSyrkTile - 1) / kSyrkTile;
   const int ntri = nt * (nt + 1) / 2;
-  const int64_t tot = (int64_t)ntri * kSyrkTile * kSyrkTile;
   const int n1 = d + 1;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+  const double sigma = st->sigma, tos = st->tau / sigma;
+  const double nI = st->last[P_NI], nM = st->last[P_NM], s1t = V.st1[0];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)n1 * n1;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int tri = (int)(e / (kSyrkTile * kSyrkTile));
-    const int loc = (int)(e % (kSyrkTile * kSyrkTile));
-    int ti = 0;
-    while ((ti + 1) * (ti + 2) / 2 <= tri) ti++;
-    const int tj = tri - ti * (ti + 1) / 2;
-    const int j = ti * kSyrkTile + loc / kSyrkTile, l = tj * kSyrkTile + loc % kSyrkTile;
-    if (j >= d || l >= d || l > j) continue;
-    double s = 0.0;
-    for (int g = 0; g < kSyrkGroups; g++)
-      s += B.hpart[((int64_t)g * ntri + tri) * (kSyrkTile * kSyrkTile) + loc];
-    B.H[(int64_t)(1 + j) * n1 + (1 + l)] = s;
+    const int i = (int)(e / n1), l = (int)(e % n1);
+    if (l > i) continue;   // the thread of (i, l) writes (i, l) and (l, i)
+    double h;
+    if (i == 0) {
+      h = tos + sigma * (nI + 0.5 * nM);
+    } else if (l == 0) {
+      h = sigma * 0.5 * V.sw[i - 1];
+    } else {
+      const int j = i - 1, k = l - 1;   // k <= j
+      const int ti = j / kSyrkTile, tj = k / kSyrkTile;
+      const int tri = ti * (ti + 1) / 2 + tj;
+      const int loc = (j % kSyrkTile) * kSyrkTile + (k % kSyrkTile);
+      double sy = 0.0;
+      for (int g = 0; g < kSyrkGroups; g++)
+        sy += B.hpart[((int64_t)g * ntri + tri) * (kSyrkTile * kSyrkTile) + loc];
+      h = -0.5 * sigma * sy;
+      if (i == l) h += tos + sigma * (nI + 0.5 * s1t);
+    }
+    B.H[(int64_t)i * n1 + l] = h;
+    B.H[(int64_t)l * n1 + i] = h;
   }
 }
 
@@ -424,31 +207,6 @@ __global__ void __launch_bounds__(256) k_newton_chol(Buffers B, int d) {
   }
   __syncthreads();
   set_trial(st, V, d, sh);
-}
-
-// Full FP64 H (both triangles) in B.H from the SYRK block (lower triangle of
-// rows/cols 1..d) and the scalar / vector parts.
-__global__ void k_assemble_h(Buffers B, int d, int force) {
-  DevState* st = B.st;
-  if (!force && (st->status != 0 || st->action != ACT_NEWTON)) return;
-  const DevVecs& V = B.vec;
-  const int n = d + 1;
-  const double sigma = st->sigma, tos = st->tau / sigma;
-  const double nI = st->last[P_NI], nM = st->last[P_NM], s1t = V.st1[0];
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)n * n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / n), l = (int)(e % n);
-    if (l > i) continue;   // the thread of (i, l) writes both (i, l) and (l, i)
-    double h;
-    if (i == 0) h = tos + sigma * (nI + 0.5 * nM);
-    else if (l == 0) h = sigma * 0.5 * V.sw[i - 1];
-    else {
-      h = -0.5 * sigma * B.H[(int64_t)i * n + l];
-      if (i == l) h += tos + sigma * (nI + 0.5 * s1t);
-    }
-    B.H[(int64_t)i * n + l] = h;
-    B.H[(int64_t)l * n + i] = h;
-  }
 }
 
 // One block: FP32 Gauss-Jordan inverse of H (SPD, no pivoting needed), then
@@ -625,7 +383,10 @@ __global__ void __launch_bounds__(256) k_newton_gj_reg(Buffers B, int d) {
     }
     __syncthreads();
     double rn0 = 0.0;
-    for (int it = 0; it < 4; it++) {
+    // x0 and at most two corrections: the Newton direction needs a small
+    // relative error, not FP64 accuracy (the stop test, Armijo and KKT use
+    // the FP64 gradient and Psi)
+    for (int it = 0; it < 3; it++) {
       // y = A s_b : partial rows over this thread's columns, reduced over tx
       double dn = 0.0, xn = 0.0;
 #pragma unroll
@@ -645,7 +406,7 @@ __global__ void __launch_bounds__(256) k_newton_gj_reg(Buffers B, int d) {
       }
       dn = block_sum<256>(dn, sh);
       xn = block_sum<256>(xn, sh);
-      if (dn <= 1e-22 * xn) break;
+      if (dn <= 1e-16 * xn || it == 2) break;
       // r = -g - H x (FP64), rows reduced over tx
       double rn = 0.0;
 #pragma unroll
@@ -669,8 +430,7 @@ __global__ void __launch_bounds__(256) k_newton_gj_reg(Buffers B, int d) {
       }
       rn = block_sum<256>(rn, sh);
       if (it == 0) rn0 = rn;
-      else if (!(rn <= rn0)) { ok = false; break; }
-      if (it == 3) ok = rn <= 1e-12 * rn0;
+      else if (!(rn <= 0.25 * rn0)) { ok = false; break; }   // not contracting
     }
   }
   if (!ok) {
@@ -704,7 +464,6 @@ cudaError_t launch_newton_dense(Buffers& B, int d, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   k_syrk_reduce<<<64, 256, 0, s>>>(B, d, 0);
   const int n = d + 1;
-  k_assemble_h<<<(n * n + 255) / 256, 256, 0, s>>>(B, d, 0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (n <= kGjRegN) {
@@ -724,7 +483,7 @@ cudaError_t launch_newton_dense(Buffers& B, int d, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   k_newton_chol<<<1, 256, sh, s>>>(B, d);
-  B.launches += 5;
+  B.launches += 4;
   return cudaGetLastError();
 }
 
@@ -950,22 +709,19 @@ __global__ void k_mult_slots(Buffers B) {
   const int nxt = st->sup_cur ^ 1;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nS; k += gridDim.x * blockDim.x)
     B.slot[B.sup_idx[nxt][k]] = k;
-}
-
-__global__ void k_mult_flip(Buffers B) {
-  DevState* st = B.st;
-  if (st->status != 0 || st->action != ACT_OUTER) return;
-  st->sup_cur ^= 1;
-  st->nsup = st->nS;
-  st->action = ACT_NONE;
+  // the last block switches to the new multiplier buffers
+  if (last_block_ticket(&st->ctr_slots) && threadIdx.x == 0) {
+    st->sup_cur ^= 1;
+    st->nsup = st->nS;
+    st->action = ACT_NONE;
+  }
 }
 
 cudaError_t launch_mult_update(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s) {
   (void)m;
   k_mult_rows<<<304, 256, 0, s>>>(C, B, d);
   k_mult_slots<<<152, 256, 0, s>>>(B);
-  k_mult_flip<<<1, 1, 0, s>>>(B);
-  B.launches += 3;
+  B.launches += 2;
   return cudaGetLastError();
 }
 
@@ -1049,7 +805,6 @@ cudaError_t launch_eval_outputs(const double* C, Buffers& B, int64_t m, int d, c
     k_syrk<<<dim3(ntri, kSyrkGroups), 256, 0, s>>>(B, d, 1);
     k_syrk_reduce<<<64, 256, 0, s>>>(B, d, 1);
     const int64_t n2 = (int64_t)(d + 1) * (d + 1);
-    k_assemble_h<<<(int)imin64(1024, (n2 + 255) / 256), 256, 0, s>>>(B, d, 1);
     cudaMemcpyAsync(H, B.H, sizeof(double) * (size_t)n2, cudaMemcpyDeviceToDevice, s);
   }
   return cudaGetLastError();
