@@ -237,12 +237,11 @@ def main():
     ok = sum(1 for e in relerr if e <= 1e-8) if r_ref else args.steps
     value, tot_ms, ok_all = aggregate(dist, sum(lat), ok, device="cuda")
 
-    # roofline of the dominant kernel, k_screen (the full FP32 pass over all
-    # balls): algorithmic bytes per launch / mean event-timed launch duration
-    d4 = (d + 3) // 4
+    # roofline of the dominant kernel, k_screen (the full pass over all balls,
+    # streaming the FP16 shadow): bytes per launch / mean event-timed duration
     pass_launches = max(st["pass_launches"], 1)
     avg_ms = st["pass_ms"] / pass_launches
-    bytes_per_launch = m * (16 * d4 + 4 + 4)
+    bytes_per_launch = st["pass_bytes"] // pass_launches
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
 
@@ -274,7 +273,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "m": int(m), "d": int(d), "tol": 1e-10,
-                       "l2": "inputs (1.6 GB) larger than L2; no flush",
+                       "l2": f"inputs ({C.nbytes / 1e9:.2f} GB FP64, {bytes_per_launch / 1e9:.2f} GB per screen) larger than L2; no flush",
                        "parallelism": f"replicas x{world}"},
             "p50_ms": statistics.median(lat), "p99_ms": float(np.percentile(lat, 99)),
             "max_relerr": max(relerr) if relerr else None, "solves_ok": ok_all,

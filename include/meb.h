@@ -89,6 +89,10 @@ typedef struct {
     double pass_ms;          /* their summed device time, milliseconds   */
     int64_t pass_balls;      /* balls they streamed (m per launch)       */
     int64_t pass_fp64_rows;  /* rows they evaluated in FP64              */
+    int64_t pass_bytes;      /* bytes they streamed: per ball the shadow
+                                row, 16*ceil(d/8) + 4 (FP16 and its norm,
+                                solves) or 16*ceil(d/4) (FP32), + 4
+                                (radius) + 4 (multiplier slot)             */
 } meb_stats;
 
 /* Create a context on `device`, issuing work on `cuda_stream` (a cudaStream_t;

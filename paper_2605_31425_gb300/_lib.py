@@ -44,7 +44,7 @@ class MebInfo(ct.Structure):
 class MebStats(ct.Structure):
     _fields_ = [
         ("kernel_launches", ct.c_int64), ("pass_launches", ct.c_int64), ("pass_ms", ct.c_double),
-        ("pass_balls", ct.c_int64), ("pass_fp64_rows", ct.c_int64),
+        ("pass_balls", ct.c_int64), ("pass_fp64_rows", ct.c_int64), ("pass_bytes", ct.c_int64),
     ]
 
 

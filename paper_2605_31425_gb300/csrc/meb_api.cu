@@ -44,6 +44,7 @@ struct meb_ctx {
   // tick loop: 0 = graph of kUnrollTicks ticks relaunched until the controller
   // stops (default), 1 = host-driven ticks, 2 = graph with a while-node
   int loop_mode = 0;
+  bool screen_fp32 = false;   // solves screen the FP16 shadow unless set
   cudaEvent_t ev[2] = {nullptr, nullptr};
   meb_stats stats{};
   int prof_screens = 0;
@@ -77,7 +78,7 @@ static int fail(meb_ctx* ctx, int code, const char* fmt, ...) {
 
 static void free_buffers(meb_ctx* ctx) {
   Buffers& B = ctx->B;
-  void* ptrs[] = {B.X32, B.R32, B.slot, B.sup_idx[0], B.sup_idx[1], B.sup_u[0], B.sup_u[1],
+  void* ptrs[] = {B.X32, B.X16, B.XN16, B.R32, B.slot, B.sup_idx[0], B.sup_idx[1], B.sup_u[0], B.sup_u[1],
                   B.sup_v[0], B.sup_v[1], B.part_flag, B.part, B.cand_cnt, B.cand_idx,
                   B.unc_cnt, B.unc_idx, B.unc_slot, B.vlb_part,
                   B.cand_case, B.cand_a, B.cand_n, B.cand_u, B.S_idx, B.S_case, B.S_a, B.S_n,
@@ -92,6 +93,9 @@ static void free_buffers(meb_ctx* ctx) {
   B.launches = launches;
   ctx->buf_m = 0;
   ctx->buf_d = 0;
+  // the captured tick graph holds the freed pointers: rebuild it on next use
+  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+  if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
 }
 
 template <typename T>
@@ -120,6 +124,8 @@ static int ensure_buffers(meb_ctx* ctx, int64_t m, int d) {
   B.nblk_cap = nblk;
   B.hpart_cap = hp;
   CK(dalloc(&B.X32, (size_t)d4 * m_pad));
+  CK(dalloc(&B.X16, (size_t)((d4 + 1) / 2) * m_pad));
+  CK(dalloc(&B.XN16, (size_t)m_pad));
   CK(dalloc(&B.R32, (size_t)m_pad));
   CK(dalloc(&B.slot, (size_t)m));
   for (int k = 0; k < 2; k++) {
@@ -258,6 +264,8 @@ int meb_create(meb_ctx** out, int device, void* cuda_stream) {
     const char* lm = getenv("MEB_TICK_LOOP");
     if (lm && !strcmp(lm, "host")) ctx->loop_mode = 1;
     if (lm && !strcmp(lm, "while")) ctx->loop_mode = 2;
+    const char* sp = getenv("MEB_SCREEN");   // "fp32": solves screen the FP32 shadow
+    ctx->screen_fp32 = sp && !strcmp(sp, "fp32");
   }
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_st, sizeof(DevState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_scal, 64 * sizeof(double));
@@ -372,6 +380,7 @@ static int solve_graph(meb_ctx* ctx, const double* C, const double* R, int64_t m
   const int mode = ctx->loop_mode;
   const int prof = ctx->profiling;
   if (ctx->gexec && ctx->gkey[0] == C && ctx->gkey[1] == R && ctx->gkey[2] == B.st &&
+      ctx->gkey[3] == (const void*)(B.use_x16 ? (const void*)B.X16 : (const void*)B.X32) &&
       ctx->gm == m && ctx->gd == d && ctx->gmode == mode && ctx->gprof == prof)
     return MEB_OK;
   if (prof && !ctx->gev[0])
@@ -421,6 +430,7 @@ static int solve_graph(meb_ctx* ctx, const double* C, const double* R, int64_t m
   }
   CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
   ctx->gkey[0] = C; ctx->gkey[1] = R; ctx->gkey[2] = B.st;
+  ctx->gkey[3] = B.use_x16 ? (const void*)B.X16 : (const void*)B.X32;
   ctx->gm = m; ctx->gd = d; ctx->gmode = mode; ctx->gprof = prof;
   return MEB_OK;
 }
@@ -496,12 +506,18 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   double sc = ldexp(1.0, ex);
   if (sc / 2.0 >= r0) sc /= 2.0;
   CK(cudaMemsetAsync(B.slot, 0xff, sizeof(int) * (size_t)m, s));
+  B.use_x16 = !ctx->screen_fp32;
+  if (B.use_x16) CK(launch_shadow16(B, m, d, 1.0 / sc, s));
   host_state_defaults(*ctx->h_st, m, d, P, sc);
   ctx->h_st->rt_abs = r0;   // initial radius; k_state_init scales it
   CK(cudaMemcpyAsync(B.st, ctx->h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
   CK(launch_state_init(B, d, s));
   const bool dense = ctx->h_st->dense;
   ctx->prof_screens = 0;
+  // per ball: the shadow row (FP16: 16 bytes per 8 coordinates, + 4 for its
+  // squared norm; FP32: 16 bytes per 4 coordinates), the FP32 radius, the slot
+  const int64_t d4 = (d + 3) / 4;
+  const int64_t pass_bytes = m * (B.use_x16 ? 16 * ((d4 + 1) / 2) + 12 : 16 * d4 + 8);
 
   const int64_t max_ticks =
       (int64_t)P.max_outer * (P.max_ssn + 2) * (P.max_backtrack + 2) + 16;
@@ -536,6 +552,7 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
             ctx->stats.pass_ms += ms;
             ctx->stats.pass_launches += 1;
             ctx->stats.pass_balls += m;
+            ctx->stats.pass_bytes += pass_bytes;
           }
         }
         if (ctx->h_st->status != 0) break;
@@ -557,6 +574,7 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
         ctx->stats.pass_ms += ms;
         ctx->stats.pass_launches += 1;
         ctx->stats.pass_balls += m;
+        ctx->stats.pass_bytes += pass_bytes;
         ctx->stats.pass_fp64_rows += (int64_t)ctx->h_st->last[P_N64];
       }
       ctx->prof_screens = ctx->h_st->screens;
@@ -662,6 +680,7 @@ extern "C" int meb_eval_alm(meb_ctx* ctx, const double* centers, const double* r
   CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
   CK(launch_shadow(C, R, m, d, B, B.vec.o, B.vec.c0, ctx->d_flags, s));
   CK(cudaMemsetAsync(B.slot, 0xff, sizeof(int) * (size_t)m, s));
+  B.use_x16 = false;   // unscaled data (s = 1): the FP32 shadow
   meb_params P;
   meb_params_default(&P);
   P.sigma0 = sigma;

@@ -132,4 +132,21 @@ __device__ __forceinline__ void set_trial(DevState* st, const DevVecs& V, int d,
   __syncthreads();
 }
 
+// FP16 shadow (scaled by 1/s): x16 = fl16(x32 / s) with x32 the FP32 shadow.
+// Per element |x/s - x16| <= kHalfU |x16| + kHalfAbs (normal and subnormal
+// halves), so ||x/s - x16_i|| <= kHalfU ||x16_i|| + sqrt(k4) kHalfAbs.
+constexpr float kHalfU = 4.8828125e-4f + 1.001f * kShadowU;   // 2^-11 + shadow error
+constexpr float kHalfAbs = 2.99e-8f;                            // 2^-25 (1 + shadow error)
+
+__device__ __forceinline__ float dist_ub16(float S, float N, float yn, int k4) {
+  return (sqrtf(S) + kHalfU * sqrtf(N) + kShadowU * yn + sqrtf((float)k4) * kHalfAbs) *
+             (1.0f + (float)(k4 + 16) * kU32) + 1e-30f;
+}
+__device__ __forceinline__ float dist_lb16(float S, float N, float yn, int k4) {
+  const float v = sqrtf(S) * (1.0f - (float)(k4 + 16) * kU32) -
+                  (kHalfU * sqrtf(N) + kShadowU * yn + sqrtf((float)k4) * kHalfAbs) *
+                      (1.0f + (float)(k4 + 16) * kU32) - 1e-30f;
+  return v > 0.0f ? v : 0.0f;
+}
+
 }  // namespace meb

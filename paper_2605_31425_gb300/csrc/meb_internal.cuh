@@ -118,6 +118,9 @@ struct Buffers {
   int64_t nblk_cap;
   // shadow
   float4* X32;          // [d4][m_pad]
+  uint4* X16;           // [ceil(d4/2)][m_pad] FP16 shadow scaled by 1/s (meb_solve)
+  float* XN16;          // [m_pad] sum of squares of each ball's X16 row (FP32)
+  bool use_x16;         // host side: the screens read X16
   float* R32;           // [m_pad]
   // multipliers (double buffered)
   int* slot;            // [m]
@@ -165,6 +168,7 @@ struct Buffers {
 int pass_blocks(int64_t m, int d, int* tiles_per_block);
 cudaError_t launch_shadow(const double* C, const double* R, int64_t m, int d, Buffers& B,
                           double* o, double* c0, int* bad, cudaStream_t s);
+cudaError_t launch_shadow16(Buffers& B, int64_t m, int d, double inv_s, cudaStream_t s);
 cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m, int d,
                         cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
                         int log_slot = -1);

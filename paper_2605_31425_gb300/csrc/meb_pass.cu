@@ -17,6 +17,8 @@
 // it contributes exactly nothing).  Every other ball is evaluated in FP64
 // from its original row.  All reductions use fixed block-to-ball maps and
 // fixed-order trees, so results are deterministic.
+#include <cuda_fp16.h>
+
 #include "meb_control.cuh"
 
 namespace meb {
@@ -113,6 +115,53 @@ cudaError_t launch_shadow(const double* C, const double* R, int64_t m, int d, Bu
   return cudaGetLastError();
 }
 
+// FP16 copy of the shadow in scaled units, x16 = fl16(x32 / s) (round to
+// nearest), built once s is known: rows of 8 halves (groups 2k and 2k+1 of
+// the FP32 shadow; zeros past d), layout [ceil(d4/2)][m_pad], and per ball
+// N = sum x16^2 (FP32 fmaf chain, the rounding model of the screen's own
+// sums).  The screens then read 8 bytes per group of 4 and no squares of x.
+// One thread per ball: a warp's reads and writes are 32 consecutive balls of
+// one row.
+__global__ void k_shadow16(const float4* __restrict__ X32, int64_t m_pad, int d4, float inv_s,
+                           uint4* __restrict__ X16, float* __restrict__ XN) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m_pad) return;
+  const int d8 = (d4 + 1) / 2;
+  float n = 0.0f;
+#pragma unroll 2
+  for (int k = 0; k < d8; k++) {
+    const float4 v = X32[(int64_t)(2 * k) * m_pad + i];
+    const float4 u = (2 * k + 1 < d4) ? X32[(int64_t)(2 * k + 1) * m_pad + i]
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    __half2 h[4];
+    h[0] = __floats2half2_rn(v.x * inv_s, v.y * inv_s);
+    h[1] = __floats2half2_rn(v.z * inv_s, v.w * inv_s);
+    h[2] = __floats2half2_rn(u.x * inv_s, u.y * inv_s);
+    h[3] = __floats2half2_rn(u.z * inv_s, u.w * inv_s);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const float2 f = __half22float2(h[q]);
+      n = fmaf(f.x, f.x, n);
+      n = fmaf(f.y, f.y, n);
+    }
+    uint4 o;
+    o.x = *reinterpret_cast<const unsigned*>(&h[0]);
+    o.y = *reinterpret_cast<const unsigned*>(&h[1]);
+    o.z = *reinterpret_cast<const unsigned*>(&h[2]);
+    o.w = *reinterpret_cast<const unsigned*>(&h[3]);
+    X16[(int64_t)k * m_pad + i] = o;
+  }
+  XN[i] = n;
+}
+
+cudaError_t launch_shadow16(Buffers& B, int64_t m, int d, double inv_s, cudaStream_t s) {
+  const int64_t m_pad = ((m + 255) / 256) * 256;
+  k_shadow16<<<(unsigned)(m_pad / 256), 256, 0, s>>>(B.X32, m_pad, (d + 3) / 4, (float)inv_s,
+                                                     B.X16, B.XN16);
+  B.launches += 1;
+  return cudaGetLastError();
+}
+
 // ===========================================================================
 // The pass, in two kernels over the same block -> tiles map (block b takes the
 // tiles [b*T, (b+1)*T) of 256 balls):
@@ -130,6 +179,8 @@ struct PassArgs {
   int d, d4, tiles_per_block;
   int log_slot;
   const float4* X32;
+  const uint4* X16;     // FP16 shadow scaled by 1/s (8 halves per row), or null
+  const float* XN16;    // per ball: FP32 sum of squares of its X16 row
   const float* R32;
   const int* slot;
   const int* sup_idx0; const int* sup_idx1;
@@ -150,7 +201,68 @@ struct PassArgs {
   double* cand_a; double* cand_n; double* cand_u;
 };
 
-__global__ void __launch_bounds__(kPassThreads) k_screen(PassArgs A, Buffers B) {
+// Shadow rows of the screen (one 16-byte load per ball and row): HALF reads
+// the FP16 shadow, 8 halves = 2 groups of 4 coordinates per row, in units
+// scaled by 1/s; otherwise the FP32 shadow, 1 group per row, unscaled.
+template <bool HALF> struct ScreenRaw { using T = float4; static constexpr int kGroups = 1; };
+template <> struct ScreenRaw<true> { using T = uint4; static constexpr int kGroups = 2; };
+constexpr int kScreenBatch = 4;   // rows per register batch (two batches in flight)
+
+__device__ __forceinline__ float2 h2f(unsigned u) {
+  return __half22float2(*reinterpret_cast<const __half2*>(&u));
+}
+
+// rows g .. g+kScreenBatch-1 of a ball (p points at its row g, row stride
+// m_pad); FULL: all of them exist, else only rows < nrows are read
+template <bool HALF, bool FULL>
+__device__ __forceinline__ void load_batch(typename ScreenRaw<HALF>::T* r,
+                                           const typename ScreenRaw<HALF>::T* __restrict__ p,
+                                           int64_t m_pad, int g, int nrows) {
+#pragma unroll
+  for (int q = 0; q < kScreenBatch; q++) {
+    if (FULL || g + q < nrows) r[q] = *p;
+    p += m_pad;
+  }
+}
+
+// S += ||x - y||^2 over coordinate pairs with s_ny = -y (zero past d), in
+// packed FP32x2 adds and fmas (each rounds to nearest, as the scalar ones).
+__device__ __forceinline__ void acc_pair(float2 x, float2 ny, float2& S) {
+  const float2 t = __fadd2_rn(x, ny);
+  S = __ffma2_rn(t, t, S);
+}
+
+// Sums over the batch; for the FP32 shadow also N += ||x||^2 (the FP16
+// shadow's N is precomputed per ball).
+template <bool HALF, bool FULL>
+__device__ __forceinline__ void sum_batch(const typename ScreenRaw<HALF>::T* r,
+                                          const float4* s_ny, int g, int nrows, float2& Sa,
+                                          float2& Sb, float2& Na, float2& Nb) {
+#pragma unroll
+  for (int q = 0; q < kScreenBatch; q++) {
+    if (FULL || g + q < nrows) {
+      if constexpr (HALF) {
+        const uint4 h = r[q];
+        const float4 y0 = s_ny[2 * (g + q)], y1 = s_ny[2 * (g + q) + 1];
+        acc_pair(h2f(h.x), make_float2(y0.x, y0.y), Sa);
+        acc_pair(h2f(h.y), make_float2(y0.z, y0.w), Sb);
+        acc_pair(h2f(h.z), make_float2(y1.x, y1.y), Sa);
+        acc_pair(h2f(h.w), make_float2(y1.z, y1.w), Sb);
+      } else {
+        const float4 v = r[q];
+        const float4 y = s_ny[g + q];
+        const float2 xl = make_float2(v.x, v.y), xh = make_float2(v.z, v.w);
+        acc_pair(xl, make_float2(y.x, y.y), Sa);
+        acc_pair(xh, make_float2(y.z, y.w), Sb);
+        Na = __ffma2_rn(xl, xl, Na);
+        Nb = __ffma2_rn(xh, xh, Nb);
+      }
+    }
+  }
+}
+
+template <bool HALF>
+__global__ void __launch_bounds__(kPassThreads, 4) k_screen(PassArgs A, Buffers B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DevState* st = A.st;
   // reuse_lists: the point is the one of the last screen and only the
@@ -163,14 +275,23 @@ __global__ void __launch_bounds__(kPassThreads) k_screen(PassArgs A, Buffers B) 
   float4* s_y = reinterpret_cast<float4*>(smem_raw);
   __shared__ int s_wc[kPassWarps];
   __shared__ float s_v2[kPassWarps];
+  // scaled units for the FP16 shadow: multiplying by the power of two 1/s is exact
+  const float sc = HALF ? (float)st->inv_s : 1.0f;
   const float4* y4 = reinterpret_cast<const float4*>(A.y32);
-  for (int g = threadIdx.x; g < d4; g += kPassThreads) s_y[g] = y4[g];
+  constexpr int GR = ScreenRaw<HALF>::kGroups;
+  constexpr int NB = kScreenBatch;
+  const int nrows = (d4 + GR - 1) / GR;       // shadow rows per ball
+  for (int g = threadIdx.x; g < nrows * GR; g += kPassThreads) {
+    const float4 y = g < d4 ? y4[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+    s_y[g] = make_float4(-y.x * sc, -y.y * sc, -y.z * sc, -y.w * sc);   // -y, scaled
+  }
   const int cur = st->sup_cur;
   const int nsup = st->nsup;
   const int* sidx = cur ? A.sup_idx1 : A.sup_idx0;
-  const float rq = st->rq32, yn = st->yn32;
+  const float rq = st->rq32 * sc, yn = st->yn32 * sc;
+  const float unsc = HALF ? (float)st->s : 1.0f;
   float v2sum = 0.0f;
-  const int k4 = 4 * d4;
+  const int k4 = 4 * GR * nrows;   // terms of each sum (padding terms are exact zeros)
   __syncthreads();
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t ntiles = (A.m + kPassThreads - 1) / kPassThreads;
@@ -181,51 +302,51 @@ __global__ void __launch_bounds__(kPassThreads) k_screen(PassArgs A, Buffers B) 
   for (int64_t tile = t0; tile < t1; tile++) {
     const int64_t i = tile * kPassThreads + tid;
     bool need = false;
-    int myslot = -1;
     if (i < A.m) {
+      // the shadow row is read for every ball (support balls are few): its
+      // first batch and the per-ball scalars go out together
+      using Raw = typename ScreenRaw<HALF>::T;
+      const Raw* xp = (HALF ? reinterpret_cast<const Raw*>(A.X16)
+                            : reinterpret_cast<const Raw*>(A.X32)) + i;
+      Raw ra[NB], rb[NB];
       const int sl = A.slot[i];
-      if ((unsigned)sl < (unsigned)nsup && sidx[sl] == (int)i) myslot = sl;
-      if (myslot >= 0) {
-        need = true;
+      const float r32 = A.R32[i] * sc;
+      const float nx = HALF ? A.XN16[i] : 0.0f;
+      const int64_t step = (int64_t)NB * A.m_pad;
+      float2 Sa = make_float2(0.f, 0.f), Sb = Sa, Na = Sa, Nb = Sa;
+      // two register batches in flight: load the next while summing this one
+      if (NB <= nrows) load_batch<HALF, true>(ra, xp, A.m_pad, 0, nrows);
+      else load_batch<HALF, false>(ra, xp, A.m_pad, 0, nrows);
+      for (int g = 0;;) {
+        xp += step;
+        if (g + 2 * NB <= nrows) load_batch<HALF, true>(rb, xp, A.m_pad, g + NB, nrows);
+        else if (g + NB < nrows) load_batch<HALF, false>(rb, xp, A.m_pad, g + NB, nrows);
+        if (g + NB <= nrows) sum_batch<HALF, true>(ra, s_y, g, nrows, Sa, Sb, Na, Nb);
+        else sum_batch<HALF, false>(ra, s_y, g, nrows, Sa, Sb, Na, Nb);
+        g += NB;
+        if (g >= nrows) break;
+        xp += step;
+        if (g + 2 * NB <= nrows) load_batch<HALF, true>(ra, xp, A.m_pad, g + NB, nrows);
+        else if (g + NB < nrows) load_batch<HALF, false>(ra, xp, A.m_pad, g + NB, nrows);
+        if (g + NB <= nrows) sum_batch<HALF, true>(rb, s_y, g, nrows, Sa, Sb, Na, Nb);
+        else sum_batch<HALF, false>(rb, s_y, g, nrows, Sa, Sb, Na, Nb);
+        g += NB;
+        if (g >= nrows) break;
+      }
+      const float S = (Sa.x + Sa.y) + (Sb.x + Sb.y);
+      const float N = HALF ? nx : (Na.x + Na.y) + (Nb.x + Nb.y);
+      if ((unsigned)sl < (unsigned)nsup && sidx[sl] == (int)i) {
+        need = true;   // the ball holds a multiplier
       } else {
         // certify ||c_i - c|| <= r - r_i from the shadows
-        const float4* xp = A.X32 + i;
-        float S0 = 0.f, S1 = 0.f, N0 = 0.f, N1 = 0.f;
-        int g = 0;
-        for (; g + 4 <= d4; g += 4) {
-          float4 xa[4];
-#pragma unroll
-          for (int q = 0; q < 4; q++) xa[q] = xp[(int64_t)(g + q) * A.m_pad];
-#pragma unroll
-          for (int q = 0; q < 4; q++) {
-            const float4 ya = s_y[g + q];
-            float t;
-            float& S = (q & 1) ? S1 : S0;
-            float& N = (q & 1) ? N1 : N0;
-            t = xa[q].x - ya.x; S = fmaf(t, t, S); N = fmaf(xa[q].x, xa[q].x, N);
-            t = xa[q].y - ya.y; S = fmaf(t, t, S); N = fmaf(xa[q].y, xa[q].y, N);
-            t = xa[q].z - ya.z; S = fmaf(t, t, S); N = fmaf(xa[q].z, xa[q].z, N);
-            t = xa[q].w - ya.w; S = fmaf(t, t, S); N = fmaf(xa[q].w, xa[q].w, N);
-          }
-        }
-        for (; g < d4; g++) {
-          const float4 xa = xp[(int64_t)g * A.m_pad];
-          const float4 ya = s_y[g];
-          float t;
-          t = xa.x - ya.x; S0 = fmaf(t, t, S0); N0 = fmaf(xa.x, xa.x, N0);
-          t = xa.y - ya.y; S0 = fmaf(t, t, S0); N0 = fmaf(xa.y, xa.y, N0);
-          t = xa.z - ya.z; S0 = fmaf(t, t, S0); N0 = fmaf(xa.z, xa.z, N0);
-          t = xa.w - ya.w; S0 = fmaf(t, t, S0); N0 = fmaf(xa.w, xa.w, N0);
-        }
-        const float r32 = A.R32[i];
-        const float ub = dist_ub(S0 + S1, N0 + N1, yn, k4);
+        const float ub = HALF ? dist_ub16(S, N, yn, k4) : dist_ub(S, N, yn, k4);
         const float lb = (rq - r32) - 6.0f * kU32 * (fabsf(rq) + fabsf(r32)) - 1e-30f;
         need = !(ub <= lb);
         if (need) {
           // violation ||c_i - c|| + r_i - r >= D_lb + r32 - rq - margins; with zero
-          // multipliers ||Pi(z_i)||^2 >= max(0, violation / s)^2 / 2
-          const float dl = dist_lb(S0 + S1, N0 + N1, yn, k4);
-          const float v = (dl + r32 - rq) - 3.0f * kU32 * (dl + fabsf(r32) + fabsf(rq));
+          // multipliers ||Pi(z_i)||^2 >= max(0, violation / s)^2 / 2 (summed unscaled)
+          const float dl = HALF ? dist_lb16(S, N, yn, k4) : dist_lb(S, N, yn, k4);
+          const float v = ((dl + r32 - rq) - 3.0f * kU32 * (dl + fabsf(r32) + fabsf(rq))) * unsc;
           if (v > 0.0f) v2sum = fmaf(v, v, v2sum);
         }
       }
@@ -426,7 +547,11 @@ static int screen_resident_blocks(int d4) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_screen, kPassThreads, 16 * (size_t)d4);
+    int per2 = 0;
+    const size_t sh1 = 16 * (size_t)(2 * ((d4 + 1) / 2));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_screen<false>, kPassThreads, sh1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_screen<true>, kPassThreads, sh1);
+    if (per2 < per) per = per2;
     if (per < 1) per = 1;
     if (sms < 1) sms = 1;
     cached = sms * per;
@@ -453,7 +578,7 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
   A.m_pad = ((m + 255) / 256) * 256;
   A.d = d; A.d4 = d4;
   const int nb = pass_blocks(m, d, &A.tiles_per_block);
-  A.X32 = B.X32; A.R32 = B.R32; A.slot = B.slot;
+  A.X32 = B.X32; A.X16 = B.use_x16 ? B.X16 : nullptr; A.XN16 = B.XN16; A.R32 = B.R32; A.slot = B.slot;
   A.sup_idx0 = B.sup_idx[0]; A.sup_idx1 = B.sup_idx[1];
   A.sup_u0 = B.sup_u[0]; A.sup_u1 = B.sup_u[1];
   A.sup_v0 = B.sup_v[0]; A.sup_v1 = B.sup_v[1];
@@ -463,10 +588,12 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
   A.part_flag = B.part_flag; A.part = B.part;
   A.cand_cnt = B.cand_cnt; A.cand_idx = B.cand_idx; A.cand_case = B.cand_case;
   A.cand_a = B.cand_a; A.cand_n = B.cand_n; A.cand_u = B.cand_u;
-  const size_t sh1 = 16 * (size_t)d4;
+  const size_t sh1 = 16 * (size_t)(2 * ((d4 + 1) / 2));   // -y padded to whole FP16 rows
   cudaError_t e;
   if (sh1 > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh1);
+    e = cudaFuncSetAttribute(k_screen<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh1);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_screen<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh1);
     if (e != cudaSuccess) return e;
   }
   // cudaEventRecordExternal: inside a stream capture the records become event
@@ -475,7 +602,8 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
   if (ev0 || ev1) cudaStreamIsCapturing(s, &cap);
   const unsigned evf = (cap == cudaStreamCaptureStatusActive) ? cudaEventRecordExternal : 0u;
   if (ev0) cudaEventRecordWithFlags(ev0, s, evf);
-  k_screen<<<nb, kPassThreads, sh1, s>>>(A, B);
+  if (A.X16) k_screen<true><<<nb, kPassThreads, sh1, s>>>(A, B);
+  else k_screen<false><<<nb, kPassThreads, sh1, s>>>(A, B);
   if (ev1) cudaEventRecordWithFlags(ev1, s, evf);
   const size_t sh2 = 8 * (size_t)d;
   if (sh2 > 48 * 1024) {

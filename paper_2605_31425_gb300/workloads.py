@@ -126,6 +126,8 @@ def workload(name: str):
         return gaussian(10_000, 10, 1001, 0.1)
     if name == "cube_m2e6_d100":
         return cube(2_000_000, 100, 1002, 0.05)
+    if name == "cube_m1e6_d100":   # half-size cube instance for counter captures
+        return cube(1_000_000, 100, 1012, 0.05)
     if name == "sphere_m2e5_d2000":
         C, R, _ = sphere(200_000, 2000, 1003)
         return C, R

@@ -196,6 +196,24 @@ def test_device_pointer_path():
     assert np.array_equal(g["active"].cpu().numpy(), h["active"])
 
 
+def test_screen_shadows_agree(monkeypatch):
+    """Solves screen the FP16 shadow; MEB_SCREEN=fp32 screens the FP32 one.
+    Both certificates only decide which balls skip the FP64 evaluation, so the
+    two solves agree to the solve tolerance and keep the same active set."""
+    C, R = workloads.cube(30_000, 40, 23, 0.05)
+    monkeypatch.setenv("MEB_SCREEN", "fp32")
+    c32 = meb.Context(0)
+    monkeypatch.delenv("MEB_SCREEN", raising=False)
+    c16 = meb.Context(0)
+    a = meb.solve(C, R, ctx=c32)
+    b = meb.solve(C, R, ctx=c16)
+    ref = oracle.solve(C, R)
+    for res in (a, b):
+        assert res["status"] == 0 and res["kkt_max"] <= 1e-10
+        assert abs(res["r"] - ref["r"]) <= 1e-8 * ref["r"]
+    assert np.array_equal(a["active"], b["active"])
+
+
 def test_tick_loops_agree(monkeypatch):
     """The graph-batched tick loop (default), the host-driven loop and the
     while-node graph run the same kernels in the same order: bit-identical."""
