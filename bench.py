@@ -278,6 +278,8 @@ def main():
             "p50_ms": statistics.median(lat), "p99_ms": float(np.percentile(lat, 99)),
             "max_relerr": max(relerr) if relerr else None, "solves_ok": ok_all,
             "passes_per_solve": res["passes"], "ssn_per_solve": res["ssn_iters"],
+            "newton_per_solve": {"inverses": res["newton_inverses"], "fp64": res["newton_fp64"]},
+            "fp64_rows_per_pass": res["fp64_rows"] / max(res["passes"], 1),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "k_screen", "bytes_per_launch": bytes_per_launch,

@@ -76,6 +76,8 @@ typedef struct {
     int64_t fp64_rows;   /* ball rows evaluated in FP64 over all passes                */
     int32_t outer_iters, ssn_iters, cg_iters, passes, backtracks;
     int32_t status;      /* 0 converged, 1 iteration cap                               */
+    int32_t newton_inverses; /* dense Newton systems: FP32 Gauss-Jordan inverses of H  */
+    int32_t newton_fp64; /* dense Newton systems that fell back to FP64 Cholesky       */
 } meb_info;
 
 /* Measurement counters of a context (no counterpart in the paper: they

@@ -38,6 +38,7 @@ class MebInfo(ct.Structure):
         ("n_active", ct.c_int64), ("fp64_rows", ct.c_int64),
         ("outer_iters", ct.c_int32), ("ssn_iters", ct.c_int32), ("cg_iters", ct.c_int32),
         ("passes", ct.c_int32), ("backtracks", ct.c_int32), ("status", ct.c_int32),
+        ("newton_inverses", ct.c_int32), ("newton_fp64", ct.c_int32),
     ]
 
 
@@ -234,7 +235,8 @@ def solve(centers, radii, tol: float = 0.0, params: MebParams | None = None,
         kkt=list(info.kkt), kkt_max=info.kkt_max, delta_max=info.delta_max, scale=info.scale,
         fp64_rows=int(info.fp64_rows), outer_iters=info.outer_iters, ssn_iters=info.ssn_iters,
         cg_iters=info.cg_iters, passes=info.passes, backtracks=info.backtracks,
-        status=info.status, rc=rc,
+        status=info.status, rc=rc, newton_inverses=info.newton_inverses,
+        newton_fp64=info.newton_fp64,
     )
 
 

@@ -78,7 +78,7 @@ static int fail(meb_ctx* ctx, int code, const char* fmt, ...) {
 
 static void free_buffers(meb_ctx* ctx) {
   Buffers& B = ctx->B;
-  void* ptrs[] = {B.X32, B.X16, B.XN16, B.R32, B.slot, B.sup_idx[0], B.sup_idx[1], B.sup_u[0], B.sup_u[1],
+  void* ptrs[] = {B.X32, B.X16, B.XN16, B.Hhi, B.Hlo, B.R32, B.slot, B.sup_idx[0], B.sup_idx[1], B.sup_u[0], B.sup_u[1],
                   B.sup_v[0], B.sup_v[1], B.part_flag, B.part, B.cand_cnt, B.cand_idx,
                   B.unc_cnt, B.unc_idx, B.unc_slot, B.vlb_part,
                   B.cand_case, B.cand_a, B.cand_n, B.cand_u, B.S_idx, B.S_case, B.S_a, B.S_n,
@@ -126,6 +126,8 @@ static int ensure_buffers(meb_ctx* ctx, int64_t m, int d) {
   CK(dalloc(&B.X32, (size_t)d4 * m_pad));
   CK(dalloc(&B.X16, (size_t)((d4 + 1) / 2) * m_pad));
   CK(dalloc(&B.XN16, (size_t)m_pad));
+  CK(dalloc(&B.Hhi, (size_t)(d + 1 <= kMaxDenseN ? n1 * n1 : 1)));
+  CK(dalloc(&B.Hlo, (size_t)(d + 1 <= kMaxDenseN ? n1 * n1 : 1)));
   CK(dalloc(&B.R32, (size_t)m_pad));
   CK(dalloc(&B.slot, (size_t)m));
   for (int k = 0; k < 2; k++) {
@@ -641,6 +643,8 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
     info->passes = S.tot_passes;
     info->backtracks = S.tot_bt;
     info->status = S.status == 1 ? 0 : 1;
+    info->newton_inverses = S.gj_inverses;
+    info->newton_fp64 = S.fp64_solves;
   }
   return S.status == 1 ? MEB_OK : fail(ctx, MEB_ENOTCONV, "iteration cap reached");
 }

@@ -73,6 +73,7 @@ struct DevState {
   int accept_mode;             // 1: accepted, go to the stop test; 2: accepted, outer forced
   int need_fp64_solve;         // FP32 inverse + refinement failed: FP64 Cholesky
   int fp64_solves;             // count of FP64 Cholesky fallbacks
+  int gj_inverses;             // count of FP32 Gauss-Jordan inverses
   int early_rejects;           // trials rejected by the certified lower bound
   int reuse_lists;             // next pass: same point, new multipliers (skip the screen)
   int64_t ticks, max_ticks;    // controller ticks of the device-resident loop and their cap
@@ -120,6 +121,8 @@ struct Buffers {
   float4* X32;          // [d4][m_pad]
   uint4* X16;           // [ceil(d4/2)][m_pad] FP16 shadow scaled by 1/s (meb_solve)
   float* XN16;          // [m_pad] sum of squares of each ball's X16 row (FP32)
+  float* Hhi;           // [n1 x n1] fl32(H)
+  float* Hlo;           // [n1 x n1] fl32(H - Hhi)
   bool use_x16;         // host side: the screens read X16
   float* R32;           // [m_pad]
   // multipliers (double buffered)

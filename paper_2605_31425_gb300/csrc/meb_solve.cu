@@ -120,6 +120,14 @@ __global__ void k_syrk_reduce(Buffers B, int d, int force) {
     }
     B.H[(int64_t)i * n1 + l] = h;
     B.H[(int64_t)l * n1 + i] = h;
+    // the FP32 pair hi + lo = h to 2^-48 relative (Gauss-Jordan and its
+    // double-float residual)
+    const float hi = __double2float_rn(h);
+    const float lo = __double2float_rn(h - (double)hi);
+    B.Hhi[(int64_t)i * n1 + l] = hi;
+    B.Hhi[(int64_t)l * n1 + i] = hi;
+    B.Hlo[(int64_t)i * n1 + l] = lo;
+    B.Hlo[(int64_t)l * n1 + i] = lo;
   }
 }
 
@@ -199,6 +207,31 @@ __global__ void __launch_bounds__(256) k_newton_chol(Buffers B, int d) {
   }
   gd = block_sum<256>(gd, sh);
   if (threadIdx.x == 0) {
+    st->fp64_solves += 1;
+    st->gdx = gd;
+    st->eta = 1.0;
+    st->phase = 1;
+    st->bt = 0;
+    st->action = ACT_TRIAL;
+  }
+  __syncthreads();
+  set_trial(st, V, d, sh);
+}
+
+// The Newton direction dx (in shared memory) becomes the first line-search
+// trial: dx, gdx = g.dx, xt = x + dx and the trial's query shadow.
+__device__ void newton_accept(DevState* st, const DevVecs& V, int d, const double* s_x,
+                              double* sh) {
+  const int n = d + 1;
+  double gd = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    V.dx[k] = s_x[k];
+    gd += V.g[k] * s_x[k];
+    V.xt[k] = V.x[k] + s_x[k];
+  }
+  gd = block_sum<256>(gd, sh);
+  if (threadIdx.x == 0) {
+    st->need_fp64_solve = 0;
     st->gdx = gd;
     st->eta = 1.0;
     st->phase = 1;
@@ -288,6 +321,7 @@ __global__ void __launch_bounds__(256) k_newton_gj(Buffers B, int d) {
       if (it == 4) ok = rn <= 1e-16 * rn0;
     }
   }
+  if (tid == 0) st->gj_inverses += 1;
   if (!ok) {
     if (tid == 0) st->need_fp64_solve = 1;
     return;
@@ -310,150 +344,240 @@ __global__ void __launch_bounds__(256) k_newton_gj(Buffers B, int d) {
   set_trial(st, V, d, sh);
 }
 
-// Register-blocked variant for n = d + 1 <= 112: a 16 x 16 thread grid, thread
-// (ty, tx) holding the 7 x 7 tile of rows ty + 16 a and columns tx + 16 b in
-// registers.  Each Gauss-Jordan step publishes the old pivot row and column
-// through shared memory and updates all 49 entries independently.
+// Register-blocked variant for n = d + 1 <= 112, on a 16 x 16 thread grid:
+// thread (ty, tx) holds rows ty + 16 i and columns tx + 16 j (i, j < 7) of the
+// matrix in registers, as column pairs for packed FP32x2 arithmetic.  Each
+// Gauss-Jordan pivot publishes the old pivot row and column through shared
+// memory (double-buffered: one barrier per pivot) and updates every entry.
+// H is SPD: no pivoting.
+//
+// FP64 instructions are few on this GPU's FP64 pipe, so the refinement runs
+// in double-float arithmetic: dx = A (-g) is refined with the residual
+// r = -g - H dx, where H = Hhi + Hlo, dx = xh + xl and -g = bh + bl are FP32
+// pairs, products are split exactly with fmaf and sums taken by TwoSum
+// (about 2^-48 relative).
 constexpr int kGjTile = 7;
 constexpr int kGjRegN = 16 * kGjTile;
 
-__global__ void __launch_bounds__(256) k_newton_gj_reg(Buffers B, int d) {
+// exact a + b = s + e (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// s + l += (hh + hl)(xh + xl), dropping hl xl (2^-48 relative)
+__device__ __forceinline__ void df_mac(float hh, float hl, float xh, float xl, float& s,
+                                       float& l) {
+  const float p = hh * xh;
+  const float e = fmaf(hh, xh, -p);   // exact rounding error of p
+  const float c = fmaf(hh, xl, fmaf(hl, xh, e));
+  float t, err;
+  two_sum(s, p, t, err);
+  s = t;
+  l += err + c;
+}
+
+// block-wide FP32 sums of two values in a fixed order (every thread gets them)
+__device__ __forceinline__ float2 block_sum2f(float a, float b, float2* sh8) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(MEB_FULLMASK, a, o);
+    b += __shfl_xor_sync(MEB_FULLMASK, b, o);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh8[threadIdx.x >> 5] = make_float2(a, b);
+  __syncthreads();
+  float2 t = sh8[0];
+#pragma unroll
+  for (int k = 1; k < 8; k++) { t.x += sh8[k].x; t.y += sh8[k].y; }
+  return t;
+}
+
+__global__ void __launch_bounds__(256, 1) k_newton_gj_reg(Buffers B, int d) {
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_NEWTON) return;
-  __shared__ float s_row[kGjRegN], s_col[kGjRegN], s_b[kGjRegN];
+  __shared__ float s_row[2][kGjRegN], s_col[2][kGjRegN];
+  __shared__ float s_b[kGjRegN], s_bh[kGjRegN], s_bl[kGjRegN], s_xh[kGjRegN], s_xl[kGjRegN];
+  __shared__ float2 s_red[8];
   __shared__ double sh[32];
   __shared__ double s_x[kGjRegN];
   const DevVecs& V = B.vec;
   const int n = d + 1;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float a[kGjTile][kGjTile];
+  // a[i][q] = (A[ty+16i][tx+32q], A[ty+16i][tx+32q+16]); column tx+112 is a zero dummy
+  float2 a[kGjTile][4];
 #pragma unroll
   for (int i = 0; i < kGjTile; i++)
 #pragma unroll
-    for (int j = 0; j < kGjTile; j++) {
+    for (int j = 0; j < 8; j++) {
       const int row = ty + 16 * i, col = tx + 16 * j;
-      a[i][j] = (row < n && col < n) ? f64_to_f32_trunc(B.H[(int64_t)row * n + col]) : 0.0f;
+      const float v = (j == 7) ? 0.0f
+                               : (row < n && col < n) ? B.Hhi[(int64_t)row * n + col]
+                                                      : (row == col ? 1.0f : 0.0f);
+      if (j & 1) a[i][j >> 1].y = v; else a[i][j >> 1].x = v;
     }
-  __syncthreads();
-  bool fail = false;
+  for (int i = tid; i < kGjRegN; i += 256) {
+    const double b = (i < n) ? -V.g[i] : 0.0;   // solve H dx = -g
+    const float bh = __double2float_rn(b);
+    s_bh[i] = bh;
+    s_bl[i] = __double2float_rn(b - (double)bh);
+    s_b[i] = bh;
+    s_xh[i] = 0.0f;
+    s_xl[i] = 0.0f;
+  }
+  bool ok = true;
 #pragma unroll
   for (int kb = 0; kb < kGjTile; kb++) {
-    for (int kk = 0; kk < 16 && !fail; kk++) {
+    for (int kk = 0; kk < 16; kk++) {
       const int k = 16 * kb + kk;
-      if (k >= n) break;
-      if (ty == kk) {
+      if (k < n && ok) {
+        const int bf = k & 1;
+        if (ty == kk) {
 #pragma unroll
-        for (int j = 0; j < kGjTile; j++) s_row[tx + 16 * j] = a[kb][j];
-      }
-      if (tx == kk) {
+          for (int j = 0; j < kGjTile; j++)
+            s_row[bf][tx + 16 * j] = (j & 1) ? a[kb][j >> 1].y : a[kb][j >> 1].x;
+        }
+        if (tx == kk) {
 #pragma unroll
-        for (int i = 0; i < kGjTile; i++) s_col[ty + 16 * i] = a[i][kb];
-      }
-      __syncthreads();
-      const float p = s_row[k];
-      if (!(p > 0.0f) || !isfinite(p)) { fail = true; break; }
-      const float ip = 1.0f / p;
-      float rc[kGjTile], cr[kGjTile];
+          for (int i = 0; i < kGjTile; i++)
+            s_col[bf][ty + 16 * i] = (kb & 1) ? a[i][kb >> 1].y : a[i][kb >> 1].x;
+        }
+        __syncthreads();
+        const float p = s_row[bf][k];
+        ok = (p > 0.0f) && isfinite(p);   // the same for every thread
+        const float ip = __fdividef(1.0f, p);
+        float2 rc[4];
 #pragma unroll
-      for (int j = 0; j < kGjTile; j++) rc[j] = s_row[tx + 16 * j] * ip;
+        for (int q = 0; q < 4; q++) {
+          const float lo = s_row[bf][tx + 32 * q];
+          const float hi = (q < 3) ? s_row[bf][tx + 32 * q + 16] : 0.0f;
+          rc[q] = __fmul2_rn(make_float2(lo, hi), make_float2(ip, ip));
+        }
+        float cr[kGjTile];
 #pragma unroll
-      for (int i = 0; i < kGjTile; i++) cr[i] = s_col[ty + 16 * i];
-#pragma unroll
-      for (int i = 0; i < kGjTile; i++)
-#pragma unroll
-        for (int j = 0; j < kGjTile; j++) a[i][j] = fmaf(-cr[i], rc[j], a[i][j]);
-      if (ty == kk) {   // pivot row: A[k][j] / p, and 1/p on the diagonal
-#pragma unroll
-        for (int j = 0; j < kGjTile; j++) a[kb][j] = (tx + 16 * j == k) ? ip : rc[j];
-      }
-      if (tx == kk) {   // pivot column: -A[i][k] / p off the diagonal
+        for (int i = 0; i < kGjTile; i++) cr[i] = s_col[bf][ty + 16 * i];
 #pragma unroll
         for (int i = 0; i < kGjTile; i++)
-          if (ty + 16 * i != k) a[i][kb] = -cr[i] * ip;
-      }
-      __syncthreads();
-    }
-  }
-  bool ok = !fail;
-  if (ok) {
-    // dx = A (-g); refinement r = -g - H dx (FP64), dx += A r
-    for (int i = tid; i < kGjRegN; i += 256) {
-      s_b[i] = (i < n) ? (float)(-V.g[i]) : 0.0f;
-      s_x[i] = 0.0;
-    }
-    __syncthreads();
-    double rn0 = 0.0;
-    // x0 and at most two corrections: the Newton direction needs a small
-    // relative error, not FP64 accuracy (the stop test, Armijo and KKT use
-    // the FP64 gradient and Psi)
-    for (int it = 0; it < 3; it++) {
-      // y = A s_b : partial rows over this thread's columns, reduced over tx
-      double dn = 0.0, xn = 0.0;
 #pragma unroll
-      for (int i = 0; i < kGjTile; i++) {
-        float t = 0.0f;
-#pragma unroll
-        for (int j = 0; j < kGjTile; j++) t = fmaf(a[i][j], s_b[tx + 16 * j], t);
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(MEB_FULLMASK, t, o);
-        const int row = ty + 16 * i;
-        if (tx == 0 && row < n) {
-          const double xi = s_x[row] + (double)t;
-          s_x[row] = xi;
-          dn += (double)t * (double)t;
-          xn += xi * xi;
-        }
-      }
-      dn = block_sum<256>(dn, sh);
-      xn = block_sum<256>(xn, sh);
-      if (dn <= 1e-16 * xn || it == 2) break;
-      // r = -g - H x (FP64), rows reduced over tx
-      double rn = 0.0;
-#pragma unroll
-      for (int i = 0; i < kGjTile; i++) {
-        const int row = ty + 16 * i;
-        double t = 0.0;
-        if (row < n) {
+          for (int q = 0; q < 4; q++)
+            a[i][q] = __ffma2_rn(make_float2(-cr[i], -cr[i]), rc[q], a[i][q]);
+        if (ty == kk) {   // pivot row: A[k][j] / p, and 1/p on the diagonal
 #pragma unroll
           for (int j = 0; j < kGjTile; j++) {
-            const int col = tx + 16 * j;
-            if (col < n) t = fma(B.H[(int64_t)row * n + col], s_x[col], t);
+            const float rj = (j & 1) ? rc[j >> 1].y : rc[j >> 1].x;
+            const float v = (tx + 16 * j == k) ? ip : rj;
+            if (j & 1) a[kb][j >> 1].y = v; else a[kb][j >> 1].x = v;
           }
         }
+        if (tx == kk) {   // pivot column: -A[i][k] / p off the diagonal
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(MEB_FULLMASK, t, o);
-        if (tx == 0 && row < n) {
-          const double r = -V.g[row] - t;
-          s_b[row] = (float)r;
-          rn += r * r;
+          for (int i = 0; i < kGjTile; i++) {
+            if (ty + 16 * i != k) {
+              const float v = -cr[i] * ip;
+              if (kb & 1) a[i][kb >> 1].y = v; else a[i][kb >> 1].x = v;
+            }
+          }
         }
       }
-      rn = block_sum<256>(rn, sh);
-      if (it == 0) rn0 = rn;
-      else if (!(rn <= 0.25 * rn0)) { ok = false; break; }   // not contracting
     }
   }
+  __syncthreads();
+  if (ok) {
+    // x0 = A (-g) and at most two corrections dx += A r: the Newton direction
+    // needs a small relative error, not FP64 accuracy (the stop test, Armijo
+    // and KKT use the FP64 gradient and Psi)
+    float rn0 = 0.0f;
+    for (int it = 0; it < 3; it++) {
+      // t = A s_b : partial rows over this thread's columns, reduced over tx
+      float tv[kGjTile];
+#pragma unroll
+      for (int i = 0; i < kGjTile; i++) {
+        float2 t2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const float lo = s_b[tx + 32 * q];
+          const float hi = (q < 3) ? s_b[tx + 32 * q + 16] : 0.0f;
+          t2 = __ffma2_rn(a[i][q], make_float2(lo, hi), t2);
+        }
+        tv[i] = t2.x + t2.y;
+      }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < kGjTile; i++) tv[i] += __shfl_xor_sync(MEB_FULLMASK, tv[i], o);
+      float dn = 0.0f, xn = 0.0f;
+      if (tx == 0) {
+#pragma unroll
+        for (int i = 0; i < kGjTile; i++) {
+          const int row = ty + 16 * i;
+          if (row < n) {
+            float h, e;
+            two_sum(s_xh[row], tv[i], h, e);
+            const float l = s_xl[row] + e;
+            const float h2 = h + l;               // renormalise the pair
+            s_xl[row] = l - (h2 - h);
+            s_xh[row] = h2;
+            dn = fmaf(tv[i], tv[i], dn);
+            xn = fmaf(h2, h2, xn);
+          }
+        }
+      }
+      const float2 dx2 = block_sum2f(dn, xn, s_red);   // (barriers: s_xh, s_xl visible)
+      if (dx2.x <= 1e-16f * dx2.y || it == 2) break;
+      // r = -g - H x in double-float, rows reduced over tx
+      float sa[kGjTile], la[kGjTile];
+#pragma unroll
+      for (int i = 0; i < kGjTile; i++) {
+        const int row = ty + 16 * i;
+        sa[i] = 0.0f;
+        la[i] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < kGjTile; j++) {
+          const int col = tx + 16 * j;
+          if (row < n && col < n)
+            df_mac(B.Hhi[(int64_t)row * n + col], B.Hlo[(int64_t)row * n + col], s_xh[col],
+                   s_xl[col], sa[i], la[i]);
+        }
+      }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < kGjTile; i++) {
+          const float so = __shfl_xor_sync(MEB_FULLMASK, sa[i], o);
+          const float lo = __shfl_xor_sync(MEB_FULLMASK, la[i], o);
+          float t, err;
+          two_sum(sa[i], so, t, err);
+          sa[i] = t;
+          la[i] += lo + err;
+        }
+      float rn = 0.0f;
+      if (tx == 0) {
+#pragma unroll
+        for (int i = 0; i < kGjTile; i++) {
+          const int row = ty + 16 * i;
+          if (row < n) {
+            float h, e;
+            two_sum(s_bh[row], -sa[i], h, e);   // exact leading difference
+            const float r = h + ((e + s_bl[row]) - la[i]);
+            s_b[row] = r;
+            rn = fmaf(r, r, rn);
+          }
+        }
+      }
+      const float rr = block_sum2f(rn, 0.0f, s_red).x;   // (barriers: s_b visible)
+      if (it == 0) rn0 = rr;
+      else if (!(rr <= 0.25f * rn0)) { ok = false; break; }   // not contracting
+    }
+  }
+  if (tid == 0) st->gj_inverses += 1;
   if (!ok) {
     if (tid == 0) st->need_fp64_solve = 1;
     return;
   }
-  double gd = 0.0;
-  for (int k = tid; k < n; k += 256) {
-    V.dx[k] = s_x[k];
-    gd += V.g[k] * s_x[k];
-    V.xt[k] = V.x[k] + s_x[k];
-  }
-  gd = block_sum<256>(gd, sh);
-  if (tid == 0) {
-    st->need_fp64_solve = 0;
-    st->gdx = gd;
-    st->eta = 1.0;
-    st->phase = 1;
-    st->bt = 0;
-    st->action = ACT_TRIAL;
-  }
+  for (int i = tid; i < kGjRegN; i += 256) s_x[i] = (double)s_xh[i] + (double)s_xl[i];
   __syncthreads();
-  set_trial(st, V, d, sh);
+  newton_accept(st, V, d, s_x, sh);
 }
 
 cudaError_t launch_newton_dense(Buffers& B, int d, cudaStream_t s) {
