@@ -79,7 +79,7 @@ static int fail(meb_ctx* ctx, int code, const char* fmt, ...) {
 static void free_buffers(meb_ctx* ctx) {
   Buffers& B = ctx->B;
   void* ptrs[] = {B.X32, B.X16, B.XN16, B.Hhi, B.Hlo, B.R32, B.slot, B.sup_idx[0], B.sup_idx[1], B.sup_u[0], B.sup_u[1],
-                  B.sup_v[0], B.sup_v[1], B.part_flag, B.part, B.cand_cnt, B.cand_idx,
+                  B.sup_v[0], B.sup_v[1], B.part_flag, B.part, B.part_cnt, B.cand_cnt, B.cand_idx,
                   B.unc_cnt, B.unc_idx, B.unc_slot, B.vlb_part,
                   B.cand_case, B.cand_a, B.cand_n, B.cand_u, B.S_idx, B.S_case, B.S_a, B.S_n,
                   B.S_u, B.S_t, B.W, B.svec_part, B.hpart, B.H, B.hq, B.colsum_part, B.fe_ub, B.fe_lb,
@@ -139,7 +139,8 @@ static int ensure_buffers(meb_ctx* ctx, int64_t m, int d) {
   const int64_t npb = pass_blocks(m, d, &tpb);
   const int64_t ncand = npb * tpb * 256;
   CK(dalloc(&B.part_flag, (size_t)nblk));
-  CK(dalloc(&B.part, (size_t)nblk * P_COUNT));
+  CK(dalloc(&B.part, (size_t)nblk * P_NREC));
+  CK(dalloc(&B.part_cnt, (size_t)nblk * P_NCNT));
   CK(dalloc(&B.cand_cnt, (size_t)nblk));
   CK(dalloc(&B.unc_cnt, (size_t)nblk));
   CK(dalloc(&B.vlb_part, (size_t)nblk));

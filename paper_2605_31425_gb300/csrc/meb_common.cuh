@@ -27,6 +27,44 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// Transposed warp sum of 8 slots: after log2(32) exchange levels lane L holds
+// the full warp sum of slot (L >> 2) & 7, in a fixed tree order.  9 FP64 adds
+// per lane instead of 8 x 5 for eight separate warp_sum calls.
+__device__ __forceinline__ double warp_sum8_transposed(const double (&v)[8]) {
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  double w4[4], w2[2];
+#pragma unroll
+  for (int p = 0; p < 4; p++) {
+    const double send = b4 ? v[p] : v[p + 4];
+    const double keep = b4 ? v[p + 4] : v[p];
+    w4[p] = keep + __shfl_xor_sync(MEB_FULLMASK, send, 16);
+  }
+#pragma unroll
+  for (int p = 0; p < 2; p++) {
+    const double send = b3 ? w4[p] : w4[p + 2];
+    const double keep = b3 ? w4[p + 2] : w4[p];
+    w2[p] = keep + __shfl_xor_sync(MEB_FULLMASK, send, 8);
+  }
+  const double send = b2 ? w2[0] : w2[1];
+  double w1 = (b2 ? w2[1] : w2[0]) + __shfl_xor_sync(MEB_FULLMASK, send, 4);
+  w1 += __shfl_xor_sync(MEB_FULLMASK, w1, 2);
+  w1 += __shfl_xor_sync(MEB_FULLMASK, w1, 1);
+  return w1;
+}
+
+// Warp max of non-negative doubles on their bit patterns (IEEE order equals
+// integer order for x >= 0): integer instructions only.
+__device__ __forceinline__ double warp_max_nonneg(double v) {
+  long long b = __double_as_longlong(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long t = __shfl_xor_sync(MEB_FULLMASK, b, o);
+    b = t > b ? t : b;
+  }
+  return __longlong_as_double(b);
+}
+
 // Block-wide sum in a fixed tree order; every thread gets the result.
 template <int NT>
 __device__ double block_sum(double v, double* sh) {

@@ -25,6 +25,26 @@ __device__ __forceinline__ bool last_block_ticket(unsigned int* ctr) {
   return s_last != 0;
 }
 
+// The controller bodies work on a shared-memory copy of the state: its
+// scalar logic then waits on shared-memory latency instead of one global
+// round trip per field.  No other block of the kernel touches the state
+// while the last block runs; the copy is written back whole.
+__device__ __forceinline__ DevState* state_in(DevState* g, DevState* s) {
+  static_assert(sizeof(DevState) % 4 == 0, "state copied as 32-bit words");
+  const unsigned* src = reinterpret_cast<const unsigned*>(g);
+  unsigned* dst = reinterpret_cast<unsigned*>(s);
+  for (int k = threadIdx.x; k < (int)(sizeof(DevState) / 4); k += blockDim.x)
+    dst[k] = __ldcg(src + k);
+  __syncthreads();
+  return s;
+}
+__device__ __forceinline__ void state_out(DevState* g, const DevState* s) {
+  __syncthreads();
+  const unsigned* src = reinterpret_cast<const unsigned*>(s);
+  unsigned* dst = reinterpret_cast<unsigned*>(g);
+  for (int k = threadIdx.x; k < (int)(sizeof(DevState) / 4); k += blockDim.x) dst[k] = src[k];
+}
+
 // Outer update (Algorithm 1): (alpha,beta) -= sigma g, KKT_max, sigma rule.
 // Returns the action; thread 0 writes the state.
 __device__ __forceinline__ void do_outer(DevState* st, const DevVecs& V, int d, double* sh) {
@@ -81,19 +101,28 @@ __device__ __forceinline__ void do_outer(DevState* st, const DevVecs& V, int d, 
 // bound Psi_lb <= Psi(trial) (only balls with zero multipliers counted), a
 // trial with Psi_lb above the Armijo threshold is rejected without its FP64
 // rows; the next trial is set as in the controller.
-__device__ __forceinline__ void early_body(const Buffers& B, int d, int nb) {
-  DevState* st = B.st;
+__device__ __forceinline__ void early_body_impl(const Buffers& B, DevState* st, int d, int nb) {
   if (st->phase != 1 || st->eval_only) {
     if (threadIdx.x == 0 && st->action == ACT_TRIAL_EARLY) st->action = ACT_TRIAL;
     return;
   }
   __shared__ double sh[32];
+  __shared__ float shf[8];
   __shared__ int s_rej;
   const DevVecs& V = B.vec;
   const int n1 = d + 1;
-  double t = 0.0;
-  for (int b = threadIdx.x; b < nb; b += 256) t += (double)B.vlb_part[b];
-  t = block_sum<256>(t, sh);
+  // FP32 sum of the non-negative block bounds (its relative rounding, below
+  // nb 2^-24, is inside the 1% kept below)
+  float tf = 0.0f;
+  for (int b = threadIdx.x; b < nb; b += 256) tf += B.vlb_part[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tf += __shfl_xor_sync(MEB_FULLMASK, tf, o);
+  if ((threadIdx.x & 31) == 0) shf[threadIdx.x >> 5] = tf;
+  __syncthreads();
+  float tsum = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; k++) tsum += shf[k];
+  const double t = (double)tsum;
   double dx2 = 0.0;
   for (int k = threadIdx.x; k < n1; k += 256) {
     const double dk = V.xt[k] - V.xk[k];
@@ -136,36 +165,69 @@ __device__ __forceinline__ void early_body(const Buffers& B, int d, int nb) {
   }
 }
 
+__device__ __forceinline__ void early_body(const Buffers& B, int d, int nb) {
+  __shared__ DevState s_st;
+  DevState* st = state_in(B.st, &s_st);
+  early_body_impl(B, st, d, nb);
+  state_out(B.st, st);
+}
+
 // Controller, part A (the last block of k_rows64): reduce the pass partials,
 // form Psi at the trial and take the line-search decision (Algorithm 2).  A rejected trial
 // sets the next trial directly; an accepted one (or the first evaluation of an
 // outer step) asks for the gradient: action ACT_GRAD.
-__device__ __forceinline__ void control_a_body(const Buffers& B, int d, int nb) {
-  DevState* st = B.st;
+__device__ __forceinline__ void control_a_body_impl(const Buffers& B, DevState* st, int d,
+                                                    int nb) {
   const DevVecs& V = B.vec;
   const int n1 = d + 1;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __shared__ double sh[32];
   __shared__ double s_last[P_COUNT];
   __shared__ int s_next;
+  __shared__ int s_list[kMaxPassBlocks];
+  __shared__ int s_wc[8];
   {
-    double acc[P_COUNT];
+    // the blocks that evaluated rows, in block order
+    int nlist = 0;
+    for (int r0 = 0; r0 < nb; r0 += 256) {
+      const int b = r0 + threadIdx.x;
+      const bool f = b < nb && B.part_flag[b];
+      const unsigned msk = __ballot_sync(MEB_FULLMASK, f);
+      if (lane == 0) s_wc[w] = __popc(msk);
+      __syncthreads();
+      int off = nlist, tot = 0;
 #pragma unroll
-    for (int k = 0; k < P_COUNT; k++) acc[k] = 0.0;
-    for (int b = threadIdx.x; b < nb; b += 256) {
-      if (!B.part_flag[b]) continue;
-      const double* p = B.part + (int64_t)b * P_COUNT;
-#pragma unroll
-      for (int k = 0; k < P_COUNT; k++) {
-        const bool ismax = (k == P_KP || k == P_KD || k == P_KC);
-        acc[k] = ismax ? fmax(acc[k], p[k]) : acc[k] + p[k];
+      for (int k = 0; k < 8; k++) {
+        off += (k < w) ? s_wc[k] : 0;
+        tot += s_wc[k];
+      }
+      if (f) s_list[off + __popc(msk & ((1u << lane) - 1u))] = b;
+      nlist += tot;
+      __syncthreads();
+    }
+    // warps 0..4: the FP64 sums; warps 5..7: the maxima (on bit patterns) and
+    // the counts.  Lanes stride over the list, then a fixed warp tree.
+    if (w < P_NSUM) {
+      double t = 0.0;
+      for (int e = lane; e < nlist; e += 32) t += B.part[(int64_t)s_list[e] * P_NREC + w];
+      t = warp_sum(t);
+      if (lane == 0) s_last[w] = t;
+    } else {
+      long long mx = 0;
+      unsigned c = 0;
+      for (int e = lane; e < nlist; e += 32) {
+        const long long b = __double_as_longlong(B.part[(int64_t)s_list[e] * P_NREC + w]);
+        mx = b > mx ? b : mx;
+        c += (unsigned)B.part_cnt[(int64_t)s_list[e] * P_NCNT + (w - P_NSUM)];
+      }
+      const double m = warp_max_nonneg(__longlong_as_double(mx));
+      c = __reduce_add_sync(MEB_FULLMASK, c);
+      if (lane == 0) {
+        s_last[w] = m;
+        s_last[P_NI + (w - P_NSUM)] = (double)c;
       }
     }
-#pragma unroll
-    for (int k = 0; k < P_COUNT; k++) {
-      const bool ismax = (k == P_KP || k == P_KD || k == P_KC);
-      const double r = ismax ? block_max<256>(acc[k], sh) : block_sum<256>(acc[k], sh);
-      if (threadIdx.x == 0) s_last[k] = r;
-    }
+    __syncthreads();
   }
   const double sigma = st->sigma, tos = st->tau / sigma;
   double dx2 = 0.0;
@@ -225,11 +287,17 @@ __device__ __forceinline__ void control_a_body(const Buffers& B, int d, int nb) 
   }
 }
 
+__device__ __forceinline__ void control_a_body(const Buffers& B, int d, int nb) {
+  __shared__ DevState s_st;
+  DevState* st = state_in(B.st, &s_st);
+  control_a_body_impl(B, st, d, nb);
+  state_out(B.st, st);
+}
+
 // Controller, part B (the last block of k_svec, after the support rows were
 // reduced): the gradient at the accepted point, then the relative-type stopping condition
 // (Algorithm 1) and the next action.
-__device__ __forceinline__ void control_b_body(const Buffers& B, int d) {
-  DevState* st = B.st;
+__device__ __forceinline__ void control_b_body_impl(const Buffers& B, DevState* st, int d) {
   const DevVecs& V = B.vec;
   const int n1 = d + 1;
   __shared__ double sh[32];
@@ -299,6 +367,13 @@ __device__ __forceinline__ void control_b_body(const Buffers& B, int d) {
     st->action = ACT_NEWTON;
     st->bt = 0;
   }
+}
+
+__device__ __forceinline__ void control_b_body(const Buffers& B, int d) {
+  __shared__ DevState s_st;
+  DevState* st = state_in(B.st, &s_st);
+  control_b_body_impl(B, st, d);
+  state_out(B.st, st);
 }
 
 }  // namespace meb

@@ -45,6 +45,10 @@ enum : int {
   P_N64,       // rows evaluated in FP64
   P_COUNT
 };
+// block partial records: P_NREC doubles (the sums P_PI2..P_ZMAG, then the
+// maxima P_KP..P_KC) in part[], the three counts as ints in part_cnt[]
+constexpr int P_NSUM = 5, P_NREC = 8, P_NCNT = 3;
+constexpr int kMaxPassBlocks = 2048;   // cap of the pass grid (controller lists)
 
 struct DevState {
   // problem
@@ -132,6 +136,7 @@ struct Buffers {
   double* sup_v[2];     // [m*d]
   // pass outputs
   int* part_flag;       // [nblk]
+  int* part_cnt;        // [nblk][P_NCNT]
   double* part;         // [nblk][P_COUNT]
   int* unc_cnt;         // [nblk] balls each pass block could not certify
   int* unc_idx;         // [ncand] their indices (per-block segments)

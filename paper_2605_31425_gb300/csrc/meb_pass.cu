@@ -195,6 +195,7 @@ struct PassArgs {
   float* vlb_part;      // per block: sum of max(0, certified lower bound of the violation)^2
   int* part_flag;
   double* part;
+  int* part_cnt;
   int* cand_cnt;
   int* cand_idx;
   unsigned char* cand_case;
@@ -399,7 +400,8 @@ __global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A, Buffers B) 
   __shared__ unsigned char s_cc[kPassThreads];
   __shared__ double s_ca[kPassThreads], s_cn[kPassThreads], s_cu[kPassThreads];
   __shared__ int s_wc[kPassWarps];
-  __shared__ double s_wp[kPassWarps][P_COUNT];
+  __shared__ double s_wp[kPassWarps][P_NREC];
+  __shared__ int s_wn[kPassWarps][P_NCNT];
   for (int j = threadIdx.x; j < d; j += kPassThreads) s_ct[j] = A.ct[j];
   const int cur = st->sup_cur;
   const int nsup = st->nsup;
@@ -411,9 +413,10 @@ __global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A, Buffers B) 
   __syncthreads();
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t base = (int64_t)blockIdx.x * A.tiles_per_block * kPassThreads;
-  double acc[P_COUNT];
+  double acc[P_NREC];
 #pragma unroll
-  for (int k = 0; k < P_COUNT; k++) acc[k] = 0.0;
+  for (int k = 0; k < P_NREC; k++) acc[k] = 0.0;
+  int cnt[P_NCNT] = {0, 0, 0};
   int ccount = 0;
   for (int c0 = 0; c0 < n_b; c0 += kPassThreads) {
     const int tot = min(kPassThreads, n_b - c0);
@@ -483,9 +486,9 @@ __global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A, Buffers B) 
       // (r - r_i) u^+ + (c - c_i).v^+ = ap u^+ - sigma f (dl.b), dl.b = pp + dv/sigma
       acc[P_KC] = fmax(acc[P_KC], fabs(ap * up - sf * (pp + dv * inv_sigma)));
       if (cs != CASE_Z) acc[P_ZMAG] += fabs(a) + n;
-      acc[P_NI] += (cs == CASE_I);
-      acc[P_NM] += (cs == CASE_M);
-      acc[P_N64] += 1.0;
+      cnt[0] += (cs == CASE_I);
+      cnt[1] += (cs == CASE_M);
+      cnt[2] += 1;
       s_cf[my] = (cs != CASE_Z);
       s_cc[my] = (unsigned char)cs;
       s_ca[my] = a;
@@ -515,22 +518,42 @@ __global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A, Buffers B) 
     ccount += ctot;
     __syncthreads();
   }
-  // block partial: per-lane accumulators -> warp (fixed tree) -> warps in order
+  // block partial: per-lane accumulators -> warp (fixed trees) -> warps in
+  // order.  Warps that took no entry hold zeros and skip the exchanges.
+  if (32 * w < n_b) {
+    const double v8[8] = {acc[0], acc[1], acc[2], acc[3], acc[4], 0.0, 0.0, 0.0};
+    const double sv = warp_sum8_transposed(v8);
+    if ((lane & 3) == 0 && (lane >> 2) < P_NSUM) s_wp[w][lane >> 2] = sv;
 #pragma unroll
-  for (int k = 0; k < P_COUNT; k++) {
-    const bool ismax = (k == P_KP || k == P_KD || k == P_KC);
-    acc[k] = ismax ? warp_max(acc[k]) : warp_sum(acc[k]);
-  }
-  if (lane == 0) {
+    for (int k = P_NSUM; k < P_NREC; k++) {
+      const double mx = warp_max_nonneg(acc[k]);
+      if (lane == 0) s_wp[w][k] = mx;
+    }
 #pragma unroll
-    for (int k = 0; k < P_COUNT; k++) s_wp[w][k] = acc[k];
+    for (int k = 0; k < P_NCNT; k++) {
+      const int c = (int)__reduce_add_sync(MEB_FULLMASK, (unsigned)cnt[k]);
+      if (lane == 0) s_wn[w][k] = c;
+    }
+  } else if (lane < P_NREC) {
+    s_wp[w][lane] = 0.0;
+    if (lane < P_NCNT) s_wn[w][lane] = 0;
   }
   __syncthreads();
-  if (tid < P_COUNT) {
-    const bool ismax = (tid == P_KP || tid == P_KD || tid == P_KC);
+  if (tid < P_NSUM) {
     double t = 0.0;
-    for (int k = 0; k < kPassWarps; k++) t = ismax ? fmax(t, s_wp[k][tid]) : t + s_wp[k][tid];
-    A.part[(int64_t)blockIdx.x * P_COUNT + tid] = t;
+    for (int k = 0; k < kPassWarps; k++) t += s_wp[k][tid];
+    A.part[(int64_t)blockIdx.x * P_NREC + tid] = t;
+  } else if (tid < P_NREC) {
+    long long t = 0;
+    for (int k = 0; k < kPassWarps; k++) {
+      const long long b = __double_as_longlong(s_wp[k][tid]);
+      t = b > t ? b : t;
+    }
+    A.part[(int64_t)blockIdx.x * P_NREC + tid] = __longlong_as_double(t);
+  } else if (tid >= 32 && tid < 32 + P_NCNT) {
+    int t = 0;
+    for (int k = 0; k < kPassWarps; k++) t += s_wn[k][tid - 32];
+    A.part_cnt[(int64_t)blockIdx.x * P_NCNT + tid - 32] = t;
   }
   if (tid == 0) {
     A.part_flag[blockIdx.x] = 1;
@@ -563,7 +586,8 @@ static int screen_resident_blocks(int d4) {
 int pass_blocks(int64_t m, int d, int* tiles_per_block) {
   const int64_t ntiles = (m + kPassThreads - 1) / kPassThreads;
   const int64_t target = screen_resident_blocks((d + 3) / 4);
-  int64_t tpb = (ntiles + target - 1) / target;
+  const int64_t cap = target < kMaxPassBlocks ? target : kMaxPassBlocks;
+  int64_t tpb = (ntiles + cap - 1) / cap;
   if (tpb < 1) tpb = 1;
   *tiles_per_block = (int)tpb;
   return (int)((ntiles + tpb - 1) / tpb);
@@ -585,7 +609,7 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
   A.st = B.st; A.ct = B.vec.ct; A.y32 = B.vec.y32;
   A.unc_cnt = B.unc_cnt; A.unc_idx = B.unc_idx; A.unc_slot = B.unc_slot;
   A.vlb_part = B.vlb_part;
-  A.part_flag = B.part_flag; A.part = B.part;
+  A.part_flag = B.part_flag; A.part = B.part; A.part_cnt = B.part_cnt;
   A.cand_cnt = B.cand_cnt; A.cand_idx = B.cand_idx; A.cand_case = B.cand_case;
   A.cand_a = B.cand_a; A.cand_n = B.cand_n; A.cand_u = B.cand_u;
   const size_t sh1 = 16 * (size_t)(2 * ((d4 + 1) / 2));   // -y padded to whole FP16 rows
@@ -618,54 +642,47 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
 // ===========================================================================
 // Ordered gather of the pass candidates (block b's segment at b*T*256) into
 // the support list S.
-__global__ void k_compact_S(Buffers B, int nb, int64_t seg) {
+__global__ void __launch_bounds__(256) k_compact_S(Buffers B, int nb, int64_t seg) {
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_GRAD) return;
-  __shared__ long long sh[256];
-  __shared__ long long sc[256];
-  const int b0 = blockIdx.x * 256;
-  long long pre = 0;
-  for (int t = threadIdx.x; t < b0; t += 256) pre += B.cand_cnt[t];
-  sh[threadIdx.x] = pre;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  const long long base = sh[0];
-  __syncthreads();
-  const int t = b0 + threadIdx.x;
-  sc[threadIdx.x] = (t < nb) ? B.cand_cnt[t] : 0;
-  __syncthreads();
-  for (int o = 1; o < 256; o <<= 1) {
-    long long v = threadIdx.x >= o ? sc[threadIdx.x - o] : 0;
-    __syncthreads();
-    sc[threadIdx.x] += v;
-    __syncthreads();
-  }
+  __shared__ int s_w[8];
+  __shared__ int s_cnt[8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int k = w; k < 256; k += 8) {
-    const int tt = b0 + k;
-    if (tt >= nb) break;
-    const long long n = B.cand_cnt[tt];
-    const long long s0 = base + sc[k] - n;
-    for (long long e = lane; e < n; e += 32) {
-      const int64_t src = (int64_t)tt * seg + e;
-      const int64_t dst = s0 + e;
-      B.S_idx[dst] = B.cand_idx[src];
-      B.S_case[dst] = B.cand_case[src];
-      B.S_a[dst] = B.cand_a[src];
-      B.S_n[dst] = B.cand_n[src];
-      B.S_u[dst] = B.cand_u[src];
-    }
+  const int b0 = blockIdx.x * 8;   // warp w copies segment b0 + w
+  // offset of segment b0: sum of the counts before it
+  int pre = 0;
+  for (int t = threadIdx.x; t < b0; t += 256) pre += B.cand_cnt[t];
+  pre = (int)__reduce_add_sync(MEB_FULLMASK, (unsigned)pre);
+  const int tt = b0 + w;
+  const int n = (tt < nb) ? B.cand_cnt[tt] : 0;
+  if (lane == 0) { s_w[w] = pre; s_cnt[w] = n; }
+  __syncthreads();
+  int base = 0, off = 0, tot = 0;
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    base += s_w[k];
+    off += (k < w) ? s_cnt[k] : 0;
+    tot += s_cnt[k];
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 255) st->nS = (int)(base + sc[255]);
+  const int64_t s0 = (int64_t)base + off;
+  for (int e = lane; e < n; e += 32) {
+    const int64_t src = (int64_t)tt * seg + e;
+    const int64_t dst = s0 + e;
+    B.S_idx[dst] = B.cand_idx[src];
+    B.S_case[dst] = B.cand_case[src];
+    B.S_a[dst] = B.cand_a[src];
+    B.S_n[dst] = B.cand_n[src];
+    B.S_u[dst] = B.cand_u[src];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) st->nS = base + tot;
 }
 
 // Support rows: b_k = (c_k - c)/s + v_k/sigma recomputed in FP64;
 //   sum v^+ = sigma f_k b_k (all S), sum w_k (case M), sum t_k w_k^2 (case M),
 //   sum (1 + t_k) (case M);  W rows w_k = b_k / n_k (M) or b_k (I).
 // Block b takes rows [b*rpb, (b+1)*rpb) in order; thread j owns columns j, j+256, ...
+constexpr int kSvecStage = 64;   // support rows staged per round in shared memory
+
 __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buffers B, int d) {
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_GRAD) return;
@@ -678,6 +695,11 @@ __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buff
     if (last_block_ticket(&st->ctr_svec)) control_b_body(B, d);
     return;
   }
+  __shared__ int s_idx[kSvecStage], s_sl[kSvecStage];
+  __shared__ unsigned char s_cs[kSvecStage];
+  __shared__ double s_sf[kSvecStage], s_in[kSvecStage], s_t[kSvecStage];
+  __shared__ double s_red[3 * 256];
+  __shared__ double sh[32];
   const int k0 = blockIdx.x * rpb, k1 = min(nS, k0 + rpb);
   const int cur = st->sup_cur, nsup = st->nsup;
   const int* sidx = cur ? B.sup_idx[1] : B.sup_idx[0];
@@ -685,44 +707,90 @@ __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buff
   const double inv_s = st->inv_s, sigma = st->sigma, inv_sigma = st->inv_sigma;
   const double* ct = B.vec.ct;
   double* out = B.svec_part + (int64_t)blockIdx.x * (3 * d + 1);
+  // G row groups of 32 * ceil(d / 32) threads each take every G-th row (all
+  // SMSPs of the SM share the FP64 work); threads past G groups idle
+  const int span = 32 * ((d + 31) / 32);
+  const int G = span >= 256 ? 1 : 256 / span;
+  const int grp = (int)threadIdx.x / (span >= 256 ? 256 : span);
+  const int jl = (int)threadIdx.x - grp * (span >= 256 ? 256 : span);
   double s1t = 0.0;
   for (int j0 = 0; j0 < d; j0 += 256) {
-    const int j = j0 + threadIdx.x;
+    const int j = j0 + jl;
+    const bool act = grp < G && j < d;
     double av = 0.0, aw = 0.0, atw = 0.0;
-    for (int k = k0; k < k1; k++) {
-      const int idx = B.S_idx[k];
-      const int cs = B.S_case[k];
-      const double a = B.S_a[k], n = B.S_n[k];
-      const int sl0 = B.slot[idx];
-      const int sl = ((unsigned)sl0 < (unsigned)nsup && sidx[sl0] == idx) ? sl0 : -1;
-      if (j0 == 0 && threadIdx.x == 0) {
-        const double t = (cs == CASE_M) ? a / n : 0.0;
-        B.S_t[k] = t;
-        if (cs == CASE_M) s1t += 1.0 + t;
-      }
-      if (j < d) {
-        double b = (C[(int64_t)idx * d + j] - ct[j]) * inv_s;
-        if (sl >= 0) b = fma(sv[(int64_t)sl * d + j], inv_sigma, b);
-        if (cs == CASE_I) {
-          av += sigma * b;
-          B.W[(int64_t)k * d + j] = b;
+    for (int r0 = k0; r0 < k1; r0 += kSvecStage) {
+      const int nr = min(kSvecStage, k1 - r0);
+      __syncthreads();
+      // stage the rows: index, slot (checked), case and the row scalars
+      if ((int)threadIdx.x < nr) {
+        const int k = r0 + threadIdx.x;
+        const int idx = B.S_idx[k];
+        const int cs = B.S_case[k];
+        const double a = B.S_a[k], n = B.S_n[k];
+        const int sl0 = B.slot[idx];
+        const int sl = ((unsigned)sl0 < (unsigned)nsup && sidx[sl0] == idx) ? sl0 : -1;
+        s_idx[threadIdx.x] = idx;
+        s_sl[threadIdx.x] = sl;
+        s_cs[threadIdx.x] = (unsigned char)cs;
+        if (cs == CASE_M) {
+          const double in = 1.0 / n;
+          const double t = a * in;
+          s_in[threadIdx.x] = in;
+          s_t[threadIdx.x] = t;
+          s_sf[threadIdx.x] = sigma * (0.5 * (a + n) * in);
+          if (j0 == 0) {
+            B.S_t[k] = t;
+            s1t += 1.0 + t;
+          }
         } else {
-          const double f = 0.5 * (a + n) / n;
-          const double wv = b / n;
-          const double t = a / n;
-          av += sigma * f * b;
-          aw += wv;
-          atw += t * wv * wv;
-          B.W[(int64_t)k * d + j] = wv;
+          s_in[threadIdx.x] = 1.0;
+          s_t[threadIdx.x] = 0.0;
+          s_sf[threadIdx.x] = sigma;
+          if (j0 == 0) B.S_t[k] = 0.0;
+        }
+      }
+      __syncthreads();
+      if (act) {
+        for (int r = grp; r < nr; r += G) {
+          const int64_t idx = s_idx[r];
+          const int sl = s_sl[r];
+          double b = (C[idx * d + j] - ct[j]) * inv_s;
+          if (sl >= 0) b = fma(sv[(int64_t)sl * d + j], inv_sigma, b);
+          av = fma(s_sf[r], b, av);
+          const int64_t k = r0 + r;
+          if (s_cs[r] == CASE_M) {
+            const double wv = b * s_in[r];
+            aw += wv;
+            atw = fma(s_t[r] * wv, wv, atw);
+            B.W[k * d + j] = wv;
+          } else {
+            B.W[k * d + j] = b;
+          }
         }
       }
     }
-    if (j < d) {
+    // the groups' sums, in group order
+    __syncthreads();
+    if (act) {
+      s_red[3 * threadIdx.x] = av;
+      s_red[3 * threadIdx.x + 1] = aw;
+      s_red[3 * threadIdx.x + 2] = atw;
+    }
+    __syncthreads();
+    if (grp == 0 && j < d) {
+      const int gs = span >= 256 ? 256 : span;
+      for (int g = 1; g < G; g++) {
+        const int tt = g * gs + jl;
+        av += s_red[3 * tt];
+        aw += s_red[3 * tt + 1];
+        atw += s_red[3 * tt + 2];
+      }
       out[j] = av;
       out[d + j] = aw;
       out[2 * d + j] = atw;
     }
   }
+  s1t = block_sum<256>(s1t, sh);
   if (threadIdx.x == 0) out[3 * d] = s1t;
   if (last_block_ticket(&st->ctr_svec)) control_b_body(B, d);
 }
@@ -730,7 +798,7 @@ __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buff
 cudaError_t launch_support_rows(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s) {
   int tpb;
   const int nb = pass_blocks(m, d, &tpb);
-  k_compact_S<<<(nb + 255) / 256, 256, 0, s>>>(B, nb, (int64_t)tpb * kPassThreads);
+  k_compact_S<<<(nb + 7) / 8, 256, 0, s>>>(B, nb, (int64_t)tpb * kPassThreads);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_svec<<<kSvecBlocks, 256, 0, s>>>(C, B, d);
