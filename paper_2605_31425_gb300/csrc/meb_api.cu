@@ -363,6 +363,7 @@ static void host_state_defaults(DevState& S, int64_t m, int d, const meb_params&
   S.max_cg = P.max_cg;
   S.sigma = P.sigma0;
   S.inv_sigma = 1.0 / P.sigma0;
+  S.tos = P.tau / P.sigma0;
   S.pinf_prev = INFINITY;
   S.phase = 0;
   S.action = ACT_NONE;

@@ -145,27 +145,64 @@ __device__ __forceinline__ float dist_lb(float S, float N, float yn, int k4) {
   return v > 0.0f ? v : 0.0f;
 }
 
+// Two block-wide sums at once, in a fixed tree order: a transposed first
+// exchange (lanes 0..15 carry a, lanes 16..31 carry b), then one warp sums the
+// warps' results.  Every thread gets both.
+__device__ __forceinline__ double2 block_sum2(double a, double b) {
+  __shared__ double s_b2[34];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool hi = lane & 16;
+  double v = (hi ? b : a) + __shfl_xor_sync(MEB_FULLMASK, hi ? a : b, 16);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(MEB_FULLMASK, v, o);
+  __syncthreads();
+  if (lane == 0) s_b2[w] = v;
+  if (lane == 16) s_b2[16 + w] = v;
+  __syncthreads();
+  if (w == 0) {
+    const int k = lane & 15;
+    double t = (k < nw) ? s_b2[(lane & 16) + k] : 0.0;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(MEB_FULLMASK, t, o);
+    if (lane == 0) s_b2[32] = t;
+    if (lane == 16) s_b2[33] = t;
+  }
+  __syncthreads();
+  const double2 r = make_double2(s_b2[32], s_b2[33]);
+  __syncthreads();
+  return r;
+}
+
 // Trial point for the next pass: ct = s * xt[1:] (exact), rt = s * xt[0],
-// the query shadow y32 = trunc32(ct - o) with yn >= ||y32||, rq32 = fl32(rt).
+// the query shadow y32 = trunc32(ct - o) with yn >= ||y32||, rq32 = fl32(rt),
+// and dx2_t = ||xt - xk||^2 (the proximal term of Psi at the trial).
 __device__ __forceinline__ void set_trial(DevState* st, const DevVecs& V, int d, double* sh) {
   const double s = st->s;
   const int d4 = (d + 3) / 4;
-  double q = 0.0;
+  double q = 0.0, dx2 = 0.0;
+  if (threadIdx.x == 0) {
+    const double dk = V.xt[0] - V.xk[0];
+    dx2 = dk * dk;
+  }
   for (int j = threadIdx.x; j < 4 * d4; j += blockDim.x) {
     float y = 0.0f;
     if (j < d) {
-      const double c = V.xt[1 + j] * s;
+      const double xt = V.xt[1 + j];
+      const double c = xt * s;
       V.ct[j] = c;
       y = f64_to_f32_trunc(c - V.o[j]);
+      const double dk = xt - V.xk[1 + j];
+      dx2 += dk * dk;
     }
     V.y32[j] = y;
     q += (double)y * (double)y;
   }
-  q = block_sum<256>(q, sh);
+  const double2 r = block_sum2(q, dx2);
   if (threadIdx.x == 0) {
     st->rt_abs = V.xt[0] * s;
     st->rq32 = __double2float_rn(V.xt[0] * s);
-    st->yn32 = __double2float_ru(sqrt(q) * (1.0 + 1e-12));
+    st->yn32 = __double2float_ru(sqrt(r.x) * (1.0 + 1e-12));
+    st->dx2_t = r.y;
   }
   __syncthreads();
 }

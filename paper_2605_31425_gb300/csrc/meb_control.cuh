@@ -78,6 +78,7 @@ __device__ __forceinline__ void do_outer(DevState* st, const DevVecs& V, int d, 
         if (sg > st->sigma_max) sg = st->sigma_max;
         st->sigma = sg;
         st->inv_sigma = 1.0 / sg;
+        st->tos = st->tau / sg;
       }
       st->pinf_prev = pinf;
       st->phase = 0;
@@ -123,14 +124,9 @@ __device__ __forceinline__ void early_body_impl(const Buffers& B, DevState* st, 
 #pragma unroll
   for (int k = 0; k < 8; k++) tsum += shf[k];
   const double t = (double)tsum;
-  double dx2 = 0.0;
-  for (int k = threadIdx.x; k < n1; k += 256) {
-    const double dk = V.xt[k] - V.xk[k];
-    dx2 += dk * dk;
-  }
-  dx2 = block_sum<256>(dx2, sh);
+  const double dx2 = st->dx2_t;
   if (threadIdx.x == 0) {
-    const double sigma = st->sigma, tos = st->tau / sigma;
+    const double sigma = st->sigma, tos = st->tos;
     // FP32 sums of nonnegative terms: keep 1% for their rounding
     const double pi2_lb = 0.99 * t * st->inv_s * st->inv_s * 0.5;
     const double psi_lb = V.xt[0] + 0.5 * sigma * pi2_lb + 0.5 * tos * dx2;
@@ -229,13 +225,8 @@ __device__ __forceinline__ void control_a_body_impl(const Buffers& B, DevState* 
     }
     __syncthreads();
   }
-  const double sigma = st->sigma, tos = st->tau / sigma;
-  double dx2 = 0.0;
-  for (int k = threadIdx.x; k < n1; k += 256) {
-    const double dk = V.xt[k] - V.xk[k];
-    dx2 += dk * dk;
-  }
-  dx2 = block_sum<256>(dx2, sh);
+  const double sigma = st->sigma, tos = st->tos;
+  const double dx2 = st->dx2_t;
   const double psi_t = V.xt[0] + 0.5 * sigma * s_last[P_PI2] + 0.5 * tos * dx2;
   const double mag_t = fabs(V.xt[0]) + 0.5 * sigma * s_last[P_PI2] + 0.5 * tos * dx2;
   if (threadIdx.x == 0) {
@@ -244,7 +235,6 @@ __device__ __forceinline__ void control_a_body_impl(const Buffers& B, DevState* 
     st->reuse_lists = 0;
     st->tot_passes += 1;
     st->n64_total += (int64_t)s_last[P_N64];
-    st->dx2_t = dx2;
     int nxt = 0;   // 0: gradient at the (accepted) trial; 1: backtrack
     if (st->eval_only) {
       st->psi = psi_t - s_last[P_UV2] / (2.0 * sigma);
@@ -302,40 +292,40 @@ __device__ __forceinline__ void control_b_body_impl(const Buffers& B, DevState* 
   const int n1 = d + 1;
   __shared__ double sh[32];
   const int snb = st->svec_nb;
-  for (int j = threadIdx.x; j < d; j += 256) {
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int k = 0; k < snb; k++) {
-      const double* p = B.svec_part + (int64_t)k * (3 * d + 1);
-      a += p[j];
-      b += p[d + j];
-      c += p[2 * d + j];
-    }
-    V.sv[j] = a;
-    V.sw[j] = b;
-    V.cg_diag[1 + j] = c;   // sum_M t w_j^2 (Jacobi preconditioner)
-  }
-  if (threadIdx.x == 0) {
-    double s1t = 0.0;
-    for (int k = 0; k < snb; k++) s1t += B.svec_part[(int64_t)k * (3 * d + 1) + 3 * d];
-    V.st1[0] = s1t;
+  // the 3d + 1 sums over the support blocks' partials, one per thread (each
+  // in block order): sum v^+ (d), sum w (d), sum t w^2 (d), sum (1 + t)
+  const int nsum = 3 * d + 1;
+  for (int e = threadIdx.x; e < nsum; e += 256) {
+    double a = 0.0;
+    for (int k = 0; k < snb; k++) a += B.svec_part[(int64_t)k * nsum + e];
+    if (e < d) V.sv[e] = a;
+    else if (e < 2 * d) V.sw[e - d] = a;
+    else if (e < 3 * d) V.cg_diag[1 + e - 2 * d] = a;   // sum_M t w_j^2 (Jacobi preconditioner)
+    else V.st1[0] = a;
   }
   __syncthreads();
-  const double sigma = st->sigma, tau = st->tau, tos = tau / sigma;
+  const double sigma = st->sigma, tau = st->tau, tos = st->tos;
   const double su = st->last[P_SU];
+  const bool eval_only = st->eval_only != 0;
+  // the gradient at the trial; when it is accepted (not eval_only): x <- xt,
+  // g <- gt, and the terms of the stopping condition
+  double la = 0.0, g2 = 0.0;
   for (int k = threadIdx.x; k < n1; k += 256) {
-    const double dk = V.xt[k] - V.xk[k];
+    const double xt = V.xt[k];
+    const double dk = xt - V.xk[k];
     const double sk = (k == 0) ? su : V.sv[k - 1];
-    V.gt[k] = ((k == 0) ? 1.0 : 0.0) - sk + tos * dk;
+    const double gk = ((k == 0) ? 1.0 : 0.0) - sk + tos * dk;
+    V.gt[k] = gk;
+    if (!eval_only) {
+      V.x[k] = xt;
+      V.g[k] = gk;
+      la += (V.ab[k] - xt) * gk;
+      g2 += gk * gk;
+    }
   }
-  __syncthreads();
-  if (st->eval_only) {
+  if (eval_only) {
     if (threadIdx.x == 0) { st->action = ACT_DONE; st->status = 1; }
     return;
-  }
-  // accepted point: x <- xt, g <- gt
-  for (int k = threadIdx.x; k < n1; k += 256) {
-    V.x[k] = V.xt[k];
-    V.g[k] = V.gt[k];
   }
   if (threadIdx.x == 0) {
     st->gmag = 1.0 + sigma * st->last[P_ZMAG] + tos * sqrt(st->dx2_t);
@@ -346,16 +336,10 @@ __device__ __forceinline__ void control_b_body_impl(const Buffers& B, DevState* 
     do_outer(st, V, d, sh);
     return;
   }
-  double la = 0.0, g2 = 0.0, dk2 = 0.0;
-  for (int k = threadIdx.x; k < n1; k += 256) {
-    la += (V.ab[k] - V.x[k]) * V.g[k];
-    g2 += V.g[k] * V.g[k];
-    const double t = V.x[k] - V.xk[k];
-    dk2 += t * t;
-  }
-  la = block_sum<256>(la, sh);
-  g2 = block_sum<256>(g2, sh);
-  dk2 = block_sum<256>(dk2, sh);
+  const double2 lg = block_sum2(la, g2);
+  la = lg.x;
+  g2 = lg.y;
+  const double dk2 = st->dx2_t;   // ||x - xk||^2 with x = xt
   const double lhs = 2.0 * sigma * fabs(la) + sigma * sigma * g2;
   const double rhs = st->rho * (st->last[P_DUV2] + tau * dk2);
   const bool stop = (lhs <= rhs) || (sqrt(g2) <= 8.0 * DBL_EPSILON * st->gmag);

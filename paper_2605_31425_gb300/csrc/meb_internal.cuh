@@ -61,6 +61,7 @@ struct DevState {
   int max_outer, max_ssn, max_backtrack, max_cg;
   // iteration state
   double sigma, inv_sigma;
+  double tos;                  // tau / sigma
   double psi, psi_mag, gmag;   // at the accepted point x
   double gdx, eta;
   double pinf_prev;
@@ -84,7 +85,7 @@ struct DevState {
   int screen_log[8];           // profiling: tick t of a graph batch ran a full screen
   unsigned int ctr_screen, ctr_rows, ctr_svec, ctr_slots;   // last-block-done tickets
   int screens;                 // full FP32 screens run
-  double dx2_t;                // ||xt - xk||^2 of the last trial
+  double dx2_t;                // ||xt - xk||^2 of the trial (set with the trial)
   double kkt[5], kkt_max;
   double last[P_COUNT];        // reduced partials of the last pass
   // trial point shadow for the FP32 screen

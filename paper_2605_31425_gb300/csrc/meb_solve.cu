@@ -96,7 +96,7 @@ __global__ void k_syrk_reduce(Buffers B, int d, int force) {
   const int nt = (d + kSyrkTile - 1) / kSyrkTile;
   const int ntri = nt * (nt + 1) / 2;
   const int n1 = d + 1;
-  const double sigma = st->sigma, tos = st->tau / sigma;
+  const double sigma = st->sigma, tos = st->tos;
   const double nI = st->last[P_NI], nM = st->last[P_NM], s1t = V.st1[0];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)n1 * n1;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) k_newton_chol(Buffers B, int d) {
   __shared__ int s_fail;
   const DevVecs& V = B.vec;
   const int n = d + 1;
-  const double sigma = st->sigma, tos = st->tau / sigma;
+  const double sigma = st->sigma, tos = st->tos;
   const double nI = st->last[P_NI], nM = st->last[P_NM];
   const double s1t = V.st1[0];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(256) k_hvp_acc(Buffers B, int d, const double*
 __device__ void hvp_finish(DevState* st, const DevVecs& V, int d, const double* q,
                            const double* part, int nblk, double* y) {
   const int n1 = d + 1;
-  const double sigma = st->sigma, tos = st->tau / sigma;
+  const double sigma = st->sigma, tos = st->tos;
   const double nI = st->last[P_NI], nM = st->last[P_NM], s1t = V.st1[0];
   for (int k = threadIdx.x; k < n1; k += blockDim.x) {
     double a = 0.0;
@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(256) k_cg_setup(Buffers B, int d) {
   __shared__ double sh[32];
   const DevVecs& V = B.vec;
   const int n1 = d + 1;
-  const double sigma = st->sigma, tos = st->tau / sigma;
+  const double sigma = st->sigma, tos = st->tos;
   const double nI = st->last[P_NI], nM = st->last[P_NM], s1t = V.st1[0];
   double rz = 0.0, bn = 0.0;
   for (int k = threadIdx.x; k < n1; k += 256) {
