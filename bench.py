@@ -39,6 +39,11 @@ sys.path.insert(0, ROOT)
 METRIC = "MEB solves/s & p50/p99 latency at radius rel.err<=1e-8; per-iter HBM GB/s"
 UNIT = "solves/s"
 SAMPLE_M = 100_000
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full FP16
+# screen per ball, by d, from an ncu capture at m = 1e6 (traffic grows with
+# the balls streamed; scaled to a launch by m).  Valid for the screen kernel
+# as captured; None once the kernel changes.
+SCREEN_TRAFFIC_PER_BALL = {100: 223.27}
 
 
 def _peaks():
@@ -242,6 +247,9 @@ def main():
     pass_launches = max(st["pass_launches"], 1)
     avg_ms = st["pass_ms"] / pass_launches
     bytes_per_launch = st["pass_bytes"] // pass_launches
+    fp16_screen = bytes_per_launch == m * (16 * ((d + 7) // 8) + 12)
+    tpb = SCREEN_TRAFFIC_PER_BALL.get(int(d)) if fp16_screen else None
+    traffic = tpb * m if tpb else None
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
 
@@ -281,7 +289,7 @@ def main():
             "newton_per_solve": {"inverses": res["newton_inverses"], "fp64": res["newton_fp64"]},
             "fp64_rows_per_pass": res["fp64_rows"] / max(res["passes"], 1),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_screen", "bytes_per_launch": bytes_per_launch,
                          "avg_launch_ms": avg_ms, "launches_timed": st["pass_launches"],
                          "peak_kind": peak_kind},

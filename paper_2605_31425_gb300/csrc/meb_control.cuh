@@ -8,14 +8,16 @@
 
 namespace meb {
 
-// Last-block-done: every thread fences its writes, then thread 0 takes a
-// ticket; the block holding the last ticket returns true (after an acquire
-// fence) and resets the counter for the next launch.
+// Last-block-done: after a barrier (which makes the block's writes visible
+// to thread 0), thread 0 fences at GPU scope (the fence is cumulative, so it
+// orders those writes too) and takes a ticket; the block holding the last
+// ticket returns true (after an acquire fence) and resets the counter for
+// the next launch.
 __device__ __forceinline__ bool last_block_ticket(unsigned int* ctr) {
   __shared__ int s_last;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     const unsigned int t = atomicAdd(ctr, 1u);
     s_last = (t == gridDim.x - 1);
     if (s_last) *ctr = 0u;
