@@ -27,7 +27,8 @@ class MebParams(ct.Structure):
         ("sigma_max", ct.c_double), ("sigma_growth", ct.c_double), ("sigma_ratio", ct.c_double),
         ("tau", ct.c_double), ("armijo_mu", ct.c_double), ("active_theta", ct.c_double),
         ("max_outer", ct.c_int32), ("max_ssn", ct.c_int32), ("max_backtrack", ct.c_int32),
-        ("dense_max_d", ct.c_int32), ("max_cg", ct.c_int32), ("reserved", ct.c_int32 * 3),
+        ("dense_max_d", ct.c_int32), ("max_cg", ct.c_int32), ("newton_fp64", ct.c_int32),
+        ("reserved", ct.c_int32 * 2),
     ]
 
 

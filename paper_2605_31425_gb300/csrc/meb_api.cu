@@ -39,12 +39,14 @@ struct meb_ctx {
   int64_t gm = 0;
   int gd = 0;
   int gmode = -1;
+  int gvar = -1;
   int gprof = -1;
   cudaEvent_t gev[2 * 8] = {};
   // tick loop: 0 = graph of kUnrollTicks ticks relaunched until the controller
   // stops (default), 1 = host-driven ticks, 2 = graph with a while-node
   int loop_mode = 0;
   bool screen_fp32 = false;   // solves screen the FP16 shadow unless set
+  bool screen_bulk = false;   // FP16 screens through the bulk-copy pipeline
   cudaEvent_t ev[2] = {nullptr, nullptr};
   meb_stats stats{};
   int prof_screens = 0;
@@ -52,7 +54,9 @@ struct meb_ctx {
 };
 
 // kernels launched per controller tick of the device-resident loop
-static const int64_t kTickLaunches = 2 + 2 + 4 + 2;
+// kernels of one controller tick: pass (2), support rows (2), the dense
+// Newton step, the multiplier update (2)
+static int64_t tick_launches(int d) { return 2 + 2 + newton_dense_launches(d) + 2; }
 static const int kUnrollTicks = 8;
 
 enum { POOL_C, POOL_R, POOL_U, POOL_V, POOL_X, POOL_XB, POOL_Q, POOL_UP, POOL_VP, POOL_HQ,
@@ -78,7 +82,7 @@ static int fail(meb_ctx* ctx, int code, const char* fmt, ...) {
 
 static void free_buffers(meb_ctx* ctx) {
   Buffers& B = ctx->B;
-  void* ptrs[] = {B.X32, B.X16, B.XN16, B.Hhi, B.Hlo, B.R32, B.slot, B.sup_idx[0], B.sup_idx[1], B.sup_u[0], B.sup_u[1],
+  void* ptrs[] = {B.X32, B.X16, B.EPS16, B.E32, B.Hhi, B.Hlo, B.R32, B.slot, B.sup_idx[0], B.sup_idx[1], B.sup_u[0], B.sup_u[1],
                   B.sup_v[0], B.sup_v[1], B.part_flag, B.part, B.part_cnt, B.cand_cnt, B.cand_idx,
                   B.unc_cnt, B.unc_idx, B.unc_slot, B.vlb_part,
                   B.cand_case, B.cand_a, B.cand_n, B.cand_u, B.S_idx, B.S_case, B.S_a, B.S_n,
@@ -125,19 +129,19 @@ static int ensure_buffers(meb_ctx* ctx, int64_t m, int d) {
   B.hpart_cap = hp;
   CK(dalloc(&B.X32, (size_t)d4 * m_pad));
   CK(dalloc(&B.X16, (size_t)((d4 + 1) / 2) * m_pad));
-  CK(dalloc(&B.XN16, (size_t)m_pad));
+  CK(dalloc(&B.EPS16, (size_t)m_pad));
+  CK(dalloc(&B.E32, (size_t)m_pad));
   CK(dalloc(&B.Hhi, (size_t)(d + 1 <= kMaxDenseN ? n1 * n1 : 1)));
   CK(dalloc(&B.Hlo, (size_t)(d + 1 <= kMaxDenseN ? n1 * n1 : 1)));
   CK(dalloc(&B.R32, (size_t)m_pad));
-  CK(dalloc(&B.slot, (size_t)m));
+  CK(dalloc(&B.slot, (size_t)m_pad));   // whole tiles are bulk-copied
   for (int k = 0; k < 2; k++) {
     CK(dalloc(&B.sup_idx[k], (size_t)m));
     CK(dalloc(&B.sup_u[k], (size_t)m));
     CK(dalloc(&B.sup_v[k], (size_t)md));
   }
-  int tpb;
-  const int64_t npb = pass_blocks(m, d, &tpb);
-  const int64_t ncand = npb * tpb * 256;
+  // segments of 256 per tile and block: at most (tiles + blocks) * 256 for any grid
+  const int64_t ncand = (nblk + kMaxPassBlocks) * 256;
   CK(dalloc(&B.part_flag, (size_t)nblk));
   CK(dalloc(&B.part, (size_t)nblk * P_NREC));
   CK(dalloc(&B.part_cnt, (size_t)nblk * P_NCNT));
@@ -267,8 +271,11 @@ int meb_create(meb_ctx** out, int device, void* cuda_stream) {
     const char* lm = getenv("MEB_TICK_LOOP");
     if (lm && !strcmp(lm, "host")) ctx->loop_mode = 1;
     if (lm && !strcmp(lm, "while")) ctx->loop_mode = 2;
-    const char* sp = getenv("MEB_SCREEN");   // "fp32": solves screen the FP32 shadow
+    // "fp32": solves screen the FP32 shadow; "bulk": the FP16 shadow through
+    // the bulk-copy pipeline
+    const char* sp = getenv("MEB_SCREEN");
     ctx->screen_fp32 = sp && !strcmp(sp, "fp32");
+    ctx->screen_bulk = sp && !strcmp(sp, "bulk");
   }
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_st, sizeof(DevState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_scal, 64 * sizeof(double));
@@ -348,6 +355,7 @@ static void host_state_defaults(DevState& S, int64_t m, int d, const meb_params&
   S.d4 = (d + 3) / 4;
   S.n1 = d + 1;
   S.dense = (d <= P.dense_max_d && d + 1 <= kMaxDenseN) ? 1 : 0;
+  S.force_fp64_solve = P.newton_fp64 != 0;
   S.s = s;
   S.inv_s = 1.0 / s;
   S.tol = P.tol;
@@ -385,6 +393,7 @@ static int solve_graph(meb_ctx* ctx, const double* C, const double* R, int64_t m
   const int prof = ctx->profiling;
   if (ctx->gexec && ctx->gkey[0] == C && ctx->gkey[1] == R && ctx->gkey[2] == B.st &&
       ctx->gkey[3] == (const void*)(B.use_x16 ? (const void*)B.X16 : (const void*)B.X32) &&
+      ctx->gvar == screen_variant(B, d) &&
       ctx->gm == m && ctx->gd == d && ctx->gmode == mode && ctx->gprof == prof)
     return MEB_OK;
   if (prof && !ctx->gev[0])
@@ -435,6 +444,7 @@ static int solve_graph(meb_ctx* ctx, const double* C, const double* R, int64_t m
   CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
   ctx->gkey[0] = C; ctx->gkey[1] = R; ctx->gkey[2] = B.st;
   ctx->gkey[3] = B.use_x16 ? (const void*)B.X16 : (const void*)B.X32;
+  ctx->gvar = screen_variant(B, d);
   ctx->gm = m; ctx->gd = d; ctx->gmode = mode; ctx->gprof = prof;
   return MEB_OK;
 }
@@ -511,6 +521,9 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   if (sc / 2.0 >= r0) sc /= 2.0;
   CK(cudaMemsetAsync(B.slot, 0xff, sizeof(int) * (size_t)m, s));
   B.use_x16 = !ctx->screen_fp32;
+  B.bulk = ctx->screen_bulk;
+  CK(prepare_pass(B, d));
+  CK(prepare_newton(d));
   if (B.use_x16) CK(launch_shadow16(B, m, d, 1.0 / sc, s));
   host_state_defaults(*ctx->h_st, m, d, P, sc);
   ctx->h_st->rt_abs = r0;   // initial radius; k_state_init scales it
@@ -518,10 +531,10 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   CK(launch_state_init(B, d, s));
   const bool dense = ctx->h_st->dense;
   ctx->prof_screens = 0;
-  // per ball: the shadow row (FP16: 16 bytes per 8 coordinates, + 4 for its
-  // squared norm; FP32: 16 bytes per 4 coordinates), the FP32 radius, the slot
+  // per ball: the shadow row (FP16: 16 bytes per 8 coordinates; FP32: 16
+  // bytes per 4 coordinates), its error bound, the FP32 radius and the slot
   const int64_t d4 = (d + 3) / 4;
-  const int64_t pass_bytes = m * (B.use_x16 ? 16 * ((d4 + 1) / 2) + 12 : 16 * d4 + 8);
+  const int64_t pass_bytes = m * (B.use_x16 ? 16 * ((d4 + 1) / 2) + 12 : 16 * d4 + 12);
 
   const int64_t max_ticks =
       (int64_t)P.max_outer * (P.max_ssn + 2) * (P.max_backtrack + 2) + 16;
@@ -537,7 +550,7 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
       CK(cudaGraphLaunch(ctx->gexec, s));
       rc = read_state(ctx);
       if (rc) return rc;
-      B.launches = before + ctx->h_st->ticks * (kTickLaunches + 1);
+      B.launches = before + ctx->h_st->ticks * (tick_launches(d) + 1);
       if (ctx->h_st->status == 3) return fail(ctx, MEB_ECUDA, "controller did not terminate");
     } else {
       int64_t ticks = 0;
@@ -562,7 +575,7 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
         if (ctx->h_st->status != 0) break;
         if (ticks > max_ticks) return fail(ctx, MEB_ECUDA, "controller did not terminate");
       }
-      B.launches = before + ticks * kTickLaunches;
+      B.launches = before + ticks * tick_launches(d);
     }
   } else {
     int64_t ticks = 0;
@@ -602,6 +615,8 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
     }
   }
   const DevState S = *ctx->h_st;
+  if (S.status == kStatusWaitTimeout)
+    return fail(ctx, MEB_ECUDA, "a device wait timed out (a bulk copy did not complete)");
 
   // final point, radius lift (max-type value at c) and active set
   double* d_ralm = ctx->d_scal + 1;
@@ -613,7 +628,7 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   const double r_alm = ctx->h_scal[1];
   const double r_out = ctx->h_scal[2];
   CK(launch_feas_cert(C, R, m, d, (const double*)dcout, r_out, P.active_theta * r_out, 1, 0, B,
-                      nullptr, nullptr, ctx->d_i64 + 5, s));
+                      nullptr, nullptr, ctx->d_i64 + 5, s, /*reuse_bounds=*/true));
   CK(cudaMemcpyAsync(ctx->h_scal + 8, ctx->d_i64 + 5, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   if (!(flags & MEB_PTR_DEVICE))
     CK(cudaMemcpyAsync(c_out, dcout, sizeof(double) * d, cudaMemcpyDeviceToHost, s));
@@ -687,6 +702,7 @@ extern "C" int meb_eval_alm(meb_ctx* ctx, const double* centers, const double* r
   CK(launch_shadow(C, R, m, d, B, B.vec.o, B.vec.c0, ctx->d_flags, s));
   CK(cudaMemsetAsync(B.slot, 0xff, sizeof(int) * (size_t)m, s));
   B.use_x16 = false;   // unscaled data (s = 1): the FP32 shadow
+  CK(prepare_pass(B, d));
   meb_params P;
   meb_params_default(&P);
   P.sigma0 = sigma;

@@ -127,21 +127,34 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
   return __uint_as_float(r);
 }
 
-// Shadow rounding unit (truncation of an FP64 value that itself carries one
-// FP64 rounding): |x - x32| <= kShadowU |x32| per element.
+// The FP32 shadow.  The origin o is the first centre truncated to FP32 (so
+// it is exact in both precisions); each element is
+//   x32 = fl32(trunc32(c_ij) - o_j)
+// with FP32 operations only (the FP64 pipe is not used).  With x = c_i - o,
+//   |x - x32| <= 2^-24 |x32| + 2^-23 |c_ij| + 2^-126,
+// so ||x_i - x32_i|| <= kShadowU ||x32_i|| + E_i, where E_i >= 2^-23 ||c_i|| +
+// sqrt(d) 2^-126 is stored per ball.  The query shadow y32 = trunc32(y - o)
+// is formed in FP64 (one rounding, one truncation): |y - y32| <= kShadowU |y32|.
 constexpr float kU32 = 5.9604645e-08f;     // 2^-24
 constexpr float kShadowU = 2.02f * 2.0f * kU32;
 
+// E_i from cn2 = fmaf sum of trunc32(c_ij)^2 over the d elements of a row:
+// ||c_i|| <= ||trunc32(c_i)|| (1 + 2^-23) + sqrt(d) 2^-126 and the sum and
+// square root add at most (d + 4) 2^-24 relative (d <= 16384).
+__device__ __forceinline__ float shadow_abs_err(float cn2, int d) {
+  return 1.1920929e-7f * sqrtf(cn2) * (1.0f + (float)(d + 12) * kU32) + 4e-36f;
+}
+
 // Certified bounds on D = ||x - y|| from the FP32 shadows x32, y32:
 //   S = sum (x32 - y32)^2, N = sum x32^2 (fmaf sums over k4 elements, k4 = 4 d4),
-//   yn >= ||y32||.  Each of the k4 difference/square/sum steps is round-to-
-//   nearest; the shadows are within kShadowU of the exact values.
-__device__ __forceinline__ float dist_ub(float S, float N, float yn, int k4) {
-  return (sqrtf(S) + kShadowU * (sqrtf(N) + yn)) * (1.0f + (float)(k4 + 16) * kU32) + 1e-30f;
+//   yn >= ||y32||, E = the ball's absolute shadow error.  Each of the k4
+//   difference/square/sum steps is round-to-nearest.
+__device__ __forceinline__ float dist_ub(float S, float N, float yn, float E, int k4) {
+  return (sqrtf(S) + kShadowU * (sqrtf(N) + yn) + E) * (1.0f + (float)(k4 + 16) * kU32) + 1e-30f;
 }
-__device__ __forceinline__ float dist_lb(float S, float N, float yn, int k4) {
-  const float v = (sqrtf(S) * (1.0f - (float)(k4 + 16) * kU32)) - kShadowU * (sqrtf(N) + yn) *
-                  (1.0f + (float)(k4 + 16) * kU32) - 1e-30f;
+__device__ __forceinline__ float dist_lb(float S, float N, float yn, float E, int k4) {
+  const float v = (sqrtf(S) * (1.0f - (float)(k4 + 16) * kU32)) -
+                  (kShadowU * (sqrtf(N) + yn) + E) * (1.0f + (float)(k4 + 16) * kU32) - 1e-30f;
   return v > 0.0f ? v : 0.0f;
 }
 
@@ -208,19 +221,25 @@ __device__ __forceinline__ void set_trial(DevState* st, const DevVecs& V, int d,
 }
 
 // FP16 shadow (scaled by 1/s): x16 = fl16(x32 / s) with x32 the FP32 shadow.
-// Per element |x/s - x16| <= kHalfU |x16| + kHalfAbs (normal and subnormal
-// halves), so ||x/s - x16_i|| <= kHalfU ||x16_i|| + sqrt(k4) kHalfAbs.
+// Per element |x/s - x16| <= kHalfU |x16| + kHalfAbs + abs_ij / s (normal and
+// subnormal halves), so ||x/s - x16_i|| <= eps_i with
+//   eps_i = kHalfU ||x16_i|| + sqrt(k) kHalfAbs + E_i / s,
+// stored per ball (k = 8 ceil(d/8) elements, padding included).
 constexpr float kHalfU = 4.8828125e-4f + 1.001f * kShadowU;   // 2^-11 + shadow error
 constexpr float kHalfAbs = 2.99e-8f;                            // 2^-25 (1 + shadow error)
 
-__device__ __forceinline__ float dist_ub16(float S, float N, float yn, int k4) {
-  return (sqrtf(S) + kHalfU * sqrtf(N) + kShadowU * yn + sqrtf((float)k4) * kHalfAbs) *
-             (1.0f + (float)(k4 + 16) * kU32) + 1e-30f;
+// eps_i from N16 = fmaf sum of the k squared halves, E_i and 1/s
+__device__ __forceinline__ float half_err(float N16, float E, float inv_s, int k) {
+  return (kHalfU * sqrtf(N16) + sqrtf((float)k) * kHalfAbs + E * inv_s) *
+             (1.0f + (float)(k + 16) * kU32) + 1e-30f;
 }
-__device__ __forceinline__ float dist_lb16(float S, float N, float yn, int k4) {
-  const float v = sqrtf(S) * (1.0f - (float)(k4 + 16) * kU32) -
-                  (kHalfU * sqrtf(N) + kShadowU * yn + sqrtf((float)k4) * kHalfAbs) *
-                      (1.0f + (float)(k4 + 16) * kU32) - 1e-30f;
+
+__device__ __forceinline__ float dist_ub16(float S, float eps, float yn, int k) {
+  return (sqrtf(S) + eps + kShadowU * yn) * (1.0f + (float)(k + 16) * kU32) + 1e-30f;
+}
+__device__ __forceinline__ float dist_lb16(float S, float eps, float yn, int k) {
+  const float v = sqrtf(S) * (1.0f - (float)(k + 16) * kU32) -
+                  (eps + kShadowU * yn) * (1.0f + (float)(k + 16) * kU32) - 1e-30f;
   return v > 0.0f ? v : 0.0f;
 }
 

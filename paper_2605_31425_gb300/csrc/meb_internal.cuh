@@ -30,6 +30,10 @@ enum : int {
   ACT_TRIAL_EARLY = 6,  // trial rejected from the certified lower bound; next trial set
 };
 
+// DevState::status: 0 running, 1 converged, 2 iteration cap, 3 a device wait
+// gave up (a bulk copy did not complete in time)
+constexpr int kStatusWaitTimeout = 3;
+
 // per-block partial record of the pass (doubles)
 enum : int {
   P_PI2 = 0,   // sum ||Pi(z_i)||^2
@@ -77,6 +81,7 @@ struct DevState {
   int chol_fail, eval_only;
   int accept_mode;             // 1: accepted, go to the stop test; 2: accepted, outer forced
   int need_fp64_solve;         // FP32 inverse + refinement failed: FP64 Cholesky
+  int force_fp64_solve;        // every dense Newton system by the FP64 Cholesky
   int fp64_solves;             // count of FP64 Cholesky fallbacks
   int gj_inverses;             // count of FP32 Gauss-Jordan inverses
   int early_rejects;           // trials rejected by the certified lower bound
@@ -125,10 +130,12 @@ struct Buffers {
   // shadow
   float4* X32;          // [d4][m_pad]
   uint4* X16;           // [ceil(d4/2)][m_pad] FP16 shadow scaled by 1/s (meb_solve)
-  float* XN16;          // [m_pad] sum of squares of each ball's X16 row (FP32)
+  float* EPS16;         // [m_pad] per ball: bound eps_i on ||x_i/s - x16_i|| (scaled units)
+  float* E32;           // [m_pad] per ball: absolute part E_i of the FP32 shadow error
   float* Hhi;           // [n1 x n1] fl32(H)
   float* Hlo;           // [n1 x n1] fl32(H - Hhi)
   bool use_x16;         // host side: the screens read X16
+  bool bulk;            // host side: FP16 screens through the bulk-copy pipeline
   float* R32;           // [m_pad]
   // multipliers (double buffered)
   int* slot;            // [m]
@@ -174,7 +181,11 @@ struct Buffers {
 };
 
 // ---- launch wrappers: streaming kernels (meb_pass.cu) ----
-int pass_blocks(int64_t m, int d, int* tiles_per_block);
+// screen kernels: 0 FP32 shadow, 1 FP16 shadow (register batches),
+// 2 FP16 shadow through a bulk-copy (TMA) pipeline in shared memory
+int screen_variant(const Buffers& B, int d);
+int pass_blocks(int64_t m, int d, int variant, int* tiles_per_block);
+cudaError_t prepare_pass(const Buffers& B, int d);
 cudaError_t launch_shadow(const double* C, const double* R, int64_t m, int d, Buffers& B,
                           double* o, double* c0, int* bad, cudaStream_t s);
 cudaError_t launch_shadow16(Buffers& B, int64_t m, int d, double inv_s, cudaStream_t s);
@@ -185,12 +196,15 @@ cudaError_t launch_support_rows(const double* C, Buffers& B, int64_t m, int d, c
 cudaError_t launch_feas_cert(const double* C, const double* R, int64_t m, int d, const double* c,
                              double r, double eps, int mode, int want_max, Buffers& B,
                              double* dmax_out, int64_t* argmax_out, int64_t* nviol_out,
-                             cudaStream_t s);
+                             cudaStream_t s,
+                             bool reuse_bounds = false);
 cudaError_t launch_support_from_dense(const double* U, const double* V, Buffers& B, int64_t m,
                                       int d, cudaStream_t s);
 // ---- launch wrappers: solver kernels (meb_solve.cu) ----
 cudaError_t launch_tick_control(Buffers& B, int64_t m, int d, cudaStream_t s);
 cudaError_t launch_newton_dense(Buffers& B, int d, cudaStream_t s);
+int newton_dense_launches(int d);
+cudaError_t prepare_newton(int d);
 cudaError_t launch_cg_setup(Buffers& B, int d, cudaStream_t s);
 cudaError_t launch_cg_iter(Buffers& B, int d, cudaStream_t s);
 cudaError_t launch_cg_finish(Buffers& B, int d, cudaStream_t s);

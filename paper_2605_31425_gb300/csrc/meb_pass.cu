@@ -20,64 +20,109 @@
 #include <cuda_fp16.h>
 
 #include "meb_control.cuh"
+#include "meb_tma.cuh"
 
 namespace meb {
 
 
 // ===========================================================================
-// Shadow: X32[g][i] = trunc32(c_i[4g..4g+3] - o) (0 beyond d),
-// R32[i] = trunc32(r_i); o = c_0 (the first centre).  One FP64 subtraction per
-// element; the conversion uses integer operations.  A block takes 64
-// consecutive balls: their rows (contiguous in memory) are read coalesced,
-// in chunks of 128 columns, and written transposed through shared memory.
-// The same sweep checks that every centre and radius is finite (and r_i >= 0)
-// and leaves block partials of the shadow column sums for the mean centre.
+// Shadow: X32[g][i] = fl32(trunc32(c_i[4g..4g+3]) - o) (0 beyond d), with
+// o = trunc32(c_0) (the first centre), R32[i] = trunc32(r_i) and E32[i] the
+// absolute part of the shadow error (meb_common.cuh); FP32 and integer
+// operations only.  A block takes 64 consecutive balls, in chunks of 128
+// columns: warp w reads rows w, w + 8, ... coalesced (lanes over columns, 16
+// loads in flight per lane), and the tile is written transposed through
+// shared memory.  The same sweep checks that every centre and radius is
+// finite (and r_i >= 0) and leaves block partials of the shadow column sums
+// for the mean centre.
 constexpr int kShadowNT = 256;
 constexpr int kShadowBalls = 64;
 constexpr int kShadowCols = 128;
 
-__global__ void __launch_bounds__(kShadowNT) k_shadow(const double* __restrict__ C,
+__global__ void __launch_bounds__(kShadowNT, 4) k_shadow(const double* __restrict__ C,
                                                       const double* __restrict__ R, int64_t m,
                                                       int d, int64_t m_pad,
                                                       float4* __restrict__ X32,
                                                       float* __restrict__ R32,
+                                                      float* __restrict__ E32,
                                                       double* __restrict__ colpart,
                                                       int* __restrict__ bad) {
   __shared__ float tile[kShadowBalls][kShadowCols + 1];
-  __shared__ double s_o[kShadowCols];
+  __shared__ float s_o[kShadowCols];
+  __shared__ float s_cs[kShadowNT / 32][kShadowCols];   // per-warp column sums
   const int64_t i0 = (int64_t)blockIdx.x * kShadowBalls;
   const int nb = (int)imin64(kShadowBalls, m - i0);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int badf = 0;
+  float cn[kShadowBalls / 8];   // rows w + 8k: sums of trunc32(c)^2
+#pragma unroll
+  for (int k = 0; k < kShadowBalls / 8; k++) cn[k] = 0.0f;
   for (int j0 = 0; j0 < d; j0 += kShadowCols) {
     const int nc = min(kShadowCols, d - j0);
-    for (int j = threadIdx.x; j < nc; j += kShadowNT) s_o[j] = C[j0 + j];
+    for (int j = threadIdx.x; j < nc; j += kShadowNT) s_o[j] = f64_to_f32_trunc(C[j0 + j]);
     __syncthreads();
-    // coalesced read of rows i0 .. i0+nb-1, columns j0 .. j0+nc-1
-    for (int e = threadIdx.x; e < nb * nc; e += kShadowNT) {
-      const int r = e / nc, cc = e - r * nc;
-      const double v = C[(i0 + r) * (int64_t)d + j0 + cc];
-      const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-      badf |= ((bits >> 52) & 0x7ff) == 0x7ff;
-      tile[r][cc] = f64_to_f32_trunc(v - s_o[cc]);
+    float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // this lane's columns over the warp's rows
+#pragma unroll
+    for (int h = 0; h < 4; h++) {   // four steps of 2 rows per warp
+      double v[2][4];
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        const int r = w + 8 * (2 * h + k);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int cc = lane + 32 * q;
+          v[k][q] = (r < nb && cc < nc) ? C[(i0 + r) * (int64_t)d + j0 + cc] : 0.0;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        const int r = w + 8 * (2 * h + k);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int cc = lane + 32 * q;
+          const unsigned long long bits = (unsigned long long)__double_as_longlong(v[k][q]);
+          badf |= ((bits >> 52) & 0x7ff) == 0x7ff;
+          const float tc = f64_to_f32_trunc(v[k][q]);
+          cn[2 * h + k] = fmaf(tc, tc, cn[2 * h + k]);
+          if (r < nb && cc < nc) {
+            const float x = tc - s_o[cc];
+            tile[r][cc] = x;
+            cs[q] += x;
+          }
+        }
+      }
     }
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+      if (lane + 32 * q < nc) s_cs[w][lane + 32 * q] = cs[q];
     __syncthreads();
     // transposed write: group g of 4 columns for 64 balls; column sums
     const int ng = (nc + 3) / 4;
     for (int e = threadIdx.x; e < ng * kShadowBalls; e += kShadowNT) {
       const int g = e / kShadowBalls, r = e - g * kShadowBalls;
       if (r < nb) {
-        float v[4];
+        float x[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) v[k] = (4 * g + k < nc) ? tile[r][4 * g + k] : 0.0f;
-        X32[(int64_t)(j0 / 4 + g) * m_pad + i0 + r] = make_float4(v[0], v[1], v[2], v[3]);
+        for (int k = 0; k < 4; k++) x[k] = (4 * g + k < nc) ? tile[r][4 * g + k] : 0.0f;
+        X32[(int64_t)(j0 / 4 + g) * m_pad + i0 + r] = make_float4(x[0], x[1], x[2], x[3]);
       }
     }
     for (int cc = threadIdx.x; cc < nc; cc += kShadowNT) {
       float t = 0.0f;   // FP32 within the block (the mean is only a starting point)
-      for (int r = 0; r < nb; r++) t += tile[r][cc];
+#pragma unroll
+      for (int k = 0; k < kShadowNT / 32; k++) t += s_cs[k][cc];
       colpart[(int64_t)blockIdx.x * d + j0 + cc] = (double)t;
     }
     __syncthreads();
+  }
+  // E_i from the row sums of squares (lanes hold column subsets)
+#pragma unroll
+  for (int k = 0; k < kShadowBalls / 8; k++) {
+    float t = cn[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(MEB_FULLMASK, t, o);
+    const int r = w + 8 * k;
+    if (lane == 0 && r < nb) E32[i0 + r] = shadow_abs_err(t, d);
   }
   for (int r = threadIdx.x; r < nb; r += kShadowNT) {
     const double v = R[i0 + r];
@@ -87,8 +132,10 @@ __global__ void __launch_bounds__(kShadowNT) k_shadow(const double* __restrict__
   if (__syncthreads_or(badf) && threadIdx.x == 0) atomicOr(bad, 1);
 }
 
-// Mean centre c0 = c_0 + (1/m) sum_i x32_i: block j sums column j over the
-// block partials in a fixed tree order.
+// Origin o = trunc32(c_0) of the shadows, and the starting centre
+// c0 = c_0 + (1/m) sum_i x32_i (a mean to FP32 accuracy; exactly c_0 when
+// every centre equals c_0): block j sums column j over the block partials in
+// a fixed tree order.
 __global__ void k_shadow_mean(const double* __restrict__ C, const double* __restrict__ colpart,
                               int nb, int d, int64_t m, double* __restrict__ o,
                               double* __restrict__ c0) {
@@ -98,7 +145,7 @@ __global__ void k_shadow_mean(const double* __restrict__ C, const double* __rest
   for (int b = threadIdx.x; b < nb; b += 256) t += colpart[(int64_t)b * d + j];
   t = block_sum<256>(t, sh);
   if (threadIdx.x == 0) {
-    o[j] = C[j];
+    o[j] = (double)f64_to_f32_trunc(C[j]);
     c0[j] = C[j] + t / (double)m;
   }
 }
@@ -107,7 +154,7 @@ cudaError_t launch_shadow(const double* C, const double* R, int64_t m, int d, Bu
                           double* o, double* c0, int* bad, cudaStream_t s) {
   const int64_t m_pad = ((m + 255) / 256) * 256;
   const int nb = (int)((m + kShadowBalls - 1) / kShadowBalls);
-  k_shadow<<<nb, kShadowNT, 0, s>>>(C, R, m, d, m_pad, B.X32, B.R32, B.colsum_part, bad);
+  k_shadow<<<nb, kShadowNT, 0, s>>>(C, R, m, d, m_pad, B.X32, B.R32, B.E32, B.colsum_part, bad);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_shadow_mean<<<d, 256, 0, s>>>(C, B.colsum_part, nb, d, m, o, c0);
@@ -118,12 +165,14 @@ cudaError_t launch_shadow(const double* C, const double* R, int64_t m, int d, Bu
 // FP16 copy of the shadow in scaled units, x16 = fl16(x32 / s) (round to
 // nearest), built once s is known: rows of 8 halves (groups 2k and 2k+1 of
 // the FP32 shadow; zeros past d), layout [ceil(d4/2)][m_pad], and per ball
-// N = sum x16^2 (FP32 fmaf chain, the rounding model of the screen's own
-// sums).  The screens then read 8 bytes per group of 4 and no squares of x.
+// the error bound eps_i of meb_common.cuh (from N = sum x16^2 by an FP32
+// fmaf chain, and E_i).  The screens then read 8 bytes per group of 4 and one
+// bound per ball.
 // One thread per ball: a warp's reads and writes are 32 consecutive balls of
 // one row.
-__global__ void k_shadow16(const float4* __restrict__ X32, int64_t m_pad, int d4, float inv_s,
-                           uint4* __restrict__ X16, float* __restrict__ XN) {
+__global__ void k_shadow16(const float4* __restrict__ X32, const float* __restrict__ E32,
+                           int64_t m_pad, int d4, float inv_s, uint4* __restrict__ X16,
+                           float* __restrict__ EPS) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m_pad) return;
   const int d8 = (d4 + 1) / 2;
@@ -151,13 +200,13 @@ __global__ void k_shadow16(const float4* __restrict__ X32, int64_t m_pad, int d4
     o.w = *reinterpret_cast<const unsigned*>(&h[3]);
     X16[(int64_t)k * m_pad + i] = o;
   }
-  XN[i] = n;
+  EPS[i] = half_err(n, E32[i], inv_s, 8 * d8);
 }
 
 cudaError_t launch_shadow16(Buffers& B, int64_t m, int d, double inv_s, cudaStream_t s) {
   const int64_t m_pad = ((m + 255) / 256) * 256;
-  k_shadow16<<<(unsigned)(m_pad / 256), 256, 0, s>>>(B.X32, m_pad, (d + 3) / 4, (float)inv_s,
-                                                     B.X16, B.XN16);
+  k_shadow16<<<(unsigned)(m_pad / 256), 256, 0, s>>>(B.X32, B.E32, m_pad, (d + 3) / 4,
+                                                     (float)inv_s, B.X16, B.EPS16);
   B.launches += 1;
   return cudaGetLastError();
 }
@@ -180,7 +229,8 @@ struct PassArgs {
   int log_slot;
   const float4* X32;
   const uint4* X16;     // FP16 shadow scaled by 1/s (8 halves per row), or null
-  const float* XN16;    // per ball: FP32 sum of squares of its X16 row
+  const float* EPS16;   // per ball: FP16 shadow error bound eps_i (scaled units)
+  const float* E32;     // per ball: absolute FP32 shadow error E_i
   const float* R32;
   const int* slot;
   const int* sup_idx0; const int* sup_idx1;
@@ -312,7 +362,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_screen(PassArgs A, Buffers 
       Raw ra[NB], rb[NB];
       const int sl = A.slot[i];
       const float r32 = A.R32[i] * sc;
-      const float nx = HALF ? A.XN16[i] : 0.0f;
+      const float ex = HALF ? A.EPS16[i] : A.E32[i];
       const int64_t step = (int64_t)NB * A.m_pad;
       float2 Sa = make_float2(0.f, 0.f), Sb = Sa, Na = Sa, Nb = Sa;
       // two register batches in flight: load the next while summing this one
@@ -335,18 +385,18 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_screen(PassArgs A, Buffers 
         if (g >= nrows) break;
       }
       const float S = (Sa.x + Sa.y) + (Sb.x + Sb.y);
-      const float N = HALF ? nx : (Na.x + Na.y) + (Nb.x + Nb.y);
+      const float N = (Na.x + Na.y) + (Nb.x + Nb.y);   // FP32 shadow only
       if ((unsigned)sl < (unsigned)nsup && sidx[sl] == (int)i) {
         need = true;   // the ball holds a multiplier
       } else {
         // certify ||c_i - c|| <= r - r_i from the shadows
-        const float ub = HALF ? dist_ub16(S, N, yn, k4) : dist_ub(S, N, yn, k4);
+        const float ub = HALF ? dist_ub16(S, ex, yn, k4) : dist_ub(S, N, yn, ex, k4);
         const float lb = (rq - r32) - 6.0f * kU32 * (fabsf(rq) + fabsf(r32)) - 1e-30f;
         need = !(ub <= lb);
         if (need) {
           // violation ||c_i - c|| + r_i - r >= D_lb + r32 - rq - margins; with zero
           // multipliers ||Pi(z_i)||^2 >= max(0, violation / s)^2 / 2 (summed unscaled)
-          const float dl = HALF ? dist_lb16(S, N, yn, k4) : dist_lb(S, N, yn, k4);
+          const float dl = HALF ? dist_lb16(S, ex, yn, k4) : dist_lb(S, N, yn, ex, k4);
           const float v = ((dl + r32 - rq) - 3.0f * kU32 * (dl + fabsf(r32) + fabsf(rq))) * unsc;
           if (v > 0.0f) v2sum = fmaf(v, v, v2sum);
         }
@@ -562,30 +612,220 @@ __global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A, Buffers B) 
   if (last_block_ticket(&st->ctr_rows)) control_a_body(B, A.d, gridDim.x);
 }
 
-// Resident k_screen blocks on this GPU for a given dynamic shared memory size
-// (one wave of blocks), cached per size.
-static int screen_resident_blocks(int d4) {
-  static int cached_d4 = -1, cached = 0;
-  if (cached_d4 != d4) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per2 = 0;
-    const size_t sh1 = 16 * (size_t)(2 * ((d4 + 1) / 2));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_screen<false>, kPassThreads, sh1);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_screen<true>, kPassThreads, sh1);
-    if (per2 < per) per = per2;
-    if (per < 1) per = 1;
-    if (sms < 1) sms = 1;
-    cached = sms * per;
-    cached_d4 = d4;
-  }
-  return cached;
+// ---------------------------------------------------------------------------
+// FP16 screen through a bulk-copy pipeline (MEB_SCREEN=bulk).  One block per
+// SM keeps `nst` tiles in flight: a tile's shadow rows (16 B per ball and row), error
+// bounds, FP32 radii and slots are copied by the TMA engine into a shared
+// memory stage and signal its mbarrier; the block sums each ball from shared
+// memory, certifies and compacts as k_screen, and the stage is refilled with
+// the tile nst ahead once every thread has passed the tile's last barrier.
+// Same certificates as k_screen<true> (same sums in the same order).  It
+// measured slower than the register-batched screen on GB300 (one block of
+// 8 warps per SM leaves each tile's compute and compaction exposed), so it is
+// not the default.
+constexpr int kBulkSmemBudget = 200 * 1024;
+constexpr int kBulkMaxStages = 4;
+
+// stage: [nrows][256] uint4 | eps[256] | r32[256] | slot[256]
+__host__ __device__ inline int bulk_stage_bytes(int nrows) { return nrows * 4096 + 3 * 1024; }
+
+static int bulk_stages(int d) {
+  const int nrows = ((d + 3) / 4 + 1) / 2;
+  int st = (kBulkSmemBudget - 32 * nrows - 64) / bulk_stage_bytes(nrows);
+  return st > kBulkMaxStages ? kBulkMaxStages : st;
 }
 
-int pass_blocks(int64_t m, int d, int* tiles_per_block) {
+static size_t bulk_smem(int d, int nst) {
+  const int nrows = ((d + 3) / 4 + 1) / 2;
+  return (size_t)nst * bulk_stage_bytes(nrows) + 32 * (size_t)nrows + 8 * kBulkMaxStages;
+}
+
+__global__ void __launch_bounds__(kPassThreads, 1) k_screen_bulk(PassArgs A, Buffers B, int nst) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  DevState* st = A.st;
+  if (st->status != 0 || st->action == ACT_DONE || st->reuse_lists) return;
+  if (A.log_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0) st->screen_log[A.log_slot] = 1;
+  const int d4 = A.d4;
+  const int nrows = (d4 + 1) / 2;
+  const int sb = bulk_stage_bytes(nrows);
+  unsigned char* stages = smem_raw;
+  float4* s_y = reinterpret_cast<float4*>(smem_raw + (size_t)nst * sb);   // 2 nrows groups
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)nst * sb + 32 * nrows);
+  __shared__ int s_wc[kPassWarps];
+  __shared__ float s_v2[kPassWarps];
+  const float sc = (float)st->inv_s;
+  const float4* y4 = reinterpret_cast<const float4*>(A.y32);
+  for (int g = threadIdx.x; g < 2 * nrows; g += kPassThreads) {
+    const float4 y = g < d4 ? y4[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+    s_y[g] = make_float4(-y.x * sc, -y.y * sc, -y.z * sc, -y.w * sc);   // -y, scaled
+  }
+  const int cur = st->sup_cur;
+  const int nsup = st->nsup;
+  const int* sidx = cur ? A.sup_idx1 : A.sup_idx0;
+  const float rq = st->rq32 * sc, yn = st->yn32 * sc;
+  const float unsc = (float)st->s;
+  float v2sum = 0.0f;
+  const int k8 = 8 * nrows;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t ntiles = (A.m + kPassThreads - 1) / kPassThreads;
+  const int64_t t0 = (int64_t)blockIdx.x * A.tiles_per_block;
+  const int64_t t1 = imin64(ntiles, t0 + A.tiles_per_block);
+  const int ntl = t1 > t0 ? (int)(t1 - t0) : 0;
+  const int64_t base = t0 * kPassThreads;
+  if (tid == 0) {
+    for (int q = 0; q < nst; q++) mbar_init(&bars[q], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // warp 0: copies of local tile k into stage k % nst; lane 0 announces the
+  // bytes, then lanes 0 .. nrows+2 issue one copy each (in parallel)
+  auto issue = [&](int k) {
+    const int q = k % nst;
+    const int64_t b0 = (t0 + k) * kPassThreads;
+    const int nbt = (int)imin64(kPassThreads, A.m - b0);
+    const uint32_t rowb = 16u * (uint32_t)nbt;
+    const uint32_t smallb = (4u * (uint32_t)nbt + 15u) & ~15u;
+    unsigned char* dst = stages + (size_t)q * sb;
+    if (lane == 0) mbar_arrive_expect_tx(&bars[q], (uint32_t)nrows * rowb + 3u * smallb);
+    __syncwarp();
+    for (int r = lane; r < nrows + 3; r += 32) {
+      if (r < nrows)
+        bulk_g2s(dst + (size_t)r * 4096, A.X16 + (int64_t)r * A.m_pad + b0, rowb, &bars[q]);
+      else if (r == nrows)
+        bulk_g2s(dst + (size_t)nrows * 4096, A.EPS16 + b0, smallb, &bars[q]);
+      else if (r == nrows + 1)
+        bulk_g2s(dst + (size_t)nrows * 4096 + 1024, A.R32 + b0, smallb, &bars[q]);
+      else
+        bulk_g2s(dst + (size_t)nrows * 4096 + 2048, A.slot + b0, smallb, &bars[q]);
+    }
+  };
+  if (w == 0)
+    for (int k = 0; k < nst && k < ntl; k++) issue(k);
+  int count = 0;
+  for (int k = 0; k < ntl; k++) {
+    const int q = k % nst;
+    const bool ok = mbar_wait_bounded(&bars[q], (uint32_t)((k / nst) & 1));
+    if (__syncthreads_or(!ok)) {
+      // give up: record it, let the copies in flight land (bounded), return
+      if (tid == 0) {
+        st->status = kStatusWaitTimeout;
+        for (int j = k; j < ntl && j < k + nst; j++)
+          mbar_wait_bounded(&bars[j % nst], (uint32_t)((j / nst) & 1));
+      }
+      return;
+    }
+    const unsigned char* sbase = stages + (size_t)q * sb;
+    const int64_t i = (t0 + k) * kPassThreads + tid;
+    bool need = false;
+    if (i < A.m) {
+      const uint4* sx = reinterpret_cast<const uint4*>(sbase);
+      const float ex = reinterpret_cast<const float*>(sbase + (size_t)nrows * 4096)[tid];
+      const float r32 = reinterpret_cast<const float*>(sbase + (size_t)nrows * 4096 + 1024)[tid] * sc;
+      const int sl = reinterpret_cast<const int*>(sbase + (size_t)nrows * 4096 + 2048)[tid];
+      float2 Sa = make_float2(0.f, 0.f), Sb = Sa;
+#pragma unroll 4
+      for (int r = 0; r < nrows; r++) {
+        const uint4 hv = sx[r * kPassThreads + tid];
+        const float4 y0 = s_y[2 * r], y1 = s_y[2 * r + 1];
+        acc_pair(h2f(hv.x), make_float2(y0.x, y0.y), Sa);
+        acc_pair(h2f(hv.y), make_float2(y0.z, y0.w), Sb);
+        acc_pair(h2f(hv.z), make_float2(y1.x, y1.y), Sa);
+        acc_pair(h2f(hv.w), make_float2(y1.z, y1.w), Sb);
+      }
+      const float S = (Sa.x + Sa.y) + (Sb.x + Sb.y);
+      if ((unsigned)sl < (unsigned)nsup && sidx[sl] == (int)i) {
+        need = true;   // the ball holds a multiplier
+      } else {
+        const float ub = dist_ub16(S, ex, yn, k8);
+        const float lb = (rq - r32) - 6.0f * kU32 * (fabsf(rq) + fabsf(r32)) - 1e-30f;
+        need = !(ub <= lb);
+        if (need) {
+          const float dl = dist_lb16(S, ex, yn, k8);
+          const float v = ((dl + r32 - rq) - 3.0f * kU32 * (dl + fabsf(r32) + fabsf(rq))) * unsc;
+          if (v > 0.0f) v2sum = fmaf(v, v, v2sum);
+        }
+      }
+    }
+    const unsigned msk = __ballot_sync(MEB_FULLMASK, need);
+    if (lane == 0) s_wc[w] = __popc(msk);
+    __syncthreads();
+    // every thread is past its reads of stage q: refill it
+    if (w == 0 && k + nst < ntl) {
+      fence_proxy_async_smem();   // each issuing lane orders the reads before its copy
+      __syncwarp();
+      issue(k + nst);
+    }
+    int off = 0, tot = 0;
+#pragma unroll
+    for (int kk = 0; kk < kPassWarps; kk++) {
+      off += (kk < w) ? s_wc[kk] : 0;
+      tot += s_wc[kk];
+    }
+    if (need) {
+      const int64_t o = base + count + off + __popc(msk & ((1u << lane) - 1u));
+      A.unc_idx[o] = (int)i;
+    }
+    count += tot;
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v2sum += __shfl_xor_sync(MEB_FULLMASK, v2sum, o);
+  if (lane == 0) s_v2[w] = v2sum;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.0f;
+    for (int kk = 0; kk < kPassWarps; kk++) t += s_v2[kk];
+    A.unc_cnt[blockIdx.x] = count;
+    A.vlb_part[blockIdx.x] = t;
+  }
+  if (last_block_ticket(&st->ctr_screen)) early_body(B, A.d, gridDim.x);
+}
+
+int screen_variant(const Buffers& B, int d) {
+  if (!B.use_x16) return 0;
+  return (B.bulk && bulk_stages(d) >= 2) ? 2 : 1;
+}
+
+// Resident k_screen blocks on this GPU for a given dynamic shared memory size
+// (one wave of blocks), cached per size.
+static int screen_resident_blocks(int d, int variant) {
+  // one cached entry per variant (and device)
+  static int cached_dev[3] = {-1, -1, -1}, cached_d[3] = {-1, -1, -1}, cached[3] = {0, 0, 0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (cached_d[variant] != d || cached_dev[variant] != dev) {
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int d4 = (d + 3) / 4;
+    const size_t sh1 = 16 * (size_t)(2 * ((d4 + 1) / 2));
+    if (variant == 2) per = 1;
+    else if (variant == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_screen<true>, kPassThreads, sh1);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_screen<false>, kPassThreads, sh1);
+    if (per < 1) per = 1;
+    if (sms < 1) sms = 1;
+    cached[variant] = sms * per;
+    cached_d[variant] = d;
+    cached_dev[variant] = dev;
+  }
+  return cached[variant];
+}
+
+// Host set-up outside any stream capture: the grid of the current variant
+// and the shared-memory size of the bulk-copy screen.
+cudaError_t prepare_pass(const Buffers& B, int d) {
+  int tpb;
+  const int variant = screen_variant(B, d);
+  pass_blocks(1, d, variant, &tpb);
+  if (variant == 2) {
+    const size_t shb = bulk_smem(d, bulk_stages(d));
+    return cudaFuncSetAttribute(k_screen_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
+  }
+  return cudaSuccess;
+}
+
+int pass_blocks(int64_t m, int d, int variant, int* tiles_per_block) {
   const int64_t ntiles = (m + kPassThreads - 1) / kPassThreads;
-  const int64_t target = screen_resident_blocks((d + 3) / 4);
+  const int64_t target = screen_resident_blocks(d, variant);
   const int64_t cap = target < kMaxPassBlocks ? target : kMaxPassBlocks;
   int64_t tpb = (ntiles + cap - 1) / cap;
   if (tpb < 1) tpb = 1;
@@ -601,8 +841,9 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
   const int d4 = (d + 3) / 4;
   A.m_pad = ((m + 255) / 256) * 256;
   A.d = d; A.d4 = d4;
-  const int nb = pass_blocks(m, d, &A.tiles_per_block);
-  A.X32 = B.X32; A.X16 = B.use_x16 ? B.X16 : nullptr; A.XN16 = B.XN16; A.R32 = B.R32; A.slot = B.slot;
+  const int variant = screen_variant(B, d);
+  const int nb = pass_blocks(m, d, variant, &A.tiles_per_block);
+  A.X32 = B.X32; A.X16 = B.use_x16 ? B.X16 : nullptr; A.EPS16 = B.EPS16; A.E32 = B.E32; A.R32 = B.R32; A.slot = B.slot;
   A.sup_idx0 = B.sup_idx[0]; A.sup_idx1 = B.sup_idx[1];
   A.sup_u0 = B.sup_u[0]; A.sup_u1 = B.sup_u[1];
   A.sup_v0 = B.sup_v[0]; A.sup_v1 = B.sup_v[1];
@@ -626,8 +867,14 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
   if (ev0 || ev1) cudaStreamIsCapturing(s, &cap);
   const unsigned evf = (cap == cudaStreamCaptureStatusActive) ? cudaEventRecordExternal : 0u;
   if (ev0) cudaEventRecordWithFlags(ev0, s, evf);
-  if (A.X16) k_screen<true><<<nb, kPassThreads, sh1, s>>>(A, B);
-  else k_screen<false><<<nb, kPassThreads, sh1, s>>>(A, B);
+  if (variant == 2) {   // its shared-memory attribute is set by prepare_pass
+    const int nst = bulk_stages(d);
+    k_screen_bulk<<<nb, kPassThreads, bulk_smem(d, nst), s>>>(A, B, nst);
+  } else if (variant == 1) {
+    k_screen<true><<<nb, kPassThreads, sh1, s>>>(A, B);
+  } else {
+    k_screen<false><<<nb, kPassThreads, sh1, s>>>(A, B);
+  }
   if (ev1) cudaEventRecordWithFlags(ev1, s, evf);
   const size_t sh2 = 8 * (size_t)d;
   if (sh2 > 48 * 1024) {
@@ -797,7 +1044,7 @@ __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buff
 
 cudaError_t launch_support_rows(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s) {
   int tpb;
-  const int nb = pass_blocks(m, d, &tpb);
+  const int nb = pass_blocks(m, d, screen_variant(B, d), &tpb);
   k_compact_S<<<(nb + 7) / 8, 256, 0, s>>>(B, nb, (int64_t)tpb * kPassThreads);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -821,7 +1068,7 @@ struct FeasArgs {
   const double* C; const double* R;
   int64_t m, m_pad;
   int d, d4;
-  const float4* X32; const float* R32;
+  const float4* X32; const float* R32; const float* E32;
   const double* c;      // query centre (unscaled)
   const float* y32;     // trunc32(c - o), 4*d4 floats
   const float* ynp;     // device: upper bound on ||y32||
@@ -859,8 +1106,9 @@ __global__ void __launch_bounds__(kFeasNT) k_feas_a(FeasArgs A) {
     const int k4 = 4 * A.d4;
     const float yn = *A.ynp;
     const float r32 = A.R32[i];   // r32 <= r_i <= r32 (1 + 2^-23)/(1 - 2^-23)
-    const float eu = (r32 * (1.0f + 5.0f * kU32) + dist_ub(S, N, yn, k4)) * (1.0f + 2.0f * kU32);
-    const float el = (r32 + dist_lb(S, N, yn, k4)) * (1.0f - 2.0f * kU32);
+    const float E = A.E32[i];
+    const float eu = (r32 * (1.0f + 5.0f * kU32) + dist_ub(S, N, yn, E, k4)) * (1.0f + 2.0f * kU32);
+    const float el = (r32 + dist_lb(S, N, yn, E, k4)) * (1.0f - 2.0f * kU32);
     A.eub[i] = eu;
     A.elb[i] = el;
     lbv = el;
@@ -1090,12 +1338,12 @@ __global__ void k_query_shadow(const double* __restrict__ c, const double* __res
 cudaError_t launch_feas_cert(const double* C, const double* R, int64_t m, int d, const double* c,
                              double r, double eps, int mode, int want_max, Buffers& B,
                              double* dmax_out, int64_t* argmax_out, int64_t* nviol_out,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool reuse_bounds) {
   FeasArgs A;
   A.C = C; A.R = R; A.m = m;
   A.m_pad = ((m + 255) / 256) * 256;
   A.d = d; A.d4 = (d + 3) / 4;
-  A.X32 = B.X32; A.R32 = B.R32;
+  A.X32 = B.X32; A.R32 = B.R32; A.E32 = B.E32;
   A.c = c;
   A.y32 = B.fq_y32;
   A.r = r; A.eps = eps; A.mode = mode; A.want_max = want_max;
@@ -1104,16 +1352,26 @@ cudaError_t launch_feas_cert(const double* C, const double* R, int64_t m, int d,
   A.L = B.fe_L;
   A.ynp = B.fe_L + 1;
   const int nb = (int)((m + kFeasNT - 1) / kFeasNT);
-  k_query_shadow<<<1, 256, 0, s>>>(c, B.vec.o, d, B.fq_y32, B.fe_L + 1);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const size_t sha = 16 * (size_t)A.d4;
-  if (sha > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_feas_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sha);
+  cudaError_t e;
+  int launched = 3;
+  // the bounds on e_i depend only on c: a second check at the same centre
+  // (reuse_bounds) skips the shadow sweep
+  if (!reuse_bounds) {
+    k_query_shadow<<<1, 256, 0, s>>>(c, B.vec.o, d, B.fq_y32, B.fe_L + 1);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    const size_t sha = 16 * (size_t)A.d4;
+    if (sha > 48 * 1024) {
+      e = cudaFuncSetAttribute(k_feas_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sha);
+      if (e != cudaSuccess) return e;
+    }
+    k_feas_a<<<nb, kFeasNT, sha, s>>>(A);
+    launched += 2;
   }
-  k_feas_a<<<nb, kFeasNT, sha, s>>>(A);
-  if (want_max) k_feas_L<<<1, 256, 0, s>>>(B.fe_blb, nb, B.fe_L);
+  if (want_max) {
+    k_feas_L<<<1, 256, 0, s>>>(B.fe_blb, nb, B.fe_L);
+    launched += 1;
+  }
   const size_t shb = 8 * (size_t)d;
   if (shb > 48 * 1024) {
     e = cudaFuncSetAttribute(k_feas_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
@@ -1123,7 +1381,7 @@ cudaError_t launch_feas_cert(const double* C, const double* R, int64_t m, int d,
   k_feas_final<<<1, 256, 0, s>>>(B.feas_part, B.feas_ipart, B.feas_cnt, nb, dmax_out, argmax_out,
                                  nviol_out);
   k_gather_lists<<<(nb + 255) / 256, 256, 0, s>>>(B.feas_cnt, B.list_tmp, nb, kFeasNT, B.viol, m);
-  B.launches += want_max ? 6 : 5;
+  B.launches += launched;
   return cudaGetLastError();
 }
 

@@ -133,10 +133,10 @@ __global__ void k_syrk_reduce(Buffers B, int d, int force) {
 
 // One block: assemble H (packed lower, smem), Cholesky, solve H dx = -g,
 // then set the first line-search trial x + dx.
-__global__ void __launch_bounds__(256) k_newton_chol(Buffers B, int d) {
+// FP64 Cholesky solve of H dx = -g by one block of 256 threads, with Lp
+// (n(n+1)/2 doubles, packed lower: row i at i(i+1)/2) in shared memory.
+__device__ void newton_chol_body(const Buffers& B, int d, double* Lp) {
   DevState* st = B.st;
-  if (st->status != 0 || st->action != ACT_NEWTON || !st->need_fp64_solve) return;
-  extern __shared__ double Lp[];   // packed lower: row i at i(i+1)/2
   __shared__ double sh[32];
   __shared__ int s_fail;
   const DevVecs& V = B.vec;
@@ -218,6 +218,13 @@ __global__ void __launch_bounds__(256) k_newton_chol(Buffers B, int d) {
   set_trial(st, V, d, sh);
 }
 
+__global__ void __launch_bounds__(256) k_newton_chol(Buffers B, int d) {
+  DevState* st = B.st;
+  if (st->status != 0 || st->action != ACT_NEWTON || !st->need_fp64_solve) return;
+  extern __shared__ double Lp[];
+  newton_chol_body(B, d, Lp);
+}
+
 // The Newton direction dx (in shared memory) becomes the first line-search
 // trial: dx, gdx = g.dx, xt = x + dx and the trial's query shadow.
 __device__ void newton_accept(DevState* st, const DevVecs& V, int d, const double* s_x,
@@ -249,6 +256,10 @@ __device__ void newton_accept(DevState* st, const DevVecs& V, int d, const doubl
 __global__ void __launch_bounds__(256) k_newton_gj(Buffers B, int d) {
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_NEWTON) return;
+  if (st->force_fp64_solve) {   // k_newton_chol follows
+    if (threadIdx.x == 0) st->need_fp64_solve = 1;
+    return;
+  }
   extern __shared__ float A[];    // n x n, row-major
   __shared__ double sh[32];
   __shared__ int s_fail;
@@ -397,6 +408,11 @@ __device__ __forceinline__ float2 block_sum2f(float a, float b, float2* sh8) {
 __global__ void __launch_bounds__(256, 1) k_newton_gj_reg(Buffers B, int d) {
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_NEWTON) return;
+  extern __shared__ double dyn_Lp[];   // the Cholesky fallback's factor
+  if (st->force_fp64_solve) {
+    newton_chol_body(B, d, dyn_Lp);
+    return;
+  }
   __shared__ float s_row[2][kGjRegN], s_col[2][kGjRegN];
   __shared__ float s_b[kGjRegN], s_bh[kGjRegN], s_bl[kGjRegN], s_xh[kGjRegN], s_xl[kGjRegN];
   __shared__ float2 s_red[8];
@@ -572,12 +588,38 @@ __global__ void __launch_bounds__(256, 1) k_newton_gj_reg(Buffers B, int d) {
   }
   if (tid == 0) st->gj_inverses += 1;
   if (!ok) {
-    if (tid == 0) st->need_fp64_solve = 1;
+    // the FP64 Cholesky in the same launch (dynamic shared memory n(n+1)/2 doubles)
+    __syncthreads();
+    newton_chol_body(B, d, dyn_Lp);
     return;
   }
   for (int i = tid; i < kGjRegN; i += 256) s_x[i] = (double)s_xh[i] + (double)s_xl[i];
   __syncthreads();
   newton_accept(st, V, d, s_x, sh);
+}
+
+// Launches per Newton step of the dense path: SYRK, its reduction and the
+// solve (n <= kGjRegN: Gauss-Jordan with the Cholesky fallback inside), or
+// SYRK, reduction, shared-memory Gauss-Jordan and a separate Cholesky.
+int newton_dense_launches(int d) { return d + 1 <= kGjRegN ? 3 : 4; }
+
+// Host set-up outside any stream capture: dynamic shared memory limits.
+cudaError_t prepare_newton(int d) {
+  const int n = d + 1;
+  if (n > kMaxDenseN) return cudaSuccess;   // matrix-free path
+  const size_t shc = sizeof(double) * (size_t)n * (n + 1) / 2;
+  cudaError_t e = cudaSuccess;
+  if (n <= kGjRegN) {
+    if (shc > 48 * 1024)
+      e = cudaFuncSetAttribute(k_newton_gj_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shc);
+    return e;
+  }
+  const size_t shg = sizeof(float) * (size_t)n * n;
+  if (shg > 48 * 1024)
+    e = cudaFuncSetAttribute(k_newton_gj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shg);
+  if (e == cudaSuccess && shc > 48 * 1024)
+    e = cudaFuncSetAttribute(k_newton_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shc);
+  return e;
 }
 
 cudaError_t launch_newton_dense(Buffers& B, int d, cudaStream_t s) {
@@ -588,26 +630,15 @@ cudaError_t launch_newton_dense(Buffers& B, int d, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   k_syrk_reduce<<<64, 256, 0, s>>>(B, d, 0);
   const int n = d + 1;
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  const size_t shc = sizeof(double) * (size_t)n * (n + 1) / 2;
   if (n <= kGjRegN) {
-    k_newton_gj_reg<<<1, 256, 0, s>>>(B, d);
+    k_newton_gj_reg<<<1, 256, shc, s>>>(B, d);
   } else {
-    const size_t shg = sizeof(float) * (size_t)n * n;
-    if (shg > 48 * 1024) {
-      e = cudaFuncSetAttribute(k_newton_gj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shg);
-      if (e != cudaSuccess) return e;
-    }
-    k_newton_gj<<<1, 256, shg, s>>>(B, d);
+    k_newton_gj<<<1, 256, sizeof(float) * (size_t)n * n, s>>>(B, d);
+    // FP64 Cholesky only when the FP32 inverse could not be refined
+    k_newton_chol<<<1, 256, shc, s>>>(B, d);
   }
-  // FP64 Cholesky only when the FP32 inverse could not be refined
-  const size_t sh = sizeof(double) * (size_t)n * (n + 1) / 2;
-  if (sh > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_newton_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-    if (e != cudaSuccess) return e;
-  }
-  k_newton_chol<<<1, 256, sh, s>>>(B, d);
-  B.launches += 4;
+  B.launches += newton_dense_launches(d);
   return cudaGetLastError();
 }
 

@@ -164,6 +164,22 @@ def test_solve_closed_forms():
     assert abs(g["r"] - np.sqrt((n - 1) / n)) <= 1e-9 and g["n_active"] == n
 
 
+def test_fp64_newton_path():
+    """newton_fp64 = 1 solves every dense Newton system by the FP64 Cholesky
+    (the fallback of the FP32 Gauss-Jordan path): same solution."""
+    C, R = workloads.cube(20_000, 40, 31, 0.05)
+    p = meb.params_default()
+    p.newton_fp64 = 1
+    g64 = meb.solve(C, R, params=p)
+    assert g64["status"] == 0
+    assert g64["newton_fp64"] > 0 and g64["newton_inverses"] == 0
+    g = meb.solve(C, R)
+    assert g["newton_fp64"] == 0 and g["newton_inverses"] > 0
+    o = oracle.solve(C, R, tol=1e-12)
+    compare_solution(C, R, g64, o)
+    compare_solution(C, R, g, o)
+
+
 def test_sphere_cg_path():
     C, R, ctr = workloads.sphere(6000, 300, 4)
     g = meb.solve(C, R)
@@ -197,21 +213,42 @@ def test_device_pointer_path():
 
 
 def test_screen_shadows_agree(monkeypatch):
-    """Solves screen the FP16 shadow; MEB_SCREEN=fp32 screens the FP32 one.
-    Both certificates only decide which balls skip the FP64 evaluation, so the
-    two solves agree to the solve tolerance and keep the same active set."""
+    """Solves screen the FP16 shadow with register batches; MEB_SCREEN=bulk
+    screens it through the bulk-copy pipeline and MEB_SCREEN=fp32 screens the
+    FP32 shadow.  The certificates only decide which balls skip
+    the FP64 evaluation, so the solves agree to the solve tolerance and keep
+    the same active set."""
     C, R = workloads.cube(30_000, 40, 23, 0.05)
-    monkeypatch.setenv("MEB_SCREEN", "fp32")
-    c32 = meb.Context(0)
+    ctxs = {}
+    for mode in ("fp32", "bulk", None):
+        if mode is None:
+            monkeypatch.delenv("MEB_SCREEN", raising=False)
+        else:
+            monkeypatch.setenv("MEB_SCREEN", mode)
+        ctxs[mode] = meb.Context(0)
     monkeypatch.delenv("MEB_SCREEN", raising=False)
-    c16 = meb.Context(0)
-    a = meb.solve(C, R, ctx=c32)
-    b = meb.solve(C, R, ctx=c16)
+    res = {k: meb.solve(C, R, ctx=c) for k, c in ctxs.items()}
     ref = oracle.solve(C, R)
-    for res in (a, b):
-        assert res["status"] == 0 and res["kkt_max"] <= 1e-10
-        assert abs(res["r"] - ref["r"]) <= 1e-8 * ref["r"]
-    assert np.array_equal(a["active"], b["active"])
+    for k, r in res.items():
+        assert r["status"] == 0 and r["kkt_max"] <= 1e-10, k
+        assert abs(r["r"] - ref["r"]) <= 1e-8 * ref["r"], k
+        assert np.array_equal(r["active"], res[None]["active"]), k
+
+
+@pytest.mark.parametrize("mode", [None, "bulk"])
+def test_screen_ragged_tiles(monkeypatch, mode):
+    """Both FP16 screens on sizes whose last tile is partial (m not a multiple
+    of 256) and on d that leaves padding in the last FP16 row."""
+    if mode:
+        monkeypatch.setenv("MEB_SCREEN", mode)
+    ctx = meb.Context(0)
+    monkeypatch.delenv("MEB_SCREEN", raising=False)
+    for m, d, seed in [(1, 5, 1), (257, 3, 2), (5000 - 37, 17, 3), (20_011, 100, 4)]:
+        C, R = workloads.cube(m, d, seed, 0.05)
+        g = meb.solve(C, R, ctx=ctx)
+        o = oracle.solve(C, R, tol=1e-12)
+        assert g["status"] == 0
+        compare_solution(C, R, g, o)
 
 
 def test_tick_loops_agree(monkeypatch):
