@@ -15,6 +15,14 @@ namespace meb {
 
 __host__ __device__ static inline int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 
+// Programmatic dependent launch: wait for the preceding grid (a no-op when the
+// kernel was launched without the attribute), then let the next grid be
+// scheduled (it waits for this grid in turn).
+__device__ __forceinline__ void pdl_wait_and_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(MEB_FULLMASK, v, o);

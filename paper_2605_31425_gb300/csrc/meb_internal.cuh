@@ -181,6 +181,27 @@ struct Buffers {
 };
 
 // ---- launch wrappers: streaming kernels (meb_pass.cu) ----
+// Launch of a controller-tick kernel with programmatic dependent launch: the
+// kernel may be scheduled while its predecessor in the stream finishes; it
+// waits (griddepcontrol.wait, pdl_wait) for the predecessor's completion and
+// memory before it reads anything.  In a captured graph the dependency
+// becomes a programmatic edge.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // screen kernels: 0 FP32 shadow, 1 FP16 shadow (register batches),
 // 2 FP16 shadow through a bulk-copy (TMA) pipeline in shared memory
 int screen_variant(const Buffers& B, int d);

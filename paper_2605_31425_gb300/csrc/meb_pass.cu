@@ -314,6 +314,7 @@ __device__ __forceinline__ void sum_batch(const typename ScreenRaw<HALF>::T* r,
 
 template <bool HALF>
 __global__ void __launch_bounds__(kPassThreads, 4) k_screen(PassArgs A, Buffers B) {
+  pdl_wait_and_release();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DevState* st = A.st;
   // reuse_lists: the point is the one of the last screen and only the
@@ -432,6 +433,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_screen(PassArgs A, Buffers 
 }
 
 __global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A, Buffers B) {
+  pdl_wait_and_release();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DevState* st = A.st;
   if (st->status != 0 || st->action == ACT_DONE || st->action == ACT_TRIAL_EARLY) return;
@@ -641,6 +643,7 @@ static size_t bulk_smem(int d, int nst) {
 }
 
 __global__ void __launch_bounds__(kPassThreads, 1) k_screen_bulk(PassArgs A, Buffers B, int nst) {
+  pdl_wait_and_release();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   DevState* st = A.st;
   if (st->status != 0 || st->action == ACT_DONE || st->reuse_lists) return;
@@ -869,19 +872,21 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
   if (ev0) cudaEventRecordWithFlags(ev0, s, evf);
   if (variant == 2) {   // its shared-memory attribute is set by prepare_pass
     const int nst = bulk_stages(d);
-    k_screen_bulk<<<nb, kPassThreads, bulk_smem(d, nst), s>>>(A, B, nst);
+    e = launch_pdl(k_screen_bulk, dim3(nb), dim3(kPassThreads), bulk_smem(d, nst), s, A, B, nst);
   } else if (variant == 1) {
-    k_screen<true><<<nb, kPassThreads, sh1, s>>>(A, B);
+    e = launch_pdl(k_screen<true>, dim3(nb), dim3(kPassThreads), sh1, s, A, B);
   } else {
-    k_screen<false><<<nb, kPassThreads, sh1, s>>>(A, B);
+    e = launch_pdl(k_screen<false>, dim3(nb), dim3(kPassThreads), sh1, s, A, B);
   }
+  if (e != cudaSuccess) return e;
   if (ev1) cudaEventRecordWithFlags(ev1, s, evf);
   const size_t sh2 = 8 * (size_t)d;
   if (sh2 > 48 * 1024) {
     e = cudaFuncSetAttribute(k_rows64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh2);
     if (e != cudaSuccess) return e;
   }
-  k_rows64<<<nb, kPassThreads, sh2, s>>>(A, B);
+  e = launch_pdl(k_rows64, dim3(nb), dim3(kPassThreads), sh2, s, A, B);
+  if (e != cudaSuccess) return e;
   B.launches += 2;
   return cudaGetLastError();
 }
@@ -890,6 +895,7 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
 // Ordered gather of the pass candidates (block b's segment at b*T*256) into
 // the support list S.
 __global__ void __launch_bounds__(256) k_compact_S(Buffers B, int nb, int64_t seg) {
+  pdl_wait_and_release();
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_GRAD) return;
   __shared__ int s_w[8];
@@ -931,6 +937,7 @@ __global__ void __launch_bounds__(256) k_compact_S(Buffers B, int nb, int64_t se
 constexpr int kSvecStage = 64;   // support rows staged per round in shared memory
 
 __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buffers B, int d) {
+  pdl_wait_and_release();
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_GRAD) return;
   const int nS = st->nS;
@@ -1045,10 +1052,13 @@ __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buff
 cudaError_t launch_support_rows(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s) {
   int tpb;
   const int nb = pass_blocks(m, d, screen_variant(B, d), &tpb);
-  k_compact_S<<<(nb + 7) / 8, 256, 0, s>>>(B, nb, (int64_t)tpb * kPassThreads);
+  cudaError_t e0 = launch_pdl(k_compact_S, dim3((nb + 7) / 8), dim3(256), 0, s, B, nb,
+                              (int64_t)tpb * kPassThreads);
+  if (e0 != cudaSuccess) return e0;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_svec<<<kSvecBlocks, 256, 0, s>>>(C, B, d);
+  e = launch_pdl(k_svec, dim3(kSvecBlocks), dim3(256), 0, s, C, B, d);
+  if (e != cudaSuccess) return e;
   B.launches += 2;
   return cudaGetLastError();
 }

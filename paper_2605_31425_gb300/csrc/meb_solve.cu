@@ -34,6 +34,7 @@ cudaError_t launch_tick_control(Buffers& B, int64_t m, int d, cudaStream_t s) {
 constexpr int kSyrkGroups = 24;
 
 __global__ void __launch_bounds__(256) k_syrk(Buffers B, int d, int force) {
+  pdl_wait_and_release();
   DevState* st = B.st;
   if (!force && (st->status != 0 || st->action != ACT_NEWTON)) return;
   const int nt = (d + kSyrkTile - 1) / kSyrkTile;
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(256) k_syrk(Buffers B, int d, int force) {
 
 // Sum the group partials (in group order) into B.H's lower triangle block (rows/cols 1..d).
 __global__ void k_syrk_reduce(Buffers B, int d, int force) {
+  pdl_wait_and_release();
   DevState* st = B.st;
   if (!force && (st->status != 0 || st->action != ACT_NEWTON)) return;
   // H = tau/sigma I + sigma (n_I I + 1/2 [[n_M, sum w^T], [sum w, sum(1+t) I - SY]]),
@@ -219,6 +221,7 @@ __device__ void newton_chol_body(const Buffers& B, int d, double* Lp) {
 }
 
 __global__ void __launch_bounds__(256) k_newton_chol(Buffers B, int d) {
+  pdl_wait_and_release();
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_NEWTON || !st->need_fp64_solve) return;
   extern __shared__ double Lp[];
@@ -254,6 +257,7 @@ __device__ void newton_accept(DevState* st, const DevVecs& V, int d, const doubl
 // Sets need_fp64_solve when a pivot is not positive or the refinement does
 // not converge; otherwise sets up the first line-search trial.
 __global__ void __launch_bounds__(256) k_newton_gj(Buffers B, int d) {
+  pdl_wait_and_release();
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_NEWTON) return;
   if (st->force_fp64_solve) {   // k_newton_chol follows
@@ -406,6 +410,7 @@ __device__ __forceinline__ float2 block_sum2f(float a, float b, float2* sh8) {
 }
 
 __global__ void __launch_bounds__(256, 1) k_newton_gj_reg(Buffers B, int d) {
+  pdl_wait_and_release();
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_NEWTON) return;
   extern __shared__ double dyn_Lp[];   // the Cholesky fallback's factor
@@ -625,19 +630,20 @@ cudaError_t prepare_newton(int d) {
 cudaError_t launch_newton_dense(Buffers& B, int d, cudaStream_t s) {
   const int nt = (d + kSyrkTile - 1) / kSyrkTile;
   const int ntri = nt * (nt + 1) / 2;
-  k_syrk<<<dim3(ntri, kSyrkGroups), 256, 0, s>>>(B, d, 0);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_pdl(k_syrk, dim3(ntri, kSyrkGroups), dim3(256), 0, s, B, d, 0);
   if (e != cudaSuccess) return e;
-  k_syrk_reduce<<<64, 256, 0, s>>>(B, d, 0);
+  e = launch_pdl(k_syrk_reduce, dim3(64), dim3(256), 0, s, B, d, 0);
+  if (e != cudaSuccess) return e;
   const int n = d + 1;
   const size_t shc = sizeof(double) * (size_t)n * (n + 1) / 2;
   if (n <= kGjRegN) {
-    k_newton_gj_reg<<<1, 256, shc, s>>>(B, d);
+    e = launch_pdl(k_newton_gj_reg, dim3(1), dim3(256), shc, s, B, d);
   } else {
-    k_newton_gj<<<1, 256, sizeof(float) * (size_t)n * n, s>>>(B, d);
+    e = launch_pdl(k_newton_gj, dim3(1), dim3(256), sizeof(float) * (size_t)n * n, s, B, d);
     // FP64 Cholesky only when the FP32 inverse could not be refined
-    k_newton_chol<<<1, 256, shc, s>>>(B, d);
+    if (e == cudaSuccess) e = launch_pdl(k_newton_chol, dim3(1), dim3(256), shc, s, B, d);
   }
+  if (e != cudaSuccess) return e;
   B.launches += newton_dense_launches(d);
   return cudaGetLastError();
 }
@@ -827,6 +833,7 @@ cudaError_t launch_cg_finish(Buffers& B, int d, cudaStream_t s) {
 // ball->slot map and the buffer parity.
 __global__ void __launch_bounds__(256) k_mult_rows(const double* __restrict__ C, Buffers B,
                                                    int d) {
+  pdl_wait_and_release();
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_OUTER) return;
   const int nS = st->nS;
@@ -858,6 +865,7 @@ __global__ void __launch_bounds__(256) k_mult_rows(const double* __restrict__ C,
 }
 
 __global__ void k_mult_slots(Buffers B) {
+  pdl_wait_and_release();
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_OUTER) return;
   const int nS = st->nS;
@@ -874,8 +882,9 @@ __global__ void k_mult_slots(Buffers B) {
 
 cudaError_t launch_mult_update(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s) {
   (void)m;
-  k_mult_rows<<<304, 256, 0, s>>>(C, B, d);
-  k_mult_slots<<<152, 256, 0, s>>>(B);
+  cudaError_t e = launch_pdl(k_mult_rows, dim3(304), dim3(256), 0, s, C, B, d);
+  if (e == cudaSuccess) e = launch_pdl(k_mult_slots, dim3(152), dim3(256), 0, s, B);
+  if (e != cudaSuccess) return e;
   B.launches += 2;
   return cudaGetLastError();
 }
