@@ -551,7 +551,8 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
       rc = read_state(ctx);
       if (rc) return rc;
       B.launches = before + ctx->h_st->ticks * (tick_launches(d) + 1);
-      if (ctx->h_st->status == 3) return fail(ctx, MEB_ECUDA, "controller did not terminate");
+      if (ctx->h_st->status == kStatusTickCap)
+        return fail(ctx, MEB_ECUDA, "controller did not terminate");
     } else {
       int64_t ticks = 0;
       for (;;) {

@@ -33,6 +33,7 @@ enum : int {
 // DevState::status: 0 running, 1 converged, 2 iteration cap, 3 a device wait
 // gave up (a bulk copy did not complete in time)
 constexpr int kStatusWaitTimeout = 3;
+constexpr int kStatusTickCap = 4;   // the while-node loop reached its tick cap
 
 // per-block partial record of the pass (doubles)
 enum : int {

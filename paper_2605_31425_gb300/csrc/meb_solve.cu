@@ -985,11 +985,11 @@ __global__ void k_final_point(Buffers B, int d, double* __restrict__ c_out,
 
 // Loop condition of the device-resident solve (CUDA graph while-node): one
 // more tick while the controller runs; a tick cap ends a loop that does not
-// terminate with status 3.
+// terminate with status kStatusTickCap.
 __global__ void k_loop_cond(Buffers B, cudaGraphConditionalHandle h) {
   DevState* st = B.st;
   st->ticks += 1;
-  if (st->status == 0 && st->ticks >= st->max_ticks) st->status = 3;
+  if (st->status == 0 && st->ticks >= st->max_ticks) st->status = kStatusTickCap;
   cudaGraphSetConditional(h, st->status == 0 ? 1u : 0u);
 }
 
