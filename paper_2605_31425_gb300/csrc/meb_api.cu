@@ -54,9 +54,9 @@ struct meb_ctx {
 };
 
 // kernels launched per controller tick of the device-resident loop
-// kernels of one controller tick: pass (2), support rows (2), the dense
-// Newton step, the multiplier update (2)
-static int64_t tick_launches(int d) { return 2 + 2 + newton_dense_launches(d) + 2; }
+// kernels of one controller tick: pass (2), support rows (1), the dense
+// Newton step, the multiplier update (1)
+static int64_t tick_launches(int d) { return 2 + 1 + newton_dense_launches(d) + 1; }
 static const int kUnrollTicks = 8;
 
 enum { POOL_C, POOL_R, POOL_U, POOL_V, POOL_X, POOL_XB, POOL_Q, POOL_UP, POOL_VP, POOL_HQ,
@@ -83,7 +83,7 @@ static int fail(meb_ctx* ctx, int code, const char* fmt, ...) {
 static void free_buffers(meb_ctx* ctx) {
   Buffers& B = ctx->B;
   void* ptrs[] = {B.X32, B.X16, B.EPS16, B.E32, B.Hhi, B.Hlo, B.R32, B.slot, B.sup_idx[0], B.sup_idx[1], B.sup_u[0], B.sup_u[1],
-                  B.sup_v[0], B.sup_v[1], B.part_flag, B.part, B.part_cnt, B.cand_cnt, B.cand_idx,
+                  B.sup_v[0], B.sup_v[1], B.part_flag, B.part, B.part_cnt, B.cand_off, B.cand_cnt, B.cand_idx,
                   B.unc_cnt, B.unc_idx, B.unc_slot, B.vlb_part,
                   B.cand_case, B.cand_a, B.cand_n, B.cand_u, B.S_idx, B.S_case, B.S_a, B.S_n,
                   B.S_u, B.S_t, B.W, B.svec_part, B.hpart, B.H, B.hq, B.colsum_part, B.fe_ub, B.fe_lb,
@@ -145,6 +145,7 @@ static int ensure_buffers(meb_ctx* ctx, int64_t m, int d) {
   CK(dalloc(&B.part_flag, (size_t)nblk));
   CK(dalloc(&B.part, (size_t)nblk * P_NREC));
   CK(dalloc(&B.part_cnt, (size_t)nblk * P_NCNT));
+  CK(dalloc(&B.cand_off, (size_t)nblk + 1));
   CK(dalloc(&B.cand_cnt, (size_t)nblk));
   CK(dalloc(&B.unc_cnt, (size_t)nblk));
   CK(dalloc(&B.vlb_part, (size_t)nblk));

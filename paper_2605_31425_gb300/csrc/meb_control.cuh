@@ -276,6 +276,43 @@ __device__ __forceinline__ void control_a_body_impl(const Buffers& B, DevState* 
     __syncthreads();
     set_trial(st, V, d, sh);
     if (threadIdx.x == 0) st->phase = 1;
+  } else {
+    // the support S of the accepted point is the concatenation of the pass
+    // blocks' candidate segments: their start offsets (exclusive prefix of
+    // the counts, 8 per thread) and |S|
+    __shared__ int s_tot[8];
+    int v[8], run = 0;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int b = 8 * threadIdx.x + q;
+      v[q] = (b < nb) ? B.cand_cnt[b] : 0;
+      run += v[q];
+    }
+    int incl = run;   // inclusive scan of the thread totals: warp, then warps
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(MEB_FULLMASK, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_tot[w] = incl;
+    __syncthreads();
+    int base = 0, total = 0;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      base += (q < w) ? s_tot[q] : 0;
+      total += s_tot[q];
+    }
+    int off = base + incl - run;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int b = 8 * threadIdx.x + q;
+      if (b < nb) B.cand_off[b] = off;
+      off += v[q];
+    }
+    if (threadIdx.x == 0) {
+      B.cand_off[nb] = total;
+      st->nS = total;
+    }
   }
 }
 

@@ -146,6 +146,7 @@ struct Buffers {
   // pass outputs
   int* part_flag;       // [nblk]
   int* part_cnt;        // [nblk][P_NCNT]
+  int* cand_off;        // [nblk + 1] start of each pass block's candidates in S
   double* part;         // [nblk][P_COUNT]
   int* unc_cnt;         // [nblk] balls each pass block could not certify
   int* unc_idx;         // [ncand] their indices (per-block segments)

@@ -892,51 +892,14 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
 }
 
 // ===========================================================================
-// Ordered gather of the pass candidates (block b's segment at b*T*256) into
-// the support list S.
-__global__ void __launch_bounds__(256) k_compact_S(Buffers B, int nb, int64_t seg) {
-  pdl_wait_and_release();
-  DevState* st = B.st;
-  if (st->status != 0 || st->action != ACT_GRAD) return;
-  __shared__ int s_w[8];
-  __shared__ int s_cnt[8];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int b0 = blockIdx.x * 8;   // warp w copies segment b0 + w
-  // offset of segment b0: sum of the counts before it
-  int pre = 0;
-  for (int t = threadIdx.x; t < b0; t += 256) pre += B.cand_cnt[t];
-  pre = (int)__reduce_add_sync(MEB_FULLMASK, (unsigned)pre);
-  const int tt = b0 + w;
-  const int n = (tt < nb) ? B.cand_cnt[tt] : 0;
-  if (lane == 0) { s_w[w] = pre; s_cnt[w] = n; }
-  __syncthreads();
-  int base = 0, off = 0, tot = 0;
-#pragma unroll
-  for (int k = 0; k < 8; k++) {
-    base += s_w[k];
-    off += (k < w) ? s_cnt[k] : 0;
-    tot += s_cnt[k];
-  }
-  const int64_t s0 = (int64_t)base + off;
-  for (int e = lane; e < n; e += 32) {
-    const int64_t src = (int64_t)tt * seg + e;
-    const int64_t dst = s0 + e;
-    B.S_idx[dst] = B.cand_idx[src];
-    B.S_case[dst] = B.cand_case[src];
-    B.S_a[dst] = B.cand_a[src];
-    B.S_n[dst] = B.cand_n[src];
-    B.S_u[dst] = B.cand_u[src];
-  }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) st->nS = base + tot;
-}
-
 // Support rows: b_k = (c_k - c)/s + v_k/sigma recomputed in FP64;
 //   sum v^+ = sigma f_k b_k (all S), sum w_k (case M), sum t_k w_k^2 (case M),
 //   sum (1 + t_k) (case M);  W rows w_k = b_k / n_k (M) or b_k (I).
 // Block b takes rows [b*rpb, (b+1)*rpb) in order; thread j owns columns j, j+256, ...
 constexpr int kSvecStage = 64;   // support rows staged per round in shared memory
 
-__global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buffers B, int d) {
+__global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buffers B, int d,
+                                              int npb, int64_t seg) {
   pdl_wait_and_release();
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_GRAD) return;
@@ -950,6 +913,7 @@ __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buff
     return;
   }
   __shared__ int s_idx[kSvecStage], s_sl[kSvecStage];
+  __shared__ int s_off[kMaxPassBlocks + 1];   // candidate segment starts of the pass blocks
   __shared__ unsigned char s_cs[kSvecStage];
   __shared__ double s_sf[kSvecStage], s_in[kSvecStage], s_t[kSvecStage];
   __shared__ double s_red[3 * 256];
@@ -967,6 +931,7 @@ __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buff
   const int G = span >= 256 ? 1 : 256 / span;
   const int grp = (int)threadIdx.x / (span >= 256 ? 256 : span);
   const int jl = (int)threadIdx.x - grp * (span >= 256 ? 256 : span);
+  for (int b = threadIdx.x; b <= npb; b += 256) s_off[b] = B.cand_off[b];
   double s1t = 0.0;
   for (int j0 = 0; j0 < d; j0 += 256) {
     const int j = j0 + jl;
@@ -975,12 +940,28 @@ __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buff
     for (int r0 = k0; r0 < k1; r0 += kSvecStage) {
       const int nr = min(kSvecStage, k1 - r0);
       __syncthreads();
-      // stage the rows: index, slot (checked), case and the row scalars
+      // stage the rows: index, slot (checked), case and the row scalars.
+      // Row k of S is entry k - s_off[b] of pass block b's candidate segment
+      // (b the last block with s_off[b] <= k); the first j-round also writes
+      // the ordered support list S for the Newton and multiplier kernels.
       if ((int)threadIdx.x < nr) {
         const int k = r0 + threadIdx.x;
-        const int idx = B.S_idx[k];
-        const int cs = B.S_case[k];
-        const double a = B.S_a[k], n = B.S_n[k];
+        int lo = 0, hi = npb;   // s_off[lo] <= k < s_off[hi]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (s_off[mid] <= k) lo = mid; else hi = mid;
+        }
+        const int64_t src = (int64_t)lo * seg + (k - s_off[lo]);
+        const int idx = B.cand_idx[src];
+        const int cs = B.cand_case[src];
+        const double a = B.cand_a[src], n = B.cand_n[src];
+        if (j0 == 0) {
+          B.S_idx[k] = idx;
+          B.S_case[k] = (unsigned char)cs;
+          B.S_a[k] = a;
+          B.S_n[k] = n;
+          B.S_u[k] = B.cand_u[src];
+        }
         const int sl0 = B.slot[idx];
         const int sl = ((unsigned)sl0 < (unsigned)nsup && sidx[sl0] == idx) ? sl0 : -1;
         s_idx[threadIdx.x] = idx;
@@ -1052,14 +1033,10 @@ __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buff
 cudaError_t launch_support_rows(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s) {
   int tpb;
   const int nb = pass_blocks(m, d, screen_variant(B, d), &tpb);
-  cudaError_t e0 = launch_pdl(k_compact_S, dim3((nb + 7) / 8), dim3(256), 0, s, B, nb,
-                              (int64_t)tpb * kPassThreads);
-  if (e0 != cudaSuccess) return e0;
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_pdl(k_svec, dim3(kSvecBlocks), dim3(256), 0, s, C, B, d, nb,
+                             (int64_t)tpb * kPassThreads);
   if (e != cudaSuccess) return e;
-  e = launch_pdl(k_svec, dim3(kSvecBlocks), dim3(256), 0, s, C, B, d);
-  if (e != cudaSuccess) return e;
-  B.launches += 2;
+  B.launches += 1;
   return cudaGetLastError();
 }
 

@@ -829,8 +829,8 @@ cudaError_t launch_cg_finish(Buffers& B, int d, cudaStream_t s) {
 
 // ===========================================================================
 // Multiplier update (Algorithm 1): (u, v)^{k+1} = sigma_k Pi(z_k) on the
-// support of the accepted point, written to the other buffer; then the
-// ball->slot map and the buffer parity.
+// support of the accepted point, written to the other buffer, with the
+// ball->slot map; the last block flips the buffer parity.
 __global__ void __launch_bounds__(256) k_mult_rows(const double* __restrict__ C, Buffers B,
                                                    int d) {
   pdl_wait_and_release();
@@ -857,21 +857,16 @@ __global__ void __launch_bounds__(256) k_mult_rows(const double* __restrict__ C,
       if (sl >= 0) b = fma(sv[(int64_t)sl * d + j], inv_sigma, b);
       nv[(int64_t)k * d + j] = sigma * f * b;
     }
+    __syncwarp();   // every lane has read the old slot of ball idx
     if (lane == 0) {
       B.sup_idx[nxt][k] = idx;
       B.sup_u[nxt][k] = B.S_u[k];
+      // the new slot: each ball is in S once, so no other warp reads or
+      // writes slot[idx]; balls that left the support keep stale slots that
+      // fail the check against the new buffer
+      B.slot[idx] = k;
     }
   }
-}
-
-__global__ void k_mult_slots(Buffers B) {
-  pdl_wait_and_release();
-  DevState* st = B.st;
-  if (st->status != 0 || st->action != ACT_OUTER) return;
-  const int nS = st->nS;
-  const int nxt = st->sup_cur ^ 1;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nS; k += gridDim.x * blockDim.x)
-    B.slot[B.sup_idx[nxt][k]] = k;
   // the last block switches to the new multiplier buffers
   if (last_block_ticket(&st->ctr_slots) && threadIdx.x == 0) {
     st->sup_cur ^= 1;
@@ -883,9 +878,8 @@ __global__ void k_mult_slots(Buffers B) {
 cudaError_t launch_mult_update(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s) {
   (void)m;
   cudaError_t e = launch_pdl(k_mult_rows, dim3(304), dim3(256), 0, s, C, B, d);
-  if (e == cudaSuccess) e = launch_pdl(k_mult_slots, dim3(152), dim3(256), 0, s, B);
   if (e != cudaSuccess) return e;
-  B.launches += 2;
+  B.launches += 1;
   return cudaGetLastError();
 }
 
