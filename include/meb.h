@@ -40,6 +40,7 @@ extern "C" {
 #define MEB_ENOMEM (-2)    /* device allocation failed                                    */
 #define MEB_ECUDA (-3)     /* a CUDA call failed (message in meb_last_error)              */
 #define MEB_ENOTCONV (-4)  /* iteration cap reached; outputs hold the last iterate        */
+#define MEB_ETIMEOUT (-5)  /* a bounded device wait expired (a bulk copy did not land)    */
 
 #define MEB_PTR_DEVICE 1u
 

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-MEB_OK, MEB_EINVAL, MEB_ENOMEM, MEB_ECUDA, MEB_ENOTCONV = 0, -1, -2, -3, -4
+MEB_OK, MEB_EINVAL, MEB_ENOMEM, MEB_ECUDA, MEB_ENOTCONV, MEB_ETIMEOUT = 0, -1, -2, -3, -4, -5
 MEB_PTR_DEVICE = 1
 
 _D = ct.POINTER(ct.c_double)

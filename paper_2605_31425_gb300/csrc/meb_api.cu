@@ -618,7 +618,7 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   }
   const DevState S = *ctx->h_st;
   if (S.status == kStatusWaitTimeout)
-    return fail(ctx, MEB_ECUDA, "a device wait timed out (a bulk copy did not complete)");
+    return fail(ctx, MEB_ETIMEOUT, "a device wait timed out (a bulk copy did not complete)");
 
   // final point, radius lift (max-type value at c) and active set
   double* d_ralm = ctx->d_scal + 1;
