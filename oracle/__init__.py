@@ -10,6 +10,7 @@ from .oracle import (  # noqa: F401
     feas_check,
     kkt,
     params_default,
+    set_threads,
     soc_dist,
     soc_jacobian,
     soc_project,

@@ -8,9 +8,13 @@
  * it.  It shares no code, header, table or constant generator with the CUDA
  * library, and it includes nothing from it.
  *
- * Everything is FP64, single-threaded, loops over the balls in index order.
- * Sums are taken in index order.  Each function cites the passage of the
- * paper it follows:
+ * Everything is FP64.  Loops over the balls of a solve run over fixed chunks
+ * of ORC_CHUNK balls in index order; a sum over balls is the sum, in chunk
+ * order, of the chunks' sums, each taken in index order.  Chunks may run on
+ * several threads (OpenMP, when the compiler has it), and the results do not
+ * depend on the thread count (orc_feas_check takes no sums: its results are
+ * those of one loop in index order).  orc_eval_alm sums in plain index
+ * order.  Each function cites the passage of the paper it follows:
  *
  *   Sec. 2, eq. (MEB-SOCP)   : constraint (r - r_i, c - c_i) in Q_{d+1}
  *   Sec. 2, AL function      : phi_sigma and its gradient
@@ -50,6 +54,25 @@
 #include <stdlib.h>
 #include <string.h>
 #include <stdio.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_CHUNK 4096 /* balls per chunk of a solve's sums (see the header) */
+
+static int64_t nchunks(int64_t m) { return (m + ORC_CHUNK - 1) / ORC_CHUNK; }
+
+/* Threads for the chunk loops (1 without OpenMP); n <= 0 leaves the default. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 #define ORC_CASE_Z 0 /* ||b|| <= -a : projection is 0              */
 #define ORC_CASE_I 1 /* ||b|| <=  a : projection is the point      */
@@ -290,27 +313,52 @@ int orc_feas_check(int64_t m, int d, const double *C, const double *R,
                    const double *c, double r, double eps, double *delta_max,
                    int64_t *argmax, int64_t *viol, int64_t cap, int64_t *n_viol)
 {
+    /* per ball, in chunks: e_i and whether it is violated; then the maximum
+     * (lowest index on ties: chunks are merged in order with a strict >) and
+     * the list, in index order */
+    int64_t nc = nchunks(m);
+    double *cbest = (double *)malloc(sizeof(double) * (size_t)nc);
+    int64_t *carg = (int64_t *)malloc(sizeof(int64_t) * (size_t)nc);
+    unsigned char *in = (unsigned char *)malloc((size_t)m);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t ch = 0; ch < nc; ch++) {
+        double best = -INFINITY;
+        int64_t arg = -1;
+        int64_t i1 = (ch + 1) * ORC_CHUNK < m ? (ch + 1) * ORC_CHUNK : m;
+        for (int64_t i = ch * ORC_CHUNK; i < i1; i++) {
+            double s = 0.0;
+            for (int j = 0; j < d; j++) {
+                double t = c[j] - C[i * d + j];
+                s += t * t;
+            }
+            double e = R[i] + sqrt(s) - r;
+            if (e > best) {
+                best = e;
+                arg = i;
+            }
+            in[i] = e > eps;
+        }
+        cbest[ch] = best;
+        carg[ch] = arg;
+    }
     double best = -INFINITY;
     int64_t arg = -1, nv = 0;
-    for (int64_t i = 0; i < m; i++) {
-        double s = 0.0;
-        for (int j = 0; j < d; j++) {
-            double t = c[j] - C[i * d + j];
-            s += t * t;
+    for (int64_t ch = 0; ch < nc; ch++)
+        if (cbest[ch] > best) {
+            best = cbest[ch];
+            arg = carg[ch];
         }
-        double e = R[i] + sqrt(s) - r;
-        if (e > best) {
-            best = e;
-            arg = i;
-        }
-        if (e > eps) {
+    for (int64_t i = 0; i < m; i++)
+        if (in[i]) {
             if (viol && nv < cap) viol[nv] = i;
             nv++;
         }
-    }
     if (delta_max) *delta_max = best;
     if (argmax) *argmax = arg;
     if (n_viol) *n_viol = nv;
+    free(cbest);
+    free(carg);
+    free(in);
     return 0;
 }
 
@@ -323,20 +371,38 @@ int orc_feas_check(int64_t m, int d, const double *C, const double *R,
 int orc_kkt(int64_t m, int d, const double *C, const double *R, double r,
             const double *c, const double *U, const double *V, double *k)
 {
-    double su = 0.0;
+    /* per chunk: sum u, sum v (d), and the three maxima; then the chunk sums
+     * in chunk order and the maxima over chunks */
+    int64_t nc = nchunks(m);
+    int w = d + 4;
+    double *part = (double *)calloc((size_t)nc * w, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t ch = 0; ch < nc; ch++) {
+        double *p = part + ch * w; /* [0] sum u, [1..d] sum v, [d+1..d+3] maxima */
+        double *b = (double *)malloc(sizeof(double) * (size_t)d);
+        int64_t i1 = (ch + 1) * ORC_CHUNK < m ? (ch + 1) * ORC_CHUNK : m;
+        for (int64_t i = ch * ORC_CHUNK; i < i1; i++) {
+            p[0] += U[i];
+            for (int j = 0; j < d; j++) p[1 + j] += V[i * d + j];
+            for (int j = 0; j < d; j++) b[j] = c[j] - C[i * d + j];
+            double dp = orc_soc_dist(r - R[i], b, d);
+            if (dp > p[d + 1]) p[d + 1] = dp;
+            double dd = orc_soc_dist(U[i], V + i * d, d);
+            if (dd > p[d + 2]) p[d + 2] = dd;
+            double cp = fabs((r - R[i]) * U[i] + dot(b, V + i * d, d));
+            if (cp > p[d + 3]) p[d + 3] = cp;
+        }
+        free(b);
+    }
+    double su = 0.0, pinf = 0.0, dinf = 0.0, comp = 0.0;
     double *sv = (double *)calloc((size_t)d, sizeof(double));
-    double *b = (double *)malloc(sizeof(double) * (size_t)d);
-    double pinf = 0.0, dinf = 0.0, comp = 0.0;
-    for (int64_t i = 0; i < m; i++) {
-        su += U[i];
-        for (int j = 0; j < d; j++) sv[j] += V[i * d + j];
-        for (int j = 0; j < d; j++) b[j] = c[j] - C[i * d + j];
-        double dp = orc_soc_dist(r - R[i], b, d);
-        if (dp > pinf) pinf = dp;
-        double dd = orc_soc_dist(U[i], V + i * d, d);
-        if (dd > dinf) dinf = dd;
-        double cp = fabs((r - R[i]) * U[i] + dot(b, V + i * d, d));
-        if (cp > comp) comp = cp;
+    for (int64_t ch = 0; ch < nc; ch++) {
+        const double *p = part + ch * w;
+        su += p[0];
+        for (int j = 0; j < d; j++) sv[j] += p[1 + j];
+        if (p[d + 1] > pinf) pinf = p[d + 1];
+        if (p[d + 2] > dinf) dinf = p[d + 2];
+        if (p[d + 3] > comp) comp = p[d + 3];
     }
     k[0] = fabs(1.0 - su);
     k[1] = nrm(sv, d);
@@ -344,7 +410,7 @@ int orc_kkt(int64_t m, int d, const double *C, const double *R, double r,
     k[3] = dinf;
     k[4] = comp;
     free(sv);
-    free(b);
+    free(part);
     return 0;
 }
 
@@ -405,26 +471,55 @@ static void eval_point(int64_t m, int d, const double *C, const double *R,
                        double *psi_mag, double *g_mag, double *grad, double *Up,
                        double *Vp, support_t *S)
 {
-    double *b = (double *)malloc(sizeof(double) * (size_t)d);
-    double *pb = (double *)malloc(sizeof(double) * (size_t)d);
-    double *sv = (double *)calloc((size_t)d, sizeof(double));
+    /* per chunk: sum ||Pi(z_i)||^2, sum u+, sum_{I,M} |a_i| + ||b_i||, sum v+ (d);
+     * the case of every ball */
+    int64_t nc = nchunks(m);
+    int w = d + 3;
+    double *part = (double *)calloc((size_t)nc * w, sizeof(double));
+    unsigned char *cs_all = (unsigned char *)malloc((size_t)m);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t ch = 0; ch < nc; ch++) {
+        double *p = part + ch * w;
+        double *b = (double *)malloc(sizeof(double) * (size_t)d);
+        double *pb = (double *)malloc(sizeof(double) * (size_t)d);
+        int64_t i1 = (ch + 1) * ORC_CHUNK < m ? (ch + 1) * ORC_CHUNK : m;
+        for (int64_t i = ch * ORC_CHUNK; i < i1; i++) {
+            double a = R[i] - x[0] + U[i] / sigma;
+            for (int j = 0; j < d; j++) b[j] = C[i * d + j] - x[1 + j] + V[i * d + j] / sigma;
+            double pa;
+            int cs = orc_soc_project(a, b, d, &pa, pb);
+            cs_all[i] = (unsigned char)cs;
+            p[0] += pa * pa + dot(pb, pb, d);
+            p[1] += sigma * pa;
+            for (int j = 0; j < d; j++) p[3 + j] += sigma * pb[j];
+            Up[i] = sigma * pa;
+            for (int j = 0; j < d; j++) Vp[i * d + j] = sigma * pb[j];
+            if (cs != ORC_CASE_Z) p[2] += fabs(a) + nrm(b, d);
+        }
+        free(b);
+        free(pb);
+    }
     double sum_pi2 = 0.0, su = 0.0, zmag = 0.0;
+    double *sv = (double *)calloc((size_t)d, sizeof(double));
+    for (int64_t ch = 0; ch < nc; ch++) {
+        const double *p = part + ch * w;
+        sum_pi2 += p[0];
+        su += p[1];
+        zmag += p[2];
+        for (int j = 0; j < d; j++) sv[j] += p[3 + j];
+    }
+    /* the support (cases I and M) in ball order; for case M, w_i = b_i/||b_i||
+     * and t_i = a_i/||b_i|| */
+    double *b = (double *)malloc(sizeof(double) * (size_t)d);
     S->n = 0;
     for (int64_t i = 0; i < m; i++) {
-        double a = R[i] - x[0] + U[i] / sigma;
-        for (int j = 0; j < d; j++) b[j] = C[i * d + j] - x[1 + j] + V[i * d + j] / sigma;
-        double pa;
-        int cs = orc_soc_project(a, b, d, &pa, pb);
-        sum_pi2 += pa * pa + dot(pb, pb, d);
-        su += sigma * pa;
-        for (int j = 0; j < d; j++) sv[j] += sigma * pb[j];
-        Up[i] = sigma * pa;
-        for (int j = 0; j < d; j++) Vp[i * d + j] = sigma * pb[j];
+        int cs = cs_all[i];
         if (cs == ORC_CASE_Z) continue;
-        zmag += fabs(a) + nrm(b, d);
         int64_t k = S->n++;
         S->cs[k] = cs;
         if (cs == ORC_CASE_M) {
+            double a = R[i] - x[0] + U[i] / sigma;
+            for (int j = 0; j < d; j++) b[j] = C[i * d + j] - x[1 + j] + V[i * d + j] / sigma;
             double n = nrm(b, d);
             S->t[k] = a / n;
             for (int j = 0; j < d; j++) S->w[k * d + j] = b[j] / n;
@@ -438,8 +533,59 @@ static void eval_point(int64_t m, int d, const double *C, const double *R,
     grad[0] = 1.0 - su + tau / sigma * (x[0] - xbar[0]);
     for (int j = 0; j < d; j++) grad[1 + j] = -sv[j] + tau / sigma * (x[1 + j] - xbar[1 + j]);
     free(b);
-    free(pb);
     free(sv);
+    free(part);
+    free(cs_all);
+}
+
+/* sum_i ||(Up_i, Vp_i) - (U_i, V_i)||^2 in chunks (the stop test of Algorithm 1). */
+static double duv2_sum(int64_t m, int d, const double *Up, const double *U, const double *Vp,
+                       const double *V)
+{
+    int64_t nc = nchunks(m);
+    double *part = (double *)calloc((size_t)nc, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t ch = 0; ch < nc; ch++) {
+        double t2 = 0.0;
+        int64_t i1 = (ch + 1) * ORC_CHUNK < m ? (ch + 1) * ORC_CHUNK : m;
+        for (int64_t i = ch * ORC_CHUNK; i < i1; i++) {
+            t2 += (Up[i] - U[i]) * (Up[i] - U[i]);
+            for (int jj = 0; jj < d; jj++) {
+                double t = Vp[i * d + jj] - V[i * d + jj];
+                t2 += t * t;
+            }
+        }
+        part[ch] = t2;
+    }
+    double s = 0.0;
+    for (int64_t ch = 0; ch < nc; ch++) s += part[ch];
+    free(part);
+    return s;
+}
+
+/* max_i (||c - c_i|| + r_i) in chunks (the max-type value, Sec. 1). */
+static double max_type_value(int64_t m, int d, const double *C, const double *R,
+                             const double *c)
+{
+    int64_t nc = nchunks(m);
+    double *part = (double *)malloc(sizeof(double) * (size_t)nc);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t ch = 0; ch < nc; ch++) {
+        double best = -INFINITY;
+        int64_t i1 = (ch + 1) * ORC_CHUNK < m ? (ch + 1) * ORC_CHUNK : m;
+        for (int64_t i = ch * ORC_CHUNK; i < i1; i++) {
+            double q = 0.0;
+            for (int j = 0; j < d; j++) q += (c[j] - C[i * d + j]) * (c[j] - C[i * d + j]);
+            double e = sqrt(q) + R[i];
+            if (e > best) best = e;
+        }
+        part[ch] = best;
+    }
+    double best = -INFINITY;
+    for (int64_t ch = 0; ch < nc; ch++)
+        if (part[ch] > best) best = part[ch];
+    free(part);
+    return best;
 }
 
 /* y = (tau/sigma I + sigma sum P_i) q using the stored support.            */
@@ -570,18 +716,24 @@ int orc_solve(int64_t m, int d, const double *C0, const double *R0,
         return 0;
     }
 
-    /* Initial point: mean centre, radius of the max-type value there. */
+    /* Initial point: mean centre (chunk sums in chunk order), radius of the
+     * max-type value there. */
     double *c0 = (double *)calloc((size_t)d, sizeof(double));
-    for (int64_t i = 0; i < m; i++)
-        for (int j = 0; j < d; j++) c0[j] += C0[i * d + j];
-    for (int j = 0; j < d; j++) c0[j] /= (double)m;
-    double r0 = -INFINITY;
-    for (int64_t i = 0; i < m; i++) {
-        double s = 0.0;
-        for (int j = 0; j < d; j++) s += (c0[j] - C0[i * d + j]) * (c0[j] - C0[i * d + j]);
-        double e = sqrt(s) + R0[i];
-        if (e > r0) r0 = e;
+    {
+        int64_t nc = nchunks(m);
+        double *part = (double *)calloc((size_t)nc * d, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t ch = 0; ch < nc; ch++) {
+            int64_t i1 = (ch + 1) * ORC_CHUNK < m ? (ch + 1) * ORC_CHUNK : m;
+            for (int64_t i = ch * ORC_CHUNK; i < i1; i++)
+                for (int j = 0; j < d; j++) part[ch * d + j] += C0[i * d + j];
+        }
+        for (int64_t ch = 0; ch < nc; ch++)
+            for (int j = 0; j < d; j++) c0[j] += part[ch * d + j];
+        free(part);
     }
+    for (int j = 0; j < d; j++) c0[j] /= (double)m;
+    double r0 = max_type_value(m, d, C0, R0, c0);
     if (r0 == 0.0) { /* every ball is the same point */
         for (int j = 0; j < d; j++) c_out[j] = c0[j];
         info->r = info->r_alm = 0.0;
@@ -602,6 +754,7 @@ int orc_solve(int64_t m, int d, const double *C0, const double *R0,
     /* Scaled data. */
     double *C = (double *)malloc(sizeof(double) * (size_t)m * d);
     double *R = (double *)malloc(sizeof(double) * (size_t)m);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < m * d; i++) C[i] = C0[i] / s;
     for (int64_t i = 0; i < m; i++) R[i] = R0[i] / s;
 
@@ -652,13 +805,7 @@ int orc_solve(int64_t m, int d, const double *C0, const double *R0,
                 g2 += g[k] * g[k];
                 dxk2 += (x[k] - xk[k]) * (x[k] - xk[k]);
             }
-            for (int64_t i = 0; i < m; i++) {
-                duv2 += (Up[i] - U[i]) * (Up[i] - U[i]);
-                for (int jj = 0; jj < d; jj++) {
-                    double t = Vp[i * d + jj] - V[i * d + jj];
-                    duv2 += t * t;
-                }
-            }
+            duv2 = duv2_sum(m, d, Up, U, Vp, V);
             double lhs = 2.0 * sigma * fabs(lhs_a) + sigma * sigma * g2;
             double rhs_v = prm.rho * (duv2 + tau * dxk2);
             if (lhs <= rhs_v) break;
@@ -738,26 +885,24 @@ int orc_solve(int64_t m, int d, const double *C0, const double *R0,
     orc_feas_check(m, d, C0, R0, cc, r_alm, 0.0, &dmax, &amax, NULL, 0, NULL);
     double r_out = r_alm + dmax;
     /* r_out is max_i(||c - c_i|| + r_i); recompute it directly */
-    {
-        double best = -INFINITY;
-        for (int64_t i = 0; i < m; i++) {
-            double q = 0.0;
-            for (int j = 0; j < d; j++) q += (cc[j] - C0[i * d + j]) * (cc[j] - C0[i * d + j]);
-            double e = sqrt(q) + R0[i];
-            if (e > best) best = e;
-        }
-        r_out = best;
-    }
-    int64_t na = 0;
+    r_out = max_type_value(m, d, C0, R0, cc);
+    /* active set: slack r - r_i - ||c - c_i|| <= theta r, in index order */
+    unsigned char *act = (unsigned char *)malloc((size_t)m);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < m; i++) {
         double q = 0.0;
         for (int j = 0; j < d; j++) q += (cc[j] - C0[i * d + j]) * (cc[j] - C0[i * d + j]);
         double slack = r_out - R0[i] - sqrt(q);
-        if (slack <= prm.active_theta * r_out) {
+        act[i] = slack <= prm.active_theta * r_out;
+    }
+    int64_t na = 0;
+    for (int64_t i = 0; i < m; i++) {
+        if (act[i]) {
             if (active && na < cap) active[na] = i;
             na++;
         }
     }
+    free(act);
     for (int j = 0; j < d; j++) c_out[j] = cc[j];
     if (U_out) memcpy(U_out, U, sizeof(double) * (size_t)m);
     if (V_out) memcpy(V_out, V, sizeof(double) * (size_t)m * d);

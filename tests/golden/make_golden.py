@@ -38,4 +38,4 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["cube_m2e6_d100"])
+    main(sys.argv[1:] or ["cube_m2e6_d100", "gaussian_m1e4_d10"])

@@ -410,3 +410,100 @@ def test_cg_path_matches_dense_path():
     assert rc["cg_iters"] > 0
     assert rc["r"] == pytest.approx(rd["r"], rel=1e-10)
     check_solution(C, R, rc)
+
+
+# ---------------------------------------------------------------- active set
+THETA = 2e-6   # active set: slack r - r_i - ||c - c_i|| <= THETA r (the reading of Sec. 4.2)
+
+
+def _active_mask(res, m):
+    a = np.zeros(m, bool)
+    a[res["active"]] = True
+    return a
+
+
+@pytest.mark.parametrize("seed,d,m", [(s, d, m) for s in range(4) for d, m in [(2, 9), (3, 8)]])
+def test_active_set_brute_force_tiny(seed, d, m):
+    """The returned active set is the set of balls touching the brute-force
+    ball (zero slack there), outside the band where the slack is within 1e-6 r
+    of THETA r."""
+    rng = np.random.default_rng(1000 + seed)
+    C = rng.standard_normal((m, d))
+    R = rng.uniform(0, 0.5, m)
+    rb, cb = brute_force_meb(C, R)
+    res = oracle.solve(C, R, tol=1e-12)
+    slack = rb - R - np.linalg.norm(C - cb, axis=1)
+    expect = slack <= THETA * rb
+    sure = np.abs(slack - THETA * rb) > 1e-6 * rb
+    assert expect.sum() >= 2 and sure.all()
+    assert np.array_equal(_active_mask(res, m)[sure], expect[sure])
+
+
+def test_active_set_two_balls():
+    C = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0]])
+    res = oracle.solve(C, np.array([2.0, 0.25]), tol=1e-12)     # ball 1 inside ball 0
+    assert list(res["active"]) == [0]
+    res = oracle.solve(np.array([[1.0, 2.0], [4.0, 6.0]]), np.array([0.3, 1.1]), tol=1e-12)
+    assert list(res["active"]) == [0, 1]
+
+
+@pytest.mark.parametrize("n", [3, 6, 10])
+def test_active_set_simplex_with_interior_points(n):
+    """Vertices of a regular simplex plus points strictly inside it: exactly the
+    vertices are active, whatever their order among the balls."""
+    rng = np.random.default_rng(n)
+    W = rng.dirichlet(np.ones(n), size=4 * n)
+    inner = 0.7 * W + 0.3 / n                  # convex combinations, pulled to the centroid
+    C = np.vstack([inner[: 2 * n], np.eye(n), inner[2 * n:]])
+    res = oracle.solve(C, np.zeros(len(C)), tol=1e-12)
+    assert list(res["active"]) == list(range(2 * n, 3 * n))
+    assert res["r"] == pytest.approx(math.sqrt((n - 1) / n), rel=1e-10)
+
+
+def test_multipliers_only_on_active_balls():
+    """Complementarity (KKT, Sec. 2): a ball with a nonzero multiplier touches the
+    ball, so it is in the active set; balls strictly inside have u = v = 0."""
+    C, R = workloads.gaussian(2000, 6, 41, 0.1)
+    res = oracle.solve(C, R, tol=1e-12)
+    U, V = res["U"], res["V"]
+    holders = np.nonzero((U > 1e-9) | (np.linalg.norm(V, axis=1) > 1e-9))[0]
+    assert len(holders) >= 2
+    assert set(holders.tolist()) <= set(res["active"].tolist())
+    slack = res["r"] - R - np.linalg.norm(C - res["c"], axis=1)
+    inside = slack > 1e-6 * res["r"]
+    assert np.all(U[inside] == 0.0) and np.all(V[inside] == 0.0)
+
+
+@pytest.mark.parametrize("scale", [1e3, 1e-3])
+def test_active_set_threshold_is_relative(scale):
+    """Closed form: balls 0, 1 at (-L, 0), (L, 0) with radius 0 give c* = 0,
+    r* = L; balls centred at 0 with radius L (1 - k 1e-6) have slack k 1e-6 L.
+    Active iff slack <= THETA r*, i.e. k <= 2: an absolute threshold (THETA) or
+    any other power of r would move the boundary by orders of magnitude at
+    these scales."""
+    L = scale
+    ks = [0.5, 1.0, 3.5, 10.0, 1.9, 2.2]
+    C = np.zeros((2 + len(ks), 2))
+    C[0, 0], C[1, 0] = -L, L
+    R = np.concatenate([[0.0, 0.0], [L * (1 - k * 1e-6) for k in ks]])
+    res = oracle.solve(C, R, tol=1e-12)
+    assert res["r"] == pytest.approx(L, rel=1e-10)
+    expect = [0, 1] + [2 + j for j, k in enumerate(ks) if k <= 2.0]
+    assert list(res["active"]) == expect
+
+
+def test_solve_does_not_depend_on_thread_count():
+    """The solve's sums are chunk sums added in chunk order (ORC_CHUNK balls per
+    chunk), so one thread and many give bit-identical results."""
+    C, R = workloads.cube(20_000, 12, 5, 0.05)
+    n0 = oracle.set_threads(0)
+    try:
+        oracle.set_threads(1)
+        a = oracle.solve(C, R, tol=1e-12)
+        oracle.set_threads(max(n0, 4))
+        b = oracle.solve(C, R, tol=1e-12)
+    finally:
+        oracle.set_threads(n0)
+    assert a["r"] == b["r"] and np.array_equal(a["c"], b["c"])
+    assert np.array_equal(a["U"], b["U"]) and np.array_equal(a["active"], b["active"])
+    assert a["passes"] == b["passes"]
