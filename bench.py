@@ -2,28 +2,36 @@
 """Benchmark: MEB solves/s of the ripALM hot path on one GB300 (or N replicas).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload cube_m2e6_d100]
+                    [--workload cube_m2e6_d100] [--no-extra] [--no-cpu-baseline]
 
 A step is one full solve (Algorithm 1 with Algorithm 2, then the
 feasibility pass of Sec. 4.2) of the workload's synthetic instance:
 m = 2,000,000 balls in d = 100, centres U[-1,1]^d, radii U[0,0.05]
 (seed 1002).  Inputs (1.6 GB) are resident in HBM and larger than L2, so no
 flush is needed between steps.  Each solve is checked against the stored
-oracle radius (tests/golden/<workload>.json): a solve counts only if its
-radius relative error is <= 1e-8.
+oracle radius (tests/golden/<workload>.json, written by the oracle): a solve
+counts only if its radius relative error is <= 1e-8.
 
-The roofline of the screen kernel is taken from a few more solves of the same
-instance right after the timed region, with CUDA event nodes recorded around
-every screen inside the solve graphs (the nodes slow a solve by about 6%, so
-the timed region runs without them).
+The same JSON line carries, besides the headline:
+  arms       the same workload solved by the plain FP64 ripALM (no shadow:
+             every ball of every pass through the FP64 rows), the baseline the
+             reduced-precision screens are measured against;
+  workloads  the small latency-bound instance (m = 1e4, d = 10: solves/s and
+             microseconds per semismooth Newton step) and the large
+             high-dimensional one (m = 2e5, d = 2000, points on a sphere:
+             solves/s, checked against the closed form r* = 1);
+  roofline   of the screen kernel (the full pass over all balls), from a few
+             more solves with CUDA event nodes around every screen (the nodes
+             slow a solve by about 6%, so the timed region runs without them);
+  cpu_baseline  one full solve of the same instance by the CPU oracle as it
+             stands, on all host cores (the count is stated).
 
 Under torchrun (N > 1) every rank solves its own copy of the workload with no
 collective on the data path (weak scaling); the timed region is bracketed by
 barriers and the max over ranks is used.
 
---impl reference times the CPU oracle as it stands on a bounded sample of the
-same workload (the first 100,000 balls, scaled by m / 100,000 to the
-workload's solves/s), on rank 0 only.
+--impl reference times the CPU oracle as it stands: each step is one full
+solve of the same instance on all host cores, on rank 0 only.
 """
 from __future__ import annotations
 
@@ -43,13 +51,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MEB solves/s & p50/p99 latency at radius rel.err<=1e-8; per-iter HBM GB/s"
 UNIT = "solves/s"
-SAMPLE_M = 100_000
 ROOFLINE_SOLVES = 3
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full FP16
 # screen per ball, by d, from an ncu capture at m = 1e6 (traffic grows with
-# the balls streamed; scaled to a launch by m).  Valid for the screen kernel
-# as captured; None once the kernel changes.
-SCREEN_TRAFFIC_PER_BALL = {100: 223.27}
+# the balls streamed; scaled to a launch by m).  Valid only for the screen
+# kernel as captured: empty while the kernel has changed since.
+SCREEN_TRAFFIC_PER_BALL: dict = {}
 
 
 def _peaks():
@@ -141,25 +148,26 @@ def aggregate(dist, tot_ms: float, ok: int, device=None):
     return float(n.item()) / (float(t.item()) / 1e3), float(t.item()), int(n.item())
 
 
-def oracle_sample(C, R):
-    """The CPU oracle as it stands on the first SAMPLE_M balls; returns seconds."""
+def oracle_full_solve(C, R):
+    """The CPU oracle as it stands: one full solve on all host cores (its
+    results do not depend on the thread count).  Returns (seconds, threads, r)."""
     import oracle
-    ms = min(SAMPLE_M, C.shape[0])
+    threads = oracle.set_threads(os.cpu_count() or 1)
     t = time.perf_counter()
-    res = oracle.solve(C[:ms], R[:ms], tol=1e-10)
-    dt = time.perf_counter() - t
-    return dt, ms, res
+    res = oracle.solve(C, R, tol=1e-10)
+    return time.perf_counter() - t, threads, res["r"]
 
 
 def run_reference(args, C, R, m, rank):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(C, R)
+        oracle_full_solve(C, R)
     times = []
+    threads = 1
     for _ in range(args.steps):
-        dt, ms, _ = oracle_sample(C, R)
-        times.append(dt * (m / ms))
+        dt, threads, r = oracle_full_solve(C, R)
+        times.append(dt)
     tot = sum(times)
     value = args.steps / tot
     line = {
@@ -168,12 +176,71 @@ def run_reference(args, C, R, m, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "m": m, "d": int(C.shape[1]), "tol": 1e-10},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"oracle solve of the first {SAMPLE_M} of {m} balls per step, "
-                                   f"time scaled by m/{SAMPLE_M}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"each step one full oracle solve of all {m} balls "
+                                   f"(tol 1e-10) on {threads} host threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def timed_solves(meb, torch, ctx, dC, dR, steps, warmup, stream):
+    """Warm-up, then `steps` solves each bracketed by CUDA events on the solve
+    stream; returns (per-solve ms, the last result, radii)."""
+    for _ in range(warmup):
+        meb.solve(dC, dR, ctx=ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    radii = []
+    res = None
+    torch.cuda.synchronize()
+    for k in range(steps):
+        ev[k][0].record(stream)
+        res = meb.solve(dC, dR, ctx=ctx)
+        ev[k][1].record(stream)
+        radii.append(res["r"])
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], res, radii
+
+
+def extra_workloads(meb, torch, local, stream, workloads):
+    """The small latency-bound instance and the large high-dimensional one."""
+    out = {}
+    # m = 1e4, d = 10 (gaussian, seed 1001): stored oracle radius
+    C, R = workloads.workload("gaussian_m1e4_d10")
+    gold = _golden("gaussian_m1e4_d10")
+    r_ref = gold["r"] if gold and gold.get("input_sha256") == workloads.digest(C, R) else None
+    ctx = meb.Context(local, stream.cuda_stream)
+    dC, dR = torch.from_numpy(C).cuda(), torch.from_numpy(R).cuda()
+    lat, res, radii = timed_solves(meb, torch, ctx, dC, dR, 30, 5, stream)
+    rel = [abs(r - r_ref) / r_ref for r in radii] if r_ref else None
+    ok = sum(e <= 1e-8 for e in rel) if rel else len(lat)
+    out["gaussian_m1e4_d10"] = {
+        "value": ok / (sum(lat) / 1e3), "unit": UNIT, "steps": len(lat),
+        "p50_ms": statistics.median(lat), "p99_ms": float(np.percentile(lat, 99)),
+        "us_per_ssn_step": 1e3 * statistics.median(lat) / max(res["ssn_iters"], 1),
+        "ssn_per_solve": res["ssn_iters"], "passes_per_solve": res["passes"],
+        "max_relerr": max(rel) if rel else None, "reference": "stored oracle radius",
+        "bound": "latency (working set 0.9 MB, L2-resident)"}
+    del dC, dR
+    # m = 2e5, d = 2000 (sphere, seed 1003): closed form r* = 1
+    C, R, _ctr = workloads.sphere(200_000, 2000, 1003)
+    ctx = meb.Context(local, stream.cuda_stream)
+    dC, dR = torch.from_numpy(C).cuda(), torch.from_numpy(R).cuda()
+    del C
+    ctx.reset_stats()
+    lat, res, radii = timed_solves(meb, torch, ctx, dC, dR, 3, 1, stream)
+    st = ctx.stats()
+    rel = [abs(r - 1.0) for r in radii]
+    ok = sum(e <= 1e-8 for e in rel)
+    out["sphere_m2e5_d2000"] = {
+        "value": ok / (sum(lat) / 1e3), "unit": UNIT, "steps": len(lat),
+        "p50_ms": statistics.median(lat), "max_relerr": max(rel),
+        "reference": "closed form r* = 1", "ssn_per_solve": res["ssn_iters"],
+        "cg_per_solve": res["cg_iters"], "passes_per_solve": res["passes"],
+        "gpu_launches_per_solve": st["kernel_launches"] / 4}
+    del dC, dR
+    return out
 
 
 def main():
@@ -185,6 +252,8 @@ def main():
     ap.add_argument("--workload", default="cube_m2e6_d100")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="headline only (no FP64 arm, no other workloads)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -244,8 +313,7 @@ def main():
         st_run = ctx.stats()
         # roofline of the dominant kernel, k_screen (the full pass over all
         # balls): the same solves again with CUDA event nodes recorded around
-        # every screen inside the graphs (they add about 6% to a solve, so
-        # the throughput above is timed without them)
+        # every screen inside the graphs
         ctx.set_profiling(True)
         ctx.reset_stats()
         for _ in range(min(args.steps, ROOFLINE_SOLVES)):
@@ -282,13 +350,37 @@ def main():
             e2e_ok += 1
     e2e_s = time.perf_counter() - t0
     e2e_val = world * e2e_ok / e2e_s if args.e2e_steps > 0 else None
+    del pC, pR, hctx
+
+    arms, extra = None, None
+    if not args.no_extra:
+        # the plain FP64 ripALM on the same resident inputs
+        pctx = meb.Context(local, stream.cuda_stream, screen="fp64")
+        plat, pres, pradii = timed_solves(meb, torch, pctx, dC, dR, 3, 1, stream)
+        prel = [abs(r - r_ref) / r_ref for r in pradii] if r_ref else []
+        pok = sum(e <= 1e-8 for e in prel) if r_ref else len(plat)
+        arms = {
+            "fp16_certified_screen": {"value": value, "unit": UNIT, "p50_ms": statistics.median(lat),
+                                      "note": "the headline: certified FP16 screen + FP64 rows"},
+            "fp64_plain": {"value": pok / (sum(plat) / 1e3), "unit": UNIT,
+                           "p50_ms": statistics.median(plat), "steps": len(plat),
+                           "max_relerr": max(prel) if prel else None,
+                           "passes_per_solve": pres["passes"],
+                           "fp64_rows_per_pass": pres["fp64_rows"] / max(pres["passes"], 1),
+                           "note": "every ball of every pass through the FP64 rows, no shadow"},
+        }
+        del pctx
+        del dC, dR
+        torch.cuda.empty_cache()
+        extra = extra_workloads(meb, torch, local, stream, workloads)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        dt, ms, _ = oracle_sample(C, R)
-        cpu = {"value": 1.0 / (dt * m / ms), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one oracle solve of the first {ms} of {m} balls "
-                         f"({dt:.2f} s), time scaled by m/{ms}"}
+        dt, threads, r_cpu = oracle_full_solve(C, R)
+        cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"one full oracle solve of all {m} balls (tol 1e-10, {dt:.2f} s) "
+                         f"on {threads} host threads",
+               "relerr_vs_stored": abs(r_cpu - r_ref) / r_ref if r_ref else None}
 
     if rank == 0:
         line = {
@@ -316,6 +408,8 @@ def main():
             "gpu_launches": int(st_run["kernel_launches"]),
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "arms": arms,
+            "workloads": extra,
             "wall_s": wall,
         }
         print(json.dumps(line), flush=True)

@@ -108,6 +108,47 @@ void meb_destroy(meb_ctx *ctx);
 void meb_params_default(meb_params *p);
 const char *meb_last_error(const meb_ctx *ctx);
 
+/* Context options (no counterpart in the paper: they select how the same
+ * method is executed, and the numbers the tests and the benchmark compare).
+ * Each context keeps its own values; a new context starts at the defaults.
+ *
+ *  MEB_OPT_SCREEN       how every full pass of a solve decides which balls
+ *                       need FP64 rows (Algorithm 2, step 1):
+ *                       MEB_SCREEN_FP16 (default) certified FP16 shadow,
+ *                       register-batched loads; MEB_SCREEN_FP16_BULK the same
+ *                       through a bulk-copy (TMA) pipeline; MEB_SCREEN_FP32
+ *                       certified FP32 shadow; MEB_SCREEN_FP64 no shadow: every
+ *                       ball of every pass and of every feasibility pass is
+ *                       evaluated in FP64 (the plain FP64 ripALM).
+ *  MEB_OPT_EVAL_SCREEN  the same choice for meb_eval_alm (default FP32); it
+ *                       also applies to meb_feas_check when it is MEB_SCREEN_FP64.
+ *  MEB_OPT_EVAL_SHADOW_EXP  meb_eval_alm with an FP16 screen builds the shadow
+ *                       of (c_i - c_1) / 2^value (any exponent; default 0).
+ *                       Values that overflow FP16 are never certified and values
+ *                       in its subnormal range carry their absolute error bound,
+ *                       so every exponent gives the same results.
+ *  MEB_OPT_TICK_LOOP    device-resident loop of a solve: 0 (default) CUDA graphs
+ *                       of 8 controller ticks relaunched until the controller
+ *                       stops; 1 host-launched ticks; 2 one graph with a
+ *                       while-node.  All three give bit-identical results.
+ *  MEB_OPT_WAIT_CYCLES  bound, in SM clock cycles, of each wait of the
+ *                       bulk-copy screen for its copies (default 2e9, about one
+ *                       second); 0 makes each wait a single non-blocking test.
+ *                       An expired wait ends the solve with MEB_ETIMEOUT after
+ *                       the copies in flight have landed; the context stays
+ *                       usable.
+ * Returns MEB_EINVAL for an unknown option or value. */
+#define MEB_OPT_SCREEN 1
+#define MEB_OPT_EVAL_SCREEN 2
+#define MEB_OPT_EVAL_SHADOW_EXP 3
+#define MEB_OPT_TICK_LOOP 4
+#define MEB_OPT_WAIT_CYCLES 5
+#define MEB_SCREEN_FP16 0
+#define MEB_SCREEN_FP16_BULK 1
+#define MEB_SCREEN_FP32 2
+#define MEB_SCREEN_FP64 3
+int meb_set_option(meb_ctx *ctx, int32_t option, int64_t value);
+
 /* Turn per-pass event timing on (1) or off (0); reset / read the counters. */
 int meb_set_profiling(meb_ctx *ctx, int on);
 int meb_reset_stats(meb_ctx *ctx);
@@ -121,6 +162,19 @@ int meb_get_stats(meb_ctx *ctx, meb_stats *out);
 int meb_solve(meb_ctx *ctx, const double *centers, const double *radii, int64_t m, int32_t d,
               double tol, const meb_params *params, unsigned flags, double *c_out,
               int64_t *active_idx, int64_t active_cap, meb_info *info);
+
+/* The multipliers (u_i, v_i) = sigma Pi_Q(z_i) at the point the last
+ * meb_solve on this context returned (Algorithm 1's multiplier update at the
+ * last accepted point; the KKT residuals info->kkt were evaluated with them).
+ * Only balls with a nonzero multiplier are listed, in ascending ball order:
+ * idx[k], u[k] and v[k*d .. k*d+d-1] for k < min(cap, *n_sup); *n_sup is the
+ * true count.  The multipliers do not depend on the problem's scale.  For
+ * m = 1 the list is (0, 1, 0); when every ball is the same point it is every
+ * ball with u = 1/m, v = 0.  flags & MEB_PTR_DEVICE: idx, u and v are device
+ * pointers; n_sup is a host pointer.  Valid until the next call that computes
+ * on the context; MEB_EINVAL if there is no such solve. */
+int meb_get_multipliers(meb_ctx *ctx, unsigned flags, int64_t *idx, double *u, double *v,
+                        int64_t cap, int64_t *n_sup);
 
 /* One evaluation of the prox-AL subproblem (Sec. 4, Algorithm 2 steps 1-2) at
  * x = (r, c) (x[0] = r) with proximal centre xbar, multipliers U (m), V (m x d),
@@ -157,8 +211,10 @@ int meb_feas_check(meb_ctx *ctx, const double *centers, const double *radii, int
  * call returns after it completes.  centers (m x d), radii (m), c (d) and
  * viol_idx (viol_cap entries, may be NULL with viol_cap 0) are DEVICE pointers on
  * the current device; delta_max, argmax and n_viol are host pointers.
- * Scratch: a fixed static device array (about 33 KB per GPU that loads the
- * library, held until exit); the call allocates and frees nothing.  The first
+ * Scratch: a fixed static device array (about 37 KB per GPU that loads the
+ * library, held until exit); the call allocates and frees nothing.  A negative
+ * or non-finite radius, or any non-finite value of a row or of c (so that a
+ * ball's value is not finite), returns MEB_EINVAL.  The first
  * call on a device caches the array's device address (cudaGetSymbolAddress):
  * make it before any stream capture on that device.  All calls share the array:
  * calls that overlap on the GPU (several streams or host threads) race.

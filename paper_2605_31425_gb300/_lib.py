@@ -16,6 +16,11 @@ from . import build as _build
 
 MEB_OK, MEB_EINVAL, MEB_ENOMEM, MEB_ECUDA, MEB_ENOTCONV, MEB_ETIMEOUT = 0, -1, -2, -3, -4, -5
 MEB_PTR_DEVICE = 1
+# context options and screen modes (include/meb.h)
+MEB_OPT_SCREEN, MEB_OPT_EVAL_SCREEN, MEB_OPT_EVAL_SHADOW_EXP, MEB_OPT_TICK_LOOP, \
+    MEB_OPT_WAIT_CYCLES = 1, 2, 3, 4, 5
+SCREEN_MODES = {"fp16": 0, "fp16_bulk": 1, "fp32": 2, "fp64": 3}
+TICK_LOOPS = {"graph": 0, "host": 1, "while": 2}
 
 _D = ct.POINTER(ct.c_double)
 _I64 = ct.POINTER(ct.c_int64)
@@ -89,6 +94,11 @@ def load():
                                                    ct.c_double, ct.c_void_p, _D, _I64, _I64,
                                                    ct.c_int64, _I64]
             lib.meb_feas_check_noalloc.restype = ct.c_int
+            lib.meb_set_option.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int64]
+            lib.meb_set_option.restype = ct.c_int
+            lib.meb_get_multipliers.argtypes = [ct.c_void_p, ct.c_uint, _I64, _D, _D, ct.c_int64,
+                                                _I64]
+            lib.meb_get_multipliers.restype = ct.c_int
             lib.meb_set_profiling.argtypes = [ct.c_void_p, ct.c_int]
             lib.meb_reset_stats.argtypes = [ct.c_void_p]
             lib.meb_get_stats.argtypes = [ct.c_void_p, ct.POINTER(MebStats)]
@@ -104,9 +114,12 @@ def params_default() -> MebParams:
 
 class Context:
     """One libmeb context (device + stream).  ``stream`` is a raw cudaStream_t
-    handle (int) or None for a private stream."""
+    handle (int) or None for a private stream.  Keyword options map to
+    meb_set_option: screen ("fp16", "fp16_bulk", "fp32", "fp64"), eval_screen
+    (same names), eval_shadow_exp (int), tick_loop ("graph", "host", "while"),
+    wait_cycles (int)."""
 
-    def __init__(self, device: int = 0, stream: int | None = None):
+    def __init__(self, device: int = 0, stream: int | None = None, **options):
         self._lib = load()
         h = ct.c_void_p()
         rc = self._lib.meb_create(ct.byref(h), int(device), ct.c_void_p(stream) if stream else None)
@@ -114,6 +127,35 @@ class Context:
             raise MebError(rc, "meb_create failed")
         self._h = h
         self.device = device
+        for k, v in options.items():
+            self.set_option(k, v)
+
+    def set_option(self, name: str, value):
+        table = {"screen": (MEB_OPT_SCREEN, SCREEN_MODES),
+                 "eval_screen": (MEB_OPT_EVAL_SCREEN, SCREEN_MODES),
+                 "eval_shadow_exp": (MEB_OPT_EVAL_SHADOW_EXP, None),
+                 "tick_loop": (MEB_OPT_TICK_LOOP, TICK_LOOPS),
+                 "wait_cycles": (MEB_OPT_WAIT_CYCLES, None)}
+        if name not in table:
+            raise ValueError(f"unknown option {name!r}")
+        opt, names = table[name]
+        val = names[value] if names is not None and isinstance(value, str) else int(value)
+        self._check(self._lib.meb_set_option(self._h, opt, val))
+
+    def multipliers(self, cap: int | None = None):
+        """meb_get_multipliers on host arrays: (idx, u, v) of the last solve's
+        final point (balls with nonzero multipliers, ascending)."""
+        n = ct.c_int64()
+        self._check(self._lib.meb_get_multipliers(self._h, 0, None, None, None, 0, ct.byref(n)))
+        k = n.value if cap is None else min(cap, n.value)
+        d = self._last_d
+        idx = np.empty(max(k, 1), dtype=np.int64)
+        u = np.empty(max(k, 1))
+        v = np.empty((max(k, 1), d))
+        self._check(self._lib.meb_get_multipliers(self._h, 0, idx.ctypes.data_as(_I64),
+                                                  u.ctypes.data_as(_D), v.ctypes.data_as(_D),
+                                                  k, ct.byref(n)))
+        return idx[:k], u[:k], v[:k]
 
     def close(self):
         if getattr(self, "_h", None):
@@ -156,6 +198,23 @@ def default_context(device: int = 0, stream: int | None = None) -> Context:
 # ---------------------------------------------------------------- marshalling
 def _is_torch_cuda(a) -> bool:
     return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _check_dev(name, t, shape, dtype="float64"):
+    """A device-path argument must be a contiguous CUDA tensor of the given
+    dtype and shape on the current device: the kernels read exactly that many
+    elements from its pointer."""
+    import torch
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if str(t.dtype) != "torch." + dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on cuda:{t.device.index}, not the current device")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
 
 
 def _ptr(a):
@@ -203,7 +262,11 @@ def solve(centers, radii, tol: float = 0.0, params: MebParams | None = None,
     dev = _is_torch_cuda(centers)
     if dev:
         import torch
+        if centers.dim() != 2:
+            raise ValueError("centers must be m x d")
         m, d = centers.shape
+        _check_dev("centers", centers, (m, d))
+        _check_dev("radii", radii, (m,))
         c_out = torch.empty(d, dtype=torch.float64, device=centers.device)
         cap = m if active_cap is None else active_cap
         act = torch.empty(max(cap, 1), dtype=torch.int64, device=centers.device)
@@ -229,6 +292,7 @@ def solve(centers, radii, tol: float = 0.0, params: MebParams | None = None,
                            ct.byref(params) if params is not None else None,
                            MEB_PTR_DEVICE if dev else 0, _as_d(po), _as_i(pa), cap,
                            ct.byref(info))
+    cx._last_d = d
     cx._check(rc, ok=(MEB_OK, MEB_ENOTCONV) if allow_notconv else (MEB_OK,))
     na = int(info.n_active)
     return dict(
@@ -247,7 +311,15 @@ def eval_alm(centers, radii, x, xbar, U, V, sigma, tau, q=None, want_H=False,
     dev = _is_torch_cuda(centers)
     if dev:
         import torch
+        if centers.dim() != 2:
+            raise ValueError("centers must be m x d")
         m, d = centers.shape
+        for nm, t, shp in (("centers", centers, (m, d)), ("radii", radii, (m,)),
+                           ("x", x, (d + 1,)), ("xbar", xbar, (d + 1,)), ("U", U, (m,)),
+                           ("V", V, (m, d))):
+            _check_dev(nm, t, shp)
+        if q is not None:
+            _check_dev("q", q, (d + 1,))
         mk = lambda *s: torch.empty(*s, dtype=torch.float64, device=centers.device)  # noqa: E731
         C, R, X, XB, UU, VV, Q = centers, radii, x, xbar, U, V, q
     else:
@@ -279,7 +351,12 @@ def feas_check(centers, radii, c, r, eps, cap=None, ctx: Context | None = None):
     dev = _is_torch_cuda(centers)
     if dev:
         import torch
+        if centers.dim() != 2:
+            raise ValueError("centers must be m x d")
         m, d = centers.shape
+        _check_dev("centers", centers, (m, d))
+        _check_dev("radii", radii, (m,))
+        _check_dev("c", c, (d,))
         cap = m if cap is None else cap
         viol = torch.empty(max(cap, 1), dtype=torch.int64, device=centers.device)
         C, R, cc = centers, radii, c
@@ -305,9 +382,20 @@ def feas_check_noalloc(centers, radii, c, r, eps, viol, stream: int | None = Non
     """meb_feas_check_noalloc: the allocation-free feasibility check, for callers
     that cannot call cudaMalloc.  centers, radii, c and viol (int64, its length
     is the cap) are torch CUDA tensors on the current device; no context, no
-    allocation inside the library.  Returns (delta_max, argmax, n_viol)."""
+    allocation inside the library.  The work runs on ``stream`` (a raw
+    cudaStream_t), by default torch's current stream.  Returns
+    (delta_max, argmax, n_viol)."""
+    import torch
     lib = load()
+    if centers.dim() != 2:
+        raise ValueError("centers must be m x d")
     m, d = centers.shape
+    _check_dev("centers", centers, (m, d))
+    _check_dev("radii", radii, (m,))
+    _check_dev("c", c, (d,))
+    _check_dev("viol", viol, (viol.numel(),), dtype="int64")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
     dm = ct.c_double()
     am = ct.c_int64()
     nv = ct.c_int64()

@@ -1,7 +1,8 @@
 // libmeb C ABI (include/meb.h): contexts, device memory, and the host loop
 // that launches the device-resident ripALM / SSN steps.  The host never does
 // arithmetic of the method: it validates sizes, moves buffers, launches the
-// kernels of meb_kernels.cu and reads back the controller's action/status.
+// kernels of meb_pass.cu and meb_solve.cu and reads back the controller's
+// action/status.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <new>
@@ -42,11 +43,20 @@ struct meb_ctx {
   int gvar = -1;
   int gprof = -1;
   cudaEvent_t gev[2 * 8] = {};
+  long long gwait = -1;
+  // options (meb_set_option)
   // tick loop: 0 = graph of kUnrollTicks ticks relaunched until the controller
   // stops (default), 1 = host-driven ticks, 2 = graph with a while-node
   int loop_mode = 0;
-  bool screen_fp32 = false;   // solves screen the FP16 shadow unless set
-  bool screen_bulk = false;   // FP16 screens through the bulk-copy pipeline
+  int screen_mode = MEB_SCREEN_FP16;      // solves
+  int eval_screen = MEB_SCREEN_FP32;      // meb_eval_alm
+  int eval_shadow_exp = 0;                // FP16 shadow scale 2^exp of meb_eval_alm
+  long long wait_cycles = 2000000000LL;   // bound of the bulk-copy screen's waits
+  // multipliers of the last solve (meb_get_multipliers): 0 none, 1 the
+  // support arrays of the final point, 2 one ball, 3 all balls the same point
+  int mult_kind = 0;
+  int64_t mult_n = 0, mult_m = 0;
+  int mult_d = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   meb_stats stats{};
   int prof_screens = 0;
@@ -268,16 +278,6 @@ int meb_create(meb_ctx** out, int device, void* cuda_stream) {
     e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
     ctx->own_stream = (e == cudaSuccess);
   }
-  {
-    const char* lm = getenv("MEB_TICK_LOOP");
-    if (lm && !strcmp(lm, "host")) ctx->loop_mode = 1;
-    if (lm && !strcmp(lm, "while")) ctx->loop_mode = 2;
-    // "fp32": solves screen the FP32 shadow; "bulk": the FP16 shadow through
-    // the bulk-copy pipeline
-    const char* sp = getenv("MEB_SCREEN");
-    ctx->screen_fp32 = sp && !strcmp(sp, "fp32");
-    ctx->screen_bulk = sp && !strcmp(sp, "bulk");
-  }
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_st, sizeof(DevState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_scal, 64 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_flags, 16 * sizeof(int));
@@ -314,6 +314,32 @@ void meb_destroy(meb_ctx* ctx) {
 }
 
 const char* meb_last_error(const meb_ctx* ctx) { return ctx ? ctx->err : "no context"; }
+
+int meb_set_option(meb_ctx* ctx, int32_t option, int64_t value) {
+  if (!ctx) return MEB_EINVAL;
+  switch (option) {
+    case MEB_OPT_SCREEN:
+    case MEB_OPT_EVAL_SCREEN:
+      if (value < MEB_SCREEN_FP16 || value > MEB_SCREEN_FP64)
+        return fail(ctx, MEB_EINVAL, "unknown screen mode %lld", (long long)value);
+      (option == MEB_OPT_SCREEN ? ctx->screen_mode : ctx->eval_screen) = (int)value;
+      return MEB_OK;
+    case MEB_OPT_EVAL_SHADOW_EXP:
+      if (value < -60 || value > 60) return fail(ctx, MEB_EINVAL, "shadow exponent out of range");
+      ctx->eval_shadow_exp = (int)value;
+      return MEB_OK;
+    case MEB_OPT_TICK_LOOP:
+      if (value < 0 || value > 2) return fail(ctx, MEB_EINVAL, "unknown tick loop %lld", (long long)value);
+      ctx->loop_mode = (int)value;
+      return MEB_OK;
+    case MEB_OPT_WAIT_CYCLES:
+      if (value < 0) return fail(ctx, MEB_EINVAL, "negative wait limit");
+      ctx->wait_cycles = (long long)value;
+      return MEB_OK;
+    default:
+      return fail(ctx, MEB_EINVAL, "unknown option %d", (int)option);
+  }
+}
 
 int meb_set_profiling(meb_ctx* ctx, int on) {
   if (!ctx) return MEB_EINVAL;
@@ -394,7 +420,7 @@ static int solve_graph(meb_ctx* ctx, const double* C, const double* R, int64_t m
   const int prof = ctx->profiling;
   if (ctx->gexec && ctx->gkey[0] == C && ctx->gkey[1] == R && ctx->gkey[2] == B.st &&
       ctx->gkey[3] == (const void*)(B.use_x16 ? (const void*)B.X16 : (const void*)B.X32) &&
-      ctx->gvar == screen_variant(B, d) &&
+      ctx->gvar == screen_variant(B, d) && ctx->gwait == B.wait_cycles &&
       ctx->gm == m && ctx->gd == d && ctx->gmode == mode && ctx->gprof == prof)
     return MEB_OK;
   if (prof && !ctx->gev[0])
@@ -446,6 +472,7 @@ static int solve_graph(meb_ctx* ctx, const double* C, const double* R, int64_t m
   ctx->gkey[0] = C; ctx->gkey[1] = R; ctx->gkey[2] = B.st;
   ctx->gkey[3] = B.use_x16 ? (const void*)B.X16 : (const void*)B.X32;
   ctx->gvar = screen_variant(B, d);
+  ctx->gwait = B.wait_cycles;
   ctx->gm = m; ctx->gd = d; ctx->gmode = mode; ctx->gprof = prof;
   return MEB_OK;
 }
@@ -479,10 +506,16 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   rc = stage_in(ctx, POOL_R, radii, sizeof(double) * (size_t)m, flags, (const void**)&R);
   if (rc) return rc;
   B.C_in = C;
+  ctx->mult_kind = 0;
+  B.use_x16 = ctx->screen_mode == MEB_SCREEN_FP16 || ctx->screen_mode == MEB_SCREEN_FP16_BULK;
+  B.bulk = ctx->screen_mode == MEB_SCREEN_FP16_BULK;
+  B.fp64_all = ctx->screen_mode == MEB_SCREEN_FP64;
+  B.wait_cycles = ctx->wait_cycles;
   CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
   if (info) memset(info, 0, sizeof(*info));
 
   // FP32 shadow (origin c_0) and the mean centre c0; r0 = max_i ||c0 - c_i|| + r_i
+  // (the shadow also checks the input; the plain FP64 mode reads it no further)
   CK(launch_shadow(C, R, m, d, B, B.vec.o, B.vec.c0, ctx->d_flags, s));
   CK(launch_feas_cert(C, R, m, d, B.vec.c0, 0.0, INFINITY, 2, 1, B, ctx->d_scal, ctx->d_i64,
                       ctx->d_i64 + 1, s));
@@ -513,6 +546,10 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
     if (info) {
       info->r = r; info->r_alm = r; info->scale = 1.0; info->n_active = na; info->status = 0;
     }
+    ctx->mult_kind = (m == 1) ? 2 : 3;
+    ctx->mult_n = m;
+    ctx->mult_m = m;
+    ctx->mult_d = d;
     return MEB_OK;
   }
 
@@ -521,12 +558,12 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   double sc = ldexp(1.0, ex);
   if (sc / 2.0 >= r0) sc /= 2.0;
   CK(cudaMemsetAsync(B.slot, 0xff, sizeof(int) * (size_t)m, s));
-  B.use_x16 = !ctx->screen_fp32;
-  B.bulk = ctx->screen_bulk;
   CK(prepare_pass(B, d));
   CK(prepare_newton(d));
   if (B.use_x16) CK(launch_shadow16(B, m, d, 1.0 / sc, s));
   host_state_defaults(*ctx->h_st, m, d, P, sc);
+  ctx->h_st->sh_s = sc;
+  ctx->h_st->sh_inv_s = 1.0 / sc;
   ctx->h_st->rt_abs = r0;   // initial radius; k_state_init scales it
   CK(cudaMemcpyAsync(B.st, ctx->h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
   CK(launch_state_init(B, d, s));
@@ -535,7 +572,8 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   // per ball: the shadow row (FP16: 16 bytes per 8 coordinates; FP32: 16
   // bytes per 4 coordinates), its error bound, the FP32 radius and the slot
   const int64_t d4 = (d + 3) / 4;
-  const int64_t pass_bytes = m * (B.use_x16 ? 16 * ((d4 + 1) / 2) + 12 : 16 * d4 + 12);
+  const int64_t pass_bytes = B.fp64_all ? m * 8   // the slot read and the list written
+                                         : m * (B.use_x16 ? 16 * ((d4 + 1) / 2) + 12 : 16 * d4 + 12);
 
   const int64_t max_ticks =
       (int64_t)P.max_outer * (P.max_ssn + 2) * (P.max_backtrack + 2) + 16;
@@ -619,6 +657,10 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   const DevState S = *ctx->h_st;
   if (S.status == kStatusWaitTimeout)
     return fail(ctx, MEB_ETIMEOUT, "a device wait timed out (a bulk copy did not complete)");
+  ctx->mult_kind = 1;
+  ctx->mult_n = S.nS;
+  ctx->mult_m = m;
+  ctx->mult_d = d;
 
   // final point, radius lift (max-type value at c) and active set
   double* d_ralm = ctx->d_scal + 1;
@@ -700,10 +742,18 @@ extern "C" int meb_eval_alm(meb_ctx* ctx, const double* centers, const double* r
   if ((rc = stage_in(ctx, POOL_V, V, sizeof(double) * (size_t)m * d, flags, (const void**)&dV))) return rc;
   if (q && (rc = stage_in(ctx, POOL_Q, q, n1b, flags, (const void**)&dq))) return rc;
   B.C_in = C;
+  ctx->mult_kind = 0;
   CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
   CK(launch_shadow(C, R, m, d, B, B.vec.o, B.vec.c0, ctx->d_flags, s));
   CK(cudaMemsetAsync(B.slot, 0xff, sizeof(int) * (size_t)m, s));
-  B.use_x16 = false;   // unscaled data (s = 1): the FP32 shadow
+  // the evaluation is of the unscaled problem (s = 1); an FP16 screen reads
+  // the shadow of the data divided by sh = 2^eval_shadow_exp
+  B.use_x16 = ctx->eval_screen == MEB_SCREEN_FP16 || ctx->eval_screen == MEB_SCREEN_FP16_BULK;
+  B.bulk = ctx->eval_screen == MEB_SCREEN_FP16_BULK;
+  B.fp64_all = ctx->eval_screen == MEB_SCREEN_FP64;
+  B.wait_cycles = ctx->wait_cycles;
+  const double sh = ldexp(1.0, ctx->eval_shadow_exp);
+  if (B.use_x16) CK(launch_shadow16(B, m, d, 1.0 / sh, s));
   CK(prepare_pass(B, d));
   meb_params P;
   meb_params_default(&P);
@@ -711,6 +761,8 @@ extern "C" int meb_eval_alm(meb_ctx* ctx, const double* centers, const double* r
   P.sigma_max = sigma;
   P.tau = tau;
   host_state_defaults(*ctx->h_st, m, d, P, 1.0);
+  ctx->h_st->sh_s = sh;
+  ctx->h_st->sh_inv_s = 1.0 / sh;
   ctx->h_st->eval_only = 1;
   CK(cudaMemcpyAsync(B.st, ctx->h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
   CK(launch_support_from_dense(dU, dV, B, m, d, s));
@@ -773,20 +825,23 @@ extern "C" int meb_feas_check(meb_ctx* ctx, const double* centers, const double*
   rc = ensure_buffers(ctx, m, d);
   if (rc) return rc;
   Buffers& B = ctx->B;
+  ctx->mult_kind = 0;
+  B.fp64_all = ctx->eval_screen == MEB_SCREEN_FP64;
   const double *C, *R, *dc;
   if ((rc = stage_in(ctx, POOL_C, centers, sizeof(double) * (size_t)m * d, flags, (const void**)&C))) return rc;
   if ((rc = stage_in(ctx, POOL_R, radii, sizeof(double) * (size_t)m, flags, (const void**)&R))) return rc;
   if ((rc = stage_in(ctx, POOL_X, c, sizeof(double) * (size_t)d, flags, (const void**)&dc))) return rc;
   CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
   CK(launch_shadow(C, R, m, d, B, B.vec.o, B.vec.c0, ctx->d_flags, s));
-  CK(launch_feas_cert(C, R, m, d, dc, r, eps, 0, 1, B, ctx->d_scal, ctx->d_i64, ctx->d_i64 + 1, s));
+  CK(launch_feas_cert(C, R, m, d, dc, r, eps, 0, 1, B, ctx->d_scal, ctx->d_i64, ctx->d_i64 + 1, s,
+                      false, ctx->d_flags));
   CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_i64, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(ctx->h_scal + 3, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   int bad;
   memcpy(&bad, ctx->h_scal + 3, sizeof(int));
-  if (bad) return fail(ctx, MEB_EINVAL, "non-finite centre or radius, or negative radius");
+  if (bad) return fail(ctx, MEB_EINVAL, "non-finite centre, radius or query, or negative radius");
   int64_t am, nv;
   memcpy(&am, ctx->h_scal + 1, sizeof(int64_t));
   memcpy(&nv, ctx->h_scal + 2, sizeof(int64_t));
@@ -802,3 +857,58 @@ extern "C" int meb_feas_check(meb_ctx* ctx, const double* centers, const double*
   return MEB_OK;
 }
 
+
+extern "C" int meb_get_multipliers(meb_ctx* ctx, unsigned flags, int64_t* idx, double* u,
+                                   double* v, int64_t cap, int64_t* n_sup) {
+  if (!ctx) return MEB_EINVAL;
+  if (!n_sup || cap < 0 || (cap > 0 && (!idx || !u || !v)))
+    return fail(ctx, MEB_EINVAL, "NULL argument");
+  if (ctx->mult_kind == 0) return fail(ctx, MEB_EINVAL, "no solve to report multipliers of");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->mult_n;
+  const int d = ctx->mult_d;
+  *n_sup = n;
+  const int64_t k = n < cap ? n : cap;
+  if (k == 0) return MEB_OK;
+  const bool dev = (flags & MEB_PTR_DEVICE) != 0;
+  if (ctx->mult_kind == 1) {
+    int64_t* didx;
+    double *du, *dv;
+    int rc;
+    if (dev) { didx = idx; du = u; dv = v; }
+    else {
+      if ((rc = pool(ctx, POOL_ACT, sizeof(int64_t) * (size_t)k, (void**)&didx))) return rc;
+      if ((rc = pool(ctx, POOL_UP, sizeof(double) * (size_t)k, (void**)&du))) return rc;
+      if ((rc = pool(ctx, POOL_VP, sizeof(double) * (size_t)k * d, (void**)&dv))) return rc;
+    }
+    CK(launch_mult_out(ctx->B, d, didx, du, dv, k, s));
+    if (!dev) {
+      CK(cudaMemcpyAsync(idx, didx, sizeof(int64_t) * (size_t)k, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(u, du, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(v, dv, sizeof(double) * (size_t)k * d, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return MEB_OK;
+  }
+  // one ball (u = 1) or every ball the same point (u = 1/m); v = 0
+  const double uval = ctx->mult_kind == 2 ? 1.0 : 1.0 / (double)ctx->mult_m;
+  if (dev) {
+    int64_t* hi = nullptr;
+    double* hu = nullptr;
+    CK(cudaMallocHost((void**)&hi, sizeof(int64_t) * (size_t)k));
+    CK(cudaMallocHost((void**)&hu, sizeof(double) * (size_t)k));
+    for (int64_t t = 0; t < k; t++) { hi[t] = t; hu[t] = uval; }
+    cudaError_t e = cudaMemcpyAsync(idx, hi, sizeof(int64_t) * (size_t)k, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(u, hu, sizeof(double) * (size_t)k, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(double) * (size_t)k * d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeHost(hi);
+    cudaFreeHost(hu);
+    CK(e);
+  } else {
+    for (int64_t t = 0; t < k; t++) { idx[t] = t; u[t] = uval; }
+    memset(v, 0, sizeof(double) * (size_t)k * d);
+  }
+  return MEB_OK;
+}

@@ -61,6 +61,7 @@ struct DevState {
   int d, d4, n1;
   int dense;              // 1: dense Cholesky, 0: CG
   double s, inv_s;        // power-of-two scale
+  double sh_s, sh_inv_s;  // scale of the FP16 shadow (s in solves; any power of two in evaluations)
   // parameters (scaled problem)
   double tol, rho, sigma_max, sigma_growth, sigma_ratio, tau, mu;
   int max_outer, max_ssn, max_backtrack, max_cg;
@@ -137,6 +138,8 @@ struct Buffers {
   float* Hlo;           // [n1 x n1] fl32(H - Hhi)
   bool use_x16;         // host side: the screens read X16
   bool bulk;            // host side: FP16 screens through the bulk-copy pipeline
+  bool fp64_all;        // host side: no shadow is read; every ball goes through the FP64 rows
+  long long wait_cycles;   // bound of the bulk-copy screen's waits (SM clock cycles; 0: one test)
   float* R32;           // [m_pad]
   // multipliers (double buffered)
   int* slot;            // [m]
@@ -205,7 +208,8 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 }
 
 // screen kernels: 0 FP32 shadow, 1 FP16 shadow (register batches),
-// 2 FP16 shadow through a bulk-copy (TMA) pipeline in shared memory
+// 2 FP16 shadow through a bulk-copy (TMA) pipeline in shared memory,
+// 3 no shadow (every ball listed for the FP64 rows: the plain FP64 pass)
 int screen_variant(const Buffers& B, int d);
 int pass_blocks(int64_t m, int d, int variant, int* tiles_per_block);
 cudaError_t prepare_pass(const Buffers& B, int d);
@@ -219,8 +223,7 @@ cudaError_t launch_support_rows(const double* C, Buffers& B, int64_t m, int d, c
 cudaError_t launch_feas_cert(const double* C, const double* R, int64_t m, int d, const double* c,
                              double r, double eps, int mode, int want_max, Buffers& B,
                              double* dmax_out, int64_t* argmax_out, int64_t* nviol_out,
-                             cudaStream_t s,
-                             bool reuse_bounds = false);
+                             cudaStream_t s, bool reuse_bounds = false, int* bad = nullptr);
 cudaError_t launch_support_from_dense(const double* U, const double* V, Buffers& B, int64_t m,
                                       int d, cudaStream_t s);
 // ---- launch wrappers: solver kernels (meb_solve.cu) ----
@@ -239,6 +242,8 @@ cudaError_t launch_eval_outputs(const double* C, Buffers& B, int64_t m, int d, c
 cudaError_t launch_eval_prepare(Buffers& B, const double* x, const double* xbar, int d,
                                 cudaStream_t s);
 cudaError_t launch_final_point(Buffers& B, int d, double* c_out, double* r_alm, cudaStream_t s);
+cudaError_t launch_mult_out(Buffers& B, int d, int64_t* idx, double* u, double* v, int64_t cap,
+                            cudaStream_t s);
 cudaError_t launch_loop_cond(Buffers& B, cudaGraphConditionalHandle h, cudaStream_t s);
 
 }  // namespace meb

@@ -7,7 +7,7 @@
 // once they run.  meb_feas_check needs a context, whose scratch buffers are
 // allocated with cudaMalloc; this entry point needs no context and allocates
 // nothing.  Its scratch lives in a file-scope device array of fixed size
-// (kScratchBytes below, about 33 KB), which every GPU that loads the library
+// (kScratchBytes below, about 37 KB), which every GPU that loads the library
 // holds until the process exits.
 //
 // Set-up: the first call on a device (with that device current) looks up the
@@ -21,7 +21,10 @@
 //   n_viol = its true size.
 // Three kernels: per-block maxima and counts over fixed contiguous ranges,
 // one block for the global maximum and the block offsets, then a second sweep
-// that writes the indices in ascending order.  Every scratch slot is written
+// that writes the indices in ascending order (256-ball tiles, ordered by a
+// block-wide prefix of the warps' ballots).  A negative or non-finite radius,
+// a non-finite row or query centre (any value that is not finite) makes the
+// call return MEB_EINVAL, as meb_feas_check does.  Every scratch slot is written
 // before it is read in each call, so nothing needs clearing; calls that
 // overlap on the GPU (two streams, or two host threads) share the array and
 // race.
@@ -47,11 +50,13 @@ struct Scratch {
   long long barg[kBlocks];
   long long bcnt[kBlocks];
   long long boff[kBlocks];
+  int bbad[kBlocks];
   double gmax;
   long long garg;
   long long gcnt;
+  int gbad;
 };
-constexpr size_t kScratchBytes = sizeof(Scratch);   // about 33 KB
+constexpr size_t kScratchBytes = sizeof(Scratch);   // about 37 KB
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -88,6 +93,7 @@ __global__ void __launch_bounds__(kNT) k_nf_count(const double* __restrict__ C,
   extern __shared__ double s_c[];
   __shared__ double s_v[kNT / 32];
   __shared__ long long s_i[kNT / 32], s_n[kNT / 32];
+  __shared__ int s_b[kNT / 32];
   for (int j = threadIdx.x; j < d; j += kNT) s_c[j] = c[j];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -96,23 +102,29 @@ __global__ void __launch_bounds__(kNT) k_nf_count(const double* __restrict__ C,
   const int64_t i1 = (i0 + chunk < m) ? i0 + chunk : m;
   double best = -INFINITY;
   long long bi = LLONG_MAX, cnt = 0;
+  int bad = 0;
   for (int64_t i = i0 + w; i < i1; i += kNT / 32) {   // balls in order per warp
     const double v = ball_val(C, R, s_c, i, d, r, lane);
+    const double ri = R[i];
+    bad |= !isfinite(v) || !(ri >= 0.0) || !isfinite(ri);
     if (v > best) { best = v; bi = i; }
     cnt += (v > eps);
   }
-  if (lane == 0) { s_v[w] = best; s_i[w] = bi; s_n[w] = cnt; }
+  if (lane == 0) { s_v[w] = best; s_i[w] = bi; s_n[w] = cnt; s_b[w] = bad; }
   __syncthreads();
   if (threadIdx.x == 0) {
     double b = -INFINITY;
     long long ix = LLONG_MAX, n = 0;
+    int bb = 0;
     for (int k = 0; k < kNT / 32; k++) {
       if (s_v[k] > b || (s_v[k] == b && s_i[k] < ix)) { b = s_v[k]; ix = s_i[k]; }
       n += s_n[k];
+      bb |= s_b[k];
     }
     S->bmax[blockIdx.x] = b;
     S->barg[blockIdx.x] = ix;
     S->bcnt[blockIdx.x] = n;
+    S->bbad[blockIdx.x] = bb;
   }
 }
 
@@ -120,14 +132,17 @@ __global__ void k_nf_reduce(Scratch* S) {
   if (threadIdx.x != 0) return;
   double b = -INFINITY;
   long long ix = LLONG_MAX, off = 0;
+  int bad = 0;
   for (int k = 0; k < kBlocks; k++) {
     if (S->bmax[k] > b || (S->bmax[k] == b && S->barg[k] < ix)) { b = S->bmax[k]; ix = S->barg[k]; }
     S->boff[k] = off;
     off += S->bcnt[k];
+    bad |= S->bbad[k];
   }
   S->gmax = b;
   S->garg = ix;
   S->gcnt = off;
+  S->gbad = bad;
 }
 
 __global__ void __launch_bounds__(kNT) k_nf_list(const double* __restrict__ C,
@@ -136,21 +151,43 @@ __global__ void __launch_bounds__(kNT) k_nf_list(const double* __restrict__ C,
                                                   double eps, const Scratch* S,
                                                   int64_t* __restrict__ out, int64_t cap) {
   extern __shared__ double s_c[];
+  __shared__ int s_wc[kNT / 32];
   for (int j = threadIdx.x; j < d; j += kNT) s_c[j] = c[j];
   __syncthreads();
-  if (threadIdx.x >= 32) return;   // one warp keeps the ascending order
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t chunk = (m + kBlocks - 1) / kBlocks;
   const int64_t i0 = (int64_t)blockIdx.x * chunk;
   const int64_t i1 = (i0 + chunk < m) ? i0 + chunk : m;
   long long pos = S->boff[blockIdx.x];
-  if (S->bcnt[blockIdx.x] == 0 || pos >= cap) return;
-  for (int64_t i = i0; i < i1 && pos < cap; i++) {
-    const double v = ball_val(C, R, s_c, i, d, r, lane);
-    if (v > eps) {
-      if (lane == 0) out[pos] = i;
-      pos++;
+  if (S->bcnt[blockIdx.x] == 0 || pos >= cap) return;   // the same for the whole block
+  // tiles of 256 balls in order: warp w evaluates balls 32w .. 32w+31 of the
+  // tile (lane q keeps ball q's flag), then the block writes the members at
+  // their ascending positions (the same values as k_nf_count: same code)
+  for (int64_t t0 = i0; t0 < i1 && pos < cap; t0 += kNT) {
+    const int nt = (int)((i1 - t0) < kNT ? (i1 - t0) : kNT);
+    bool mine = false;
+    for (int q = 0; q < 32; q++) {
+      const int loc = 32 * w + q;
+      if (loc >= nt) break;   // uniform within the warp
+      const double v = ball_val(C, R, s_c, t0 + loc, d, r, lane);
+      if (lane == q) mine = v > eps;
     }
+    const bool f = (32 * w + lane < nt) && mine;
+    const unsigned msk = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) s_wc[w] = __popc(msk);
+    __syncthreads();
+    int off = 0, tot = 0;
+#pragma unroll
+    for (int k = 0; k < kNT / 32; k++) {
+      off += (k < w) ? s_wc[k] : 0;
+      tot += s_wc[k];
+    }
+    if (f) {
+      const long long p = pos + off + __popc(msk & ((1u << lane) - 1u));
+      if (p < cap) out[p] = t0 + 32 * w + lane;
+    }
+    pos += tot;
+    __syncthreads();
   }
 }
 
@@ -197,6 +234,7 @@ extern "C" int meb_feas_check_noalloc(const double* centers, const double* radii
   if (cudaGetLastError() != cudaSuccess) return MEB_ECUDA;
   double gmax = 0.0;
   long long garg = 0, gcnt = 0;
+  int gbad = 0;
   const char* base = static_cast<const char*>(sp);
   if (cudaMemcpyAsync(&gmax, base + offsetof(Scratch, gmax), sizeof(double),
                       cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -204,8 +242,11 @@ extern "C" int meb_feas_check_noalloc(const double* centers, const double* radii
                       cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(&gcnt, base + offsetof(Scratch, gcnt), sizeof(long long),
                       cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&gbad, base + offsetof(Scratch, gbad), sizeof(int),
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return MEB_ECUDA;
+  if (gbad) return MEB_EINVAL;
   if (delta_max) *delta_max = gmax;
   if (argmax) *argmax = (int64_t)garg;
   if (n_viol) *n_viol = (int64_t)gcnt;

@@ -227,6 +227,7 @@ struct PassArgs {
   int64_t m, m_pad;
   int d, d4, tiles_per_block;
   int log_slot;
+  long long wait_cycles;  // bound of the bulk-copy screen's waits (0: one non-blocking test)
   const float4* X32;
   const uint4* X16;     // FP16 shadow scaled by 1/s (8 halves per row), or null
   const float* EPS16;   // per ball: FP16 shadow error bound eps_i (scaled units)
@@ -327,8 +328,8 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_screen(PassArgs A, Buffers 
   float4* s_y = reinterpret_cast<float4*>(smem_raw);
   __shared__ int s_wc[kPassWarps];
   __shared__ float s_v2[kPassWarps];
-  // scaled units for the FP16 shadow: multiplying by the power of two 1/s is exact
-  const float sc = HALF ? (float)st->inv_s : 1.0f;
+  // units of the FP16 shadow: multiplying by the power of two 1/s_h is exact
+  const float sc = HALF ? (float)st->sh_inv_s : 1.0f;
   const float4* y4 = reinterpret_cast<const float4*>(A.y32);
   constexpr int GR = ScreenRaw<HALF>::kGroups;
   constexpr int NB = kScreenBatch;
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_screen(PassArgs A, Buffers 
   const int nsup = st->nsup;
   const int* sidx = cur ? A.sup_idx1 : A.sup_idx0;
   const float rq = st->rq32 * sc, yn = st->yn32 * sc;
-  const float unsc = HALF ? (float)st->s : 1.0f;
+  const float unsc = HALF ? (float)st->sh_s : 1.0f;
   float v2sum = 0.0f;
   const int k4 = 4 * GR * nrows;   // terms of each sum (padding terms are exact zeros)
   __syncthreads();
@@ -656,7 +657,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_screen_bulk(PassArgs A, Buf
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)nst * sb + 32 * nrows);
   __shared__ int s_wc[kPassWarps];
   __shared__ float s_v2[kPassWarps];
-  const float sc = (float)st->inv_s;
+  const float sc = (float)st->sh_inv_s;
   const float4* y4 = reinterpret_cast<const float4*>(A.y32);
   for (int g = threadIdx.x; g < 2 * nrows; g += kPassThreads) {
     const float4 y = g < d4 ? y4[g] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -666,7 +667,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_screen_bulk(PassArgs A, Buf
   const int nsup = st->nsup;
   const int* sidx = cur ? A.sup_idx1 : A.sup_idx0;
   const float rq = st->rq32 * sc, yn = st->yn32 * sc;
-  const float unsc = (float)st->s;
+  const float unsc = (float)st->sh_s;
   float v2sum = 0.0f;
   const int k8 = 8 * nrows;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -707,9 +708,10 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_screen_bulk(PassArgs A, Buf
   int count = 0;
   for (int k = 0; k < ntl; k++) {
     const int q = k % nst;
-    const bool ok = mbar_wait_bounded(&bars[q], (uint32_t)((k / nst) & 1));
+    const bool ok = mbar_wait_bounded(&bars[q], (uint32_t)((k / nst) & 1), A.wait_cycles);
     if (__syncthreads_or(!ok)) {
-      // give up: record it, let the copies in flight land (bounded), return
+      // give up: record it, let the copies in flight land (bounded by the
+      // default limit, whatever the wait limit was), return
       if (tid == 0) {
         st->status = kStatusWaitTimeout;
         for (int j = k; j < ntl && j < k + nst; j++)
@@ -784,7 +786,32 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_screen_bulk(PassArgs A, Buf
   if (last_block_ticket(&st->ctr_screen)) early_body(B, A.d, gridDim.x);
 }
 
+// ---------------------------------------------------------------------------
+// The plain FP64 pass (screen variant 3): no shadow is read and nothing is
+// certified; every ball of the block's tiles is listed, in order, for the
+// FP64 rows.  The lower bound of the early rejection is the trivial 0
+// (sum ||Pi||^2 >= 0), so that test stays valid.
+__global__ void __launch_bounds__(kPassThreads) k_screen_all(PassArgs A, Buffers B) {
+  pdl_wait_and_release();
+  DevState* st = A.st;
+  if (st->status != 0 || st->action == ACT_DONE || st->reuse_lists) return;
+  if (A.log_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0) st->screen_log[A.log_slot] = 1;
+  const int64_t ntiles = (A.m + kPassThreads - 1) / kPassThreads;
+  const int64_t t0 = (int64_t)blockIdx.x * A.tiles_per_block;
+  const int64_t t1 = imin64(ntiles, t0 + A.tiles_per_block);
+  const int64_t base = t0 * kPassThreads;
+  const int64_t end = imin64(A.m, t1 * kPassThreads);
+  const int n = end > base ? (int)(end - base) : 0;
+  for (int k = threadIdx.x; k < n; k += kPassThreads) A.unc_idx[base + k] = (int)(base + k);
+  if (threadIdx.x == 0) {
+    A.unc_cnt[blockIdx.x] = n;
+    A.vlb_part[blockIdx.x] = 0.0f;
+  }
+  if (last_block_ticket(&st->ctr_screen)) early_body(B, A.d, gridDim.x);
+}
+
 int screen_variant(const Buffers& B, int d) {
+  if (B.fp64_all) return 3;
   if (!B.use_x16) return 0;
   return (B.bulk && bulk_stages(d) >= 2) ? 2 : 1;
 }
@@ -793,7 +820,8 @@ int screen_variant(const Buffers& B, int d) {
 // (one wave of blocks), cached per size.
 static int screen_resident_blocks(int d, int variant) {
   // one cached entry per variant (and device)
-  static int cached_dev[3] = {-1, -1, -1}, cached_d[3] = {-1, -1, -1}, cached[3] = {0, 0, 0};
+  static int cached_dev[4] = {-1, -1, -1, -1}, cached_d[4] = {-1, -1, -1, -1},
+             cached[4] = {0, 0, 0, 0};
   int dev = 0;
   cudaGetDevice(&dev);
   if (cached_d[variant] != d || cached_dev[variant] != dev) {
@@ -802,6 +830,7 @@ static int screen_resident_blocks(int d, int variant) {
     const int d4 = (d + 3) / 4;
     const size_t sh1 = 16 * (size_t)(2 * ((d4 + 1) / 2));
     if (variant == 2) per = 1;
+    else if (variant == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_screen_all, kPassThreads, 0);
     else if (variant == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_screen<true>, kPassThreads, sh1);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_screen<false>, kPassThreads, sh1);
     if (per < 1) per = 1;
@@ -840,6 +869,7 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
                         cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int log_slot) {
   PassArgs A;
   A.log_slot = log_slot;
+  A.wait_cycles = B.wait_cycles;
   A.C = C; A.R = R; A.m = m;
   const int d4 = (d + 3) / 4;
   A.m_pad = ((m + 255) / 256) * 256;
@@ -873,6 +903,8 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
   if (variant == 2) {   // its shared-memory attribute is set by prepare_pass
     const int nst = bulk_stages(d);
     e = launch_pdl(k_screen_bulk, dim3(nb), dim3(kPassThreads), bulk_smem(d, nst), s, A, B, nst);
+  } else if (variant == 3) {
+    e = launch_pdl(k_screen_all, dim3(nb), dim3(kPassThreads), 0, s, A, B);
   } else if (variant == 1) {
     e = launch_pdl(k_screen<true>, dim3(nb), dim3(kPassThreads), sh1, s, A, B);
   } else {
@@ -1062,6 +1094,7 @@ struct FeasArgs {
   double r, eps;
   int mode;
   int want_max;
+  int all64;            // no bounds: every ball evaluated in FP64 (the plain FP64 pass)
   float* eub;           // [m] upper bound on e_i
   float* elb;           // [m] lower bound on e_i
   float* blb;           // [nb] block max of the lower bounds
@@ -1135,11 +1168,13 @@ __global__ void __launch_bounds__(kFeasNT) k_feas_b(FeasArgs A) {
   for (int j = threadIdx.x; j < A.d; j += kFeasNT) s_c[j] = A.c[j];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t i = (int64_t)blockIdx.x * kFeasNT + tid;
-  const double L = A.want_max ? (double)*A.L : INFINITY;
+  const double L = (A.want_max && !A.all64) ? (double)*A.L : INFINITY;
   // decide from the bounds; 'need' = evaluate in FP64
   bool need = false;
   unsigned char in = 0;
-  if (i < A.m) {
+  if (i < A.m && A.all64) {
+    need = true;
+  } else if (i < A.m) {
     const double eu = (double)A.eub[i], el = (double)A.elb[i];
     const double ae = isinf(A.eps) ? 0.0 : fabs(A.eps);
     const double tolr = 4.0 * DBL_EPSILON * (fabs(eu) + fabs(A.r) + ae);
@@ -1307,17 +1342,25 @@ __global__ void k_count_sum(const int* __restrict__ cnt, int nb, int64_t* __rest
   if (threadIdx.x == 0) *out = sh[0];
 }
 
-// Query shadow for the feasibility pass: y32 = trunc32(c - o), yn >= ||y32||.
+// Query shadow for the feasibility pass: y32 = trunc32(c - o), yn >= ||y32||;
+// a non-finite query centre sets *bad (when given).
 __global__ void k_query_shadow(const double* __restrict__ c, const double* __restrict__ o, int d,
-                               float* __restrict__ y32, float* __restrict__ yn) {
+                               float* __restrict__ y32, float* __restrict__ yn, int* bad) {
   __shared__ double sh[32];
   const int d4 = (d + 3) / 4;
   double q = 0.0;
+  int nf = 0;
   for (int j = threadIdx.x; j < 4 * d4; j += blockDim.x) {
-    const float y = (j < d) ? f64_to_f32_trunc(c[j] - o[j]) : 0.0f;
+    float y = 0.0f;
+    if (j < d) {
+      const double cj = c[j];
+      nf |= !isfinite(cj);
+      y = f64_to_f32_trunc(cj - o[j]);
+    }
     y32[j] = y;
     q += (double)y * (double)y;
   }
+  if (__syncthreads_or(nf) && threadIdx.x == 0 && bad) atomicOr(bad, 1);
   q = block_sum<256>(q, sh);
   if (threadIdx.x == 0) *yn = __double2float_ru(sqrt(q) * (1.0 + 1e-12));
 }
@@ -1325,7 +1368,7 @@ __global__ void k_query_shadow(const double* __restrict__ c, const double* __res
 cudaError_t launch_feas_cert(const double* C, const double* R, int64_t m, int d, const double* c,
                              double r, double eps, int mode, int want_max, Buffers& B,
                              double* dmax_out, int64_t* argmax_out, int64_t* nviol_out,
-                             cudaStream_t s, bool reuse_bounds) {
+                             cudaStream_t s, bool reuse_bounds, int* bad) {
   FeasArgs A;
   A.C = C; A.R = R; A.m = m;
   A.m_pad = ((m + 255) / 256) * 256;
@@ -1334,6 +1377,7 @@ cudaError_t launch_feas_cert(const double* C, const double* R, int64_t m, int d,
   A.c = c;
   A.y32 = B.fq_y32;
   A.r = r; A.eps = eps; A.mode = mode; A.want_max = want_max;
+  A.all64 = B.fp64_all ? 1 : 0;
   A.eub = B.fe_ub; A.elb = B.fe_lb; A.blb = B.fe_blb;
   A.bmax = B.feas_part; A.barg = B.feas_ipart; A.bcnt = B.feas_cnt; A.blist = B.list_tmp;
   A.L = B.fe_L;
@@ -1342,20 +1386,23 @@ cudaError_t launch_feas_cert(const double* C, const double* R, int64_t m, int d,
   cudaError_t e;
   int launched = 3;
   // the bounds on e_i depend only on c: a second check at the same centre
-  // (reuse_bounds) skips the shadow sweep
+  // (reuse_bounds) skips the shadow sweep; the plain FP64 pass has no bounds
   if (!reuse_bounds) {
-    k_query_shadow<<<1, 256, 0, s>>>(c, B.vec.o, d, B.fq_y32, B.fe_L + 1);
+    k_query_shadow<<<1, 256, 0, s>>>(c, B.vec.o, d, B.fq_y32, B.fe_L + 1, bad);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    launched += 1;
+  }
+  if (!reuse_bounds && !A.all64) {
     const size_t sha = 16 * (size_t)A.d4;
     if (sha > 48 * 1024) {
       e = cudaFuncSetAttribute(k_feas_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sha);
       if (e != cudaSuccess) return e;
     }
     k_feas_a<<<nb, kFeasNT, sha, s>>>(A);
-    launched += 2;
+    launched += 1;
   }
-  if (want_max) {
+  if (want_max && !A.all64) {
     k_feas_L<<<1, 256, 0, s>>>(B.fe_blb, nb, B.fe_L);
     launched += 1;
   }

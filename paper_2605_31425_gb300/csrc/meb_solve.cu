@@ -993,6 +993,34 @@ cudaError_t launch_loop_cond(Buffers& B, cudaGraphConditionalHandle h, cudaStrea
   return cudaGetLastError();
 }
 
+// Multipliers (u_i, v_i)^{k+1} = sigma Pi(z_i) at the last accepted point
+// (Algorithm 1's multiplier update), compacted over the support S in ball
+// order: idx[k], u[k], v[k*d ..]; v = sigma b (case I) or u w (case M), with
+// W holding b (I) or w = b/||b|| (M).  The first `cap` support entries.
+__global__ void k_mult_out(Buffers B, int d, int64_t* __restrict__ idx, double* __restrict__ u,
+                           double* __restrict__ v, int64_t cap) {
+  const DevState* st = B.st;
+  const int64_t nS = st->nS < cap ? st->nS : cap;
+  const double sigma = st->sigma;
+  const int lane = threadIdx.x & 31;
+  for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nS;
+       k += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const double coef = (B.S_case[k] == CASE_I) ? sigma : B.S_u[k];
+    for (int j = lane; j < d; j += 32) v[k * d + j] = coef * B.W[k * d + j];
+    if (lane == 0) {
+      idx[k] = B.S_idx[k];
+      u[k] = B.S_u[k];
+    }
+  }
+}
+
+cudaError_t launch_mult_out(Buffers& B, int d, int64_t* idx, double* u, double* v, int64_t cap,
+                            cudaStream_t s) {
+  k_mult_out<<<152, 256, 0, s>>>(B, d, idx, u, v, cap);
+  B.launches += 1;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_final_point(Buffers& B, int d, double* c_out, double* r_alm, cudaStream_t s) {
   k_final_point<<<1, 256, 0, s>>>(B, d, c_out, r_alm);
   B.launches += 1;

@@ -212,37 +212,27 @@ def test_device_pointer_path():
     assert np.array_equal(g["active"].cpu().numpy(), h["active"])
 
 
-def test_screen_shadows_agree(monkeypatch):
-    """Solves screen the FP16 shadow with register batches; MEB_SCREEN=bulk
-    screens it through the bulk-copy pipeline and MEB_SCREEN=fp32 screens the
-    FP32 shadow.  The certificates only decide which balls skip
-    the FP64 evaluation, so the solves agree to the solve tolerance and keep
-    the same active set."""
+def test_screen_shadows_agree():
+    """Solves screen the FP16 shadow with register batches (default); the
+    fp16_bulk option screens it through the bulk-copy pipeline, fp32 screens
+    the FP32 shadow and fp64 screens nothing (every ball through the FP64
+    rows).  The certificates only decide which balls skip the FP64 evaluation,
+    so the solves agree to the solve tolerance and keep the same active set."""
     C, R = workloads.cube(30_000, 40, 23, 0.05)
-    ctxs = {}
-    for mode in ("fp32", "bulk", None):
-        if mode is None:
-            monkeypatch.delenv("MEB_SCREEN", raising=False)
-        else:
-            monkeypatch.setenv("MEB_SCREEN", mode)
-        ctxs[mode] = meb.Context(0)
-    monkeypatch.delenv("MEB_SCREEN", raising=False)
-    res = {k: meb.solve(C, R, ctx=c) for k, c in ctxs.items()}
+    res = {k: meb.solve(C, R, ctx=meb.Context(0, screen=k))
+           for k in ("fp16", "fp16_bulk", "fp32", "fp64")}
     ref = oracle.solve(C, R)
     for k, r in res.items():
         assert r["status"] == 0 and r["kkt_max"] <= 1e-10, k
         assert abs(r["r"] - ref["r"]) <= 1e-8 * ref["r"], k
-        assert np.array_equal(r["active"], res[None]["active"]), k
+        assert np.array_equal(r["active"], res["fp16"]["active"]), k
 
 
-@pytest.mark.parametrize("mode", [None, "bulk"])
-def test_screen_ragged_tiles(monkeypatch, mode):
+@pytest.mark.parametrize("mode", ["fp16", "fp16_bulk"])
+def test_screen_ragged_tiles(mode):
     """Both FP16 screens on sizes whose last tile is partial (m not a multiple
     of 256) and on d that leaves padding in the last FP16 row."""
-    if mode:
-        monkeypatch.setenv("MEB_SCREEN", mode)
-    ctx = meb.Context(0)
-    monkeypatch.delenv("MEB_SCREEN", raising=False)
+    ctx = meb.Context(0, screen=mode)
     for m, d, seed in [(1, 5, 1), (257, 3, 2), (5000 - 37, 17, 3), (20_011, 100, 4)]:
         C, R = workloads.cube(m, d, seed, 0.05)
         g = meb.solve(C, R, ctx=ctx)
@@ -251,26 +241,19 @@ def test_screen_ragged_tiles(monkeypatch, mode):
         compare_solution(C, R, g, o)
 
 
-def test_tick_loops_agree(monkeypatch):
+def test_tick_loops_agree():
     """The graph-batched tick loop (default), the host-driven loop and the
     while-node graph run the same kernels in the same order: bit-identical."""
     C, R = workloads.cube(30_000, 40, 17, 0.05)
-    ctxs = {}
-    for mode in ("default", "host", "while"):
-        if mode == "default":
-            monkeypatch.delenv("MEB_TICK_LOOP", raising=False)
-        else:
-            monkeypatch.setenv("MEB_TICK_LOOP", mode)
-        ctxs[mode] = meb.Context(0)
-    monkeypatch.delenv("MEB_TICK_LOOP", raising=False)
+    ctxs = {k: meb.Context(0, tick_loop=k) for k in ("graph", "host", "while")}
     res = {k: meb.solve(C, R, ctx=c) for k, c in ctxs.items()}
-    g = res["default"]
+    g = res["graph"]
     for k in ("host", "while"):
         h = res[k]
         assert g["r"] == h["r"] and np.array_equal(g["c"], h["c"]), k
         assert g["passes"] == h["passes"] and g["ssn_iters"] == h["ssn_iters"], k
         assert np.array_equal(g["active"], h["active"]), k
-    ctx = ctxs["default"]
+    ctx = ctxs["graph"]
     ctx.set_profiling(True)          # event nodes in the graph: same results
     p = meb.solve(C, R, ctx=ctx)
     ctx.set_profiling(False)
@@ -278,3 +261,11 @@ def test_tick_loops_agree(monkeypatch):
     assert ctx.stats()["pass_launches"] > 0
     g2 = meb.solve(C, R, ctx=ctx)    # graph reused
     assert g2["r"] == g["r"] and np.array_equal(g2["c"], g["c"])
+
+
+def test_options_rejected():
+    ctx = meb.Context(0)
+    for name, val in (("screen", 7), ("tick_loop", 3), ("wait_cycles", -1),
+                      ("eval_shadow_exp", 100)):
+        with pytest.raises(meb.MebError):
+            ctx.set_option(name, val)

@@ -11,6 +11,7 @@ does not leak into the next.
 import numpy as np
 import pytest
 
+import oracle
 import paper_2605_31425_gb300 as meb
 from paper_2605_31425_gb300 import workloads
 
@@ -39,6 +40,11 @@ def test_noalloc_matches_feas_check_twice():
         k = min(nv, 500)
         np.testing.assert_array_equal(viol[:k].cpu().numpy(), ref_v[:k])
         assert (viol[k:].cpu().numpy() == -1).all()
+        # and against the CPU oracle's definition (Sec. 4.2), not only the GPU
+        o_dm, o_am, o_v, o_nv = oracle.feas_check(C, R, c, r, eps)
+        assert am == o_am and nv == o_nv
+        assert abs(dm - o_dm) <= (d + 8) * EPS * (np.max(e) + abs(r))
+        np.testing.assert_array_equal(viol[:k].cpu().numpy(), o_v[:k])
 
 
 def test_noalloc_rejects_oversize():
@@ -50,3 +56,27 @@ def test_noalloc_rejects_oversize():
     with pytest.raises(meb.MebError) as e:
         meb.feas_check_noalloc(C, R, c, 1.0, 0.0, viol)
     assert e.value.code == -1
+
+
+def test_noalloc_rejects_invalid_values():
+    torch = pytest.importorskip("torch")
+    C, R = workloads.cube(5000, 6, 3, 0.05)
+    c = np.zeros(6)
+    viol = torch.zeros(8, dtype=torch.int64, device="cuda")
+    for bad in ("radius_nan", "radius_neg", "row_inf", "query_nan"):
+        Cb, Rb, cb = C.copy(), R.copy(), c.copy()
+        if bad == "radius_nan":
+            Rb[77] = np.nan
+        elif bad == "radius_neg":
+            Rb[4000] = -0.5
+        elif bad == "row_inf":
+            Cb[123, 2] = np.inf
+        else:
+            cb[1] = np.nan
+        with pytest.raises(meb.MebError) as e:
+            meb.feas_check_noalloc(torch.from_numpy(Cb).cuda(), torch.from_numpy(Rb).cuda(),
+                                   torch.from_numpy(cb).cuda(), 1.0, 0.0, viol)
+        assert e.value.code == -1, bad
+    with pytest.raises(ValueError):     # float32 centres: refused before any launch
+        meb.feas_check_noalloc(torch.from_numpy(C).float().cuda(), torch.from_numpy(R).cuda(),
+                               torch.from_numpy(c).cuda(), 1.0, 0.0, viol)
