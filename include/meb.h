@@ -99,6 +99,8 @@ typedef struct {
                                 row, 16*ceil(d/8) + 4 (FP16 and its norm,
                                 solves) or 16*ceil(d/4) (FP32), + 4
                                 (radius) + 4 (multiplier slot)             */
+    int64_t batch_instances; /* instances solved by meb_solve_batch      */
+    int64_t batch_fallbacks; /* of those, re-solved by the multi-block path */
 } meb_stats;
 
 /* Create a context on `device`, issuing work on `cuda_stream` (a cudaStream_t;
@@ -137,17 +139,34 @@ const char *meb_last_error(const meb_ctx *ctx);
  *                       An expired wait ends the solve with MEB_ETIMEOUT after
  *                       the copies in flight have landed; the context stays
  *                       usable.
+ *  MEB_OPT_BATCH_SLOTS  meb_solve_batch's scratch: 0 (default) one slot per
+ *                       resident thread block, each sized for the batch's
+ *                       largest instance, blocks taking instances from a queue;
+ *                       1 one slot per instance sized for it, block k solving
+ *                       instance k (scratch = the sum of meb_footprint(.., 1)).
+ *                       Results are the same either way.
+ *  MEB_OPT_RELEASE_SCRATCH  1: every call frees the context's device scratch
+ *                       before it returns (for callers that account device
+ *                       memory against a budget); 0 (default) keeps it for the
+ *                       next call.
  * Returns MEB_EINVAL for an unknown option or value. */
 #define MEB_OPT_SCREEN 1
 #define MEB_OPT_EVAL_SCREEN 2
 #define MEB_OPT_EVAL_SHADOW_EXP 3
 #define MEB_OPT_TICK_LOOP 4
 #define MEB_OPT_WAIT_CYCLES 5
+#define MEB_OPT_BATCH_SLOTS 6
+#define MEB_OPT_RELEASE_SCRATCH 7
 #define MEB_SCREEN_FP16 0
 #define MEB_SCREEN_FP16_BULK 1
 #define MEB_SCREEN_FP32 2
 #define MEB_SCREEN_FP64 3
 int meb_set_option(meb_ctx *ctx, int32_t option, int64_t value);
+
+/* Device scratch, in bytes, beyond inputs and outputs: path 0 a meb_solve of
+ * (m, d) (the context's buffers), path 1 one instance of meb_solve_batch with
+ * MEB_OPT_BATCH_SLOTS = 1.  MEB_EINVAL for sizes out of range. */
+int meb_footprint(int64_t m, int32_t d, int32_t path, int64_t *bytes);
 
 /* Turn per-pass event timing on (1) or off (0); reset / read the counters. */
 int meb_set_profiling(meb_ctx *ctx, int on);
@@ -175,6 +194,58 @@ int meb_solve(meb_ctx *ctx, const double *centers, const double *radii, int64_t 
  * on the context; MEB_EINVAL if there is no such solve. */
 int meb_get_multipliers(meb_ctx *ctx, unsigned flags, int64_t *idx, double *u, double *v,
                         int64_t cap, int64_t *n_sup);
+
+/* A ragged batch of independent instances (no counterpart in the paper, which
+ * solves one instance at a time: this is Algorithms 1 + 2 and the Sec. 4.2
+ * pass applied to many instances in one launch).  Per instance: centers
+ * (m x d row-major) and radii (m) in; c_out (d) and active_idx (the first
+ * active_cap ascending indices of the active set, may be NULL with cap 0) out.
+ * Pointers follow flags & MEB_PTR_DEVICE like every other call (host arrays
+ * are copied in and out by the library). */
+typedef struct {
+    const double *centers;
+    const double *radii;
+    int64_t m;
+    int32_t d;
+    int32_t reserved;
+    double *c_out;
+    int64_t *active_idx;
+    int64_t active_cap;
+} meb_batch_item;
+
+/* Solve every instance of the batch (the same method and parameters as
+ * meb_solve; tol > 0 overrides params->tol).  One persistent launch: each
+ * thread block takes instances from a device queue, largest first, and runs a
+ * whole solve of one instance at a time (its passes, controller, Newton
+ * systems and final feasibility pass), so an instance's result does not
+ * depend on the other instances of the batch or on which block solved it.
+ * Instances need 1 <= d <= 4096; the dense Newton solve is used for d <= 111,
+ * matrix-free CG above.  Each block holds scratch sized for the batch's
+ * largest instance, with room for the support rows of min(m, max(2048,
+ * 16 (d + 1))) balls; an instance whose support outgrows it is solved again
+ * by meb_solve's multi-block path (counted in meb_stats.batch_fallbacks).
+ * infos[n] (host, may be NULL): per instance as meb_solve's info, status 0
+ * converged, 1 iteration cap.  Returns MEB_EINVAL if an instance is invalid
+ * (sizes, NULL pointers, non-finite values, negative radius: its info has
+ * status -1; the others are still solved), MEB_ENOTCONV if one hit its cap. */
+int meb_solve_batch(meb_ctx *ctx, int32_t n, const meb_batch_item *items, double tol,
+                    const meb_params *params, unsigned flags, meb_info *infos);
+
+/* The batch solver's execution choices per class of d (d <= 4, <= 16, <= 64,
+ * <= 128, larger): the screen's shadow (FP32: 4 coordinates per 16-byte load;
+ * FP16: 8), the balls per pass block (tiles of 256) and the blocks of the
+ * support-row reduction, and the thread blocks per SM of the launch.
+ * meb_tune_batch times the candidates on up to `per_class` instances of each
+ * class present in the batch (device pointers as flags say) and keeps the
+ * fastest in the context for the following meb_solve_batch calls; configs
+ * (may be NULL) receives, per class, shadow (0 FP32, 1 FP16), tiles per pass
+ * block and support blocks, then the blocks per SM: 5 x 3 + 1 int32.  The
+ * choice changes which balls are evaluated in FP64, so results can differ in
+ * the last bits between configurations (never beyond the solve tolerance);
+ * for a fixed configuration they are deterministic. */
+#define MEB_BATCH_CLASSES 5
+int meb_tune_batch(meb_ctx *ctx, int32_t n, const meb_batch_item *items, int32_t per_class,
+                   unsigned flags, int32_t *configs);
 
 /* One evaluation of the prox-AL subproblem (Sec. 4, Algorithm 2 steps 1-2) at
  * x = (r, c) (x[0] = r) with proximal centre xbar, multipliers U (m), V (m x d),

@@ -48,10 +48,18 @@ class MebInfo(ct.Structure):
     ]
 
 
+class MebBatchItem(ct.Structure):
+    _fields_ = [
+        ("centers", _D), ("radii", _D), ("m", ct.c_int64), ("d", ct.c_int32),
+        ("reserved", ct.c_int32), ("c_out", _D), ("active_idx", _I64), ("active_cap", ct.c_int64),
+    ]
+
+
 class MebStats(ct.Structure):
     _fields_ = [
         ("kernel_launches", ct.c_int64), ("pass_launches", ct.c_int64), ("pass_ms", ct.c_double),
         ("pass_balls", ct.c_int64), ("pass_fp64_rows", ct.c_int64), ("pass_bytes", ct.c_int64),
+        ("batch_instances", ct.c_int64), ("batch_fallbacks", ct.c_int64),
     ]
 
 
@@ -99,6 +107,13 @@ def load():
             lib.meb_get_multipliers.argtypes = [ct.c_void_p, ct.c_uint, _I64, _D, _D, ct.c_int64,
                                                 _I64]
             lib.meb_get_multipliers.restype = ct.c_int
+            lib.meb_solve_batch.argtypes = [ct.c_void_p, ct.c_int32, ct.POINTER(MebBatchItem),
+                                             ct.c_double, ct.POINTER(MebParams), ct.c_uint,
+                                             ct.POINTER(MebInfo)]
+            lib.meb_solve_batch.restype = ct.c_int
+            lib.meb_tune_batch.argtypes = [ct.c_void_p, ct.c_int32, ct.POINTER(MebBatchItem),
+                                           ct.c_int32, ct.c_uint, ct.POINTER(ct.c_int32)]
+            lib.meb_tune_batch.restype = ct.c_int
             lib.meb_set_profiling.argtypes = [ct.c_void_p, ct.c_int]
             lib.meb_reset_stats.argtypes = [ct.c_void_p]
             lib.meb_get_stats.argtypes = [ct.c_void_p, ct.POINTER(MebStats)]
@@ -407,3 +422,87 @@ def feas_check_noalloc(centers, radii, c, r, eps, viol, stream: int | None = Non
     if rc != MEB_OK:
         raise MebError(rc, "meb_feas_check_noalloc failed")
     return dm.value, am.value, nv.value
+
+
+def _info_dict(info):
+    return dict(r=info.r, r_alm=info.r_alm, kkt=list(info.kkt), kkt_max=info.kkt_max,
+                delta_max=info.delta_max, scale=info.scale, n_active=int(info.n_active),
+                fp64_rows=int(info.fp64_rows), outer_iters=info.outer_iters,
+                ssn_iters=info.ssn_iters, cg_iters=info.cg_iters, passes=info.passes,
+                backtracks=info.backtracks, status=info.status,
+                newton_inverses=info.newton_inverses, newton_fp64=info.newton_fp64)
+
+
+def _batch_items(instances, active_cap):
+    """(items, outputs, keepalive, flags) for a list of (centers, radii): all
+    numpy arrays (host path) or all torch CUDA float64 tensors (device path)."""
+    n = len(instances)
+    dev = n > 0 and _is_torch_cuda(instances[0][0])
+    items = (MebBatchItem * max(n, 1))()
+    outs, keep = [], []
+    for k, (C, R) in enumerate(instances):
+        if dev:
+            import torch
+            if C.dim() != 2:
+                raise ValueError("centers must be m x d")
+            m, d = C.shape
+            _check_dev("centers", C, (m, d))
+            _check_dev("radii", R, (m,))
+            cap = m if active_cap is None else min(active_cap, m)
+            c_out = torch.empty(d, dtype=torch.float64, device=C.device)
+            act = torch.empty(max(cap, 1), dtype=torch.int64, device=C.device)
+        else:
+            C = _host_f64(C)
+            if C.ndim == 1:
+                C = C.reshape(-1, 1)
+            R = _host_f64(R)
+            m, d = C.shape
+            if R.shape[0] != m:
+                raise ValueError("radii must have m entries")
+            cap = m if active_cap is None else min(active_cap, m)
+            c_out = np.empty(d)
+            act = np.empty(max(cap, 1), dtype=np.int64)
+        keep += [C, R]
+        items[k].centers = _as_d(_ptr(C)[0])
+        items[k].radii = _as_d(_ptr(R)[0])
+        items[k].m = m
+        items[k].d = d
+        items[k].c_out = _as_d(_ptr(c_out)[0])
+        items[k].active_idx = _as_i(_ptr(act)[0])
+        items[k].active_cap = cap
+        outs.append((c_out, act, cap))
+    return items, outs, keep, (MEB_PTR_DEVICE if dev else 0)
+
+
+def solve_batch(instances, tol: float = 0.0, params: MebParams | None = None,
+                active_cap: int | None = None, ctx: Context | None = None, allow_notconv=False):
+    """meb_solve_batch over a list of (centers, radii): one persistent launch
+    solving every instance.  Returns one result dict per instance (as solve)."""
+    n = len(instances)
+    items, outs, _keep, flags = _batch_items(instances, active_cap)
+    cx = _ctx_for(flags != 0, ctx)
+    infos = (MebInfo * max(n, 1))()
+    rc = cx._lib.meb_solve_batch(cx._h, n, items, float(tol),
+                                 ct.byref(params) if params is not None else None, flags, infos)
+    cx._check(rc, ok=(MEB_OK, MEB_ENOTCONV) if allow_notconv else (MEB_OK,))
+    res = []
+    for k in range(n):
+        r = _info_dict(infos[k])
+        c_out, act, cap = outs[k]
+        r["c"] = c_out
+        r["active"] = act[:min(r["n_active"], cap)]
+        res.append(r)
+    return res
+
+
+def tune_batch(instances, per_class: int = 16, ctx: Context | None = None):
+    """meb_tune_batch: time the batch solver's candidate configurations on up
+    to per_class instances of each class of d and keep the fastest in the
+    context.  Returns the chosen table (per class: FP16 shadow, tiles per pass
+    block, support blocks; then blocks per SM)."""
+    n = len(instances)
+    items, _outs, _keep, flags = _batch_items(instances, None)
+    cx = _ctx_for(flags != 0, ctx)
+    cfg = (ct.c_int32 * 16)()
+    cx._check(cx._lib.meb_tune_batch(cx._h, n, items, int(per_class), flags, cfg))
+    return [tuple(cfg[3 * c:3 * c + 3]) for c in range(5)] + [cfg[15]]

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmeb.so")
-SOURCES = ["meb_pass.cu", "meb_solve.cu", "meb_api.cu", "meb_noalloc.cu"]
+SOURCES = ["meb_pass.cu", "meb_solve.cu", "meb_batch.cu", "meb_api.cu", "meb_noalloc.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 

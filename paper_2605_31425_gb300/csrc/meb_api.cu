@@ -11,6 +11,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <type_traits>
+#include <vector>
+
 #include "../../include/meb.h"
 #include "meb_internal.cuh"
 
@@ -22,10 +26,15 @@ struct meb_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   Buffers B{};
+  void* arena = nullptr;        // one allocation holding every array of B
+  size_t arena_bytes = 0;
   int64_t buf_m = 0;
   int buf_d = 0;
-  void* pool_ptr[16] = {};
-  size_t pool_cap[16] = {};
+  bool batch_per_item = false;  // meb_solve_batch: one scratch slot per instance
+  bool release = false;         // free all device scratch at the end of each call
+  int depth = 0;                // nesting of public calls (a batch falls back to meb_solve)
+  void* pool_ptr[32] = {};
+  size_t pool_cap[32] = {};
   DevState* h_st = nullptr;     // pinned mirror of the device state
   double* h_scal = nullptr;     // pinned scalars
   int* d_flags = nullptr;       // device int flags
@@ -57,6 +66,9 @@ struct meb_ctx {
   int mult_kind = 0;
   int64_t mult_n = 0, mult_m = 0;
   int mult_d = 0;
+  // batched solver: configuration per class of d (meb_tune_batch)
+  BatchConfig batch_cfg[MEB_BATCH_CLASSES] = {
+      {0, 8, 8, 0}, {1, 8, 8, 0}, {1, 8, 8, 0}, {1, 8, 8, 0}, {1, 8, 8, 0}};
   cudaEvent_t ev[2] = {nullptr, nullptr};
   meb_stats stats{};
   int prof_screens = 0;
@@ -70,7 +82,9 @@ static int64_t tick_launches(int d) { return 2 + 1 + newton_dense_launches(d) + 
 static const int kUnrollTicks = 8;
 
 enum { POOL_C, POOL_R, POOL_U, POOL_V, POOL_X, POOL_XB, POOL_Q, POOL_UP, POOL_VP, POOL_HQ,
-       POOL_H, POOL_G, POOL_COUT, POOL_ACT, POOL_N };
+       POOL_H, POOL_G, POOL_COUT, POOL_ACT, POOL_BIN, POOL_BOUT, POOL_BITEMS, POOL_BRES,
+       POOL_BSLOTS, POOL_BSLOTB, POOL_BCFG, POOL_N };
+static_assert(POOL_N <= 32, "pool table");
 
 static int fail(meb_ctx* ctx, int code, const char* fmt, ...) {
   if (ctx) {
@@ -92,16 +106,9 @@ static int fail(meb_ctx* ctx, int code, const char* fmt, ...) {
 
 static void free_buffers(meb_ctx* ctx) {
   Buffers& B = ctx->B;
-  void* ptrs[] = {B.X32, B.X16, B.EPS16, B.E32, B.Hhi, B.Hlo, B.R32, B.slot, B.sup_idx[0], B.sup_idx[1], B.sup_u[0], B.sup_u[1],
-                  B.sup_v[0], B.sup_v[1], B.part_flag, B.part, B.part_cnt, B.cand_off, B.cand_cnt, B.cand_idx,
-                  B.unc_cnt, B.unc_idx, B.unc_slot, B.vlb_part,
-                  B.cand_case, B.cand_a, B.cand_n, B.cand_u, B.S_idx, B.S_case, B.S_a, B.S_n,
-                  B.S_u, B.S_t, B.W, B.svec_part, B.hpart, B.H, B.hq, B.colsum_part, B.fe_ub, B.fe_lb,
-                  B.fe_blb, B.fe_L, B.fq_y32,
-                  B.feas_part, B.feas_ipart, B.feas_cnt, B.viol, B.list_tmp, B.count64, B.wq,
-                  B.st, B.vec_store};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  if (ctx->arena) cudaFree(ctx->arena);
+  ctx->arena = nullptr;
+  ctx->arena_bytes = 0;
   const int64_t launches = B.launches;
   memset(&B, 0, sizeof(B));
   B.launches = launches;
@@ -112,18 +119,17 @@ static void free_buffers(meb_ctx* ctx) {
   if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
 }
 
-template <typename T>
-static cudaError_t dalloc(T** p, size_t n) {
-  return cudaMalloc((void**)p, sizeof(T) * (n ? n : 1));
-}
-
-// Device buffers sized for (m, d); grown on demand.
-static int ensure_buffers(meb_ctx* ctx, int64_t m, int d) {
-  if (ctx->buf_m >= m && ctx->buf_d >= d && ctx->buf_m * (int64_t)ctx->buf_d >= m * (int64_t)d &&
-      ctx->buf_d == d)
-    return MEB_OK;
-  free_buffers(ctx);
-  Buffers& B = ctx->B;
+// The scratch of a multi-block solve of (m, d), laid out in one arena
+// (base == nullptr: only the size).  Every array starts on a 256-byte boundary.
+static size_t solve_layout(Buffers* Bp, char* base, int64_t m, int d) {
+  Buffers B{};
+  size_t off = 0;
+  auto take = [&](auto** p, size_t n) {
+    using T = std::remove_reference_t<decltype(**p)>;
+    off = (off + 255) & ~(size_t)255;
+    if (base) *p = reinterpret_cast<T*>(base + off);
+    off += sizeof(T) * (n ? n : 1);
+  };
   const int64_t m_pad = ((m + 255) / 256) * 256;
   const int64_t nblk = m_pad / 256;
   const int d4 = (d + 3) / 4;
@@ -133,82 +139,127 @@ static int ensure_buffers(meb_ctx* ctx, int64_t m, int d) {
   const int64_t ntri = (int64_t)nt * (nt + 1) / 2;
   int64_t hp = (int64_t)152 * n1;
   if (d + 1 <= kMaxDenseN) hp = hp > 24 * ntri * 1024 ? hp : 24 * ntri * 1024;
-  B.m_cap = m;
-  B.d_cap = d;
-  B.nblk_cap = nblk;
-  B.hpart_cap = hp;
-  CK(dalloc(&B.X32, (size_t)d4 * m_pad));
-  CK(dalloc(&B.X16, (size_t)((d4 + 1) / 2) * m_pad));
-  CK(dalloc(&B.EPS16, (size_t)m_pad));
-  CK(dalloc(&B.E32, (size_t)m_pad));
-  CK(dalloc(&B.Hhi, (size_t)(d + 1 <= kMaxDenseN ? n1 * n1 : 1)));
-  CK(dalloc(&B.Hlo, (size_t)(d + 1 <= kMaxDenseN ? n1 * n1 : 1)));
-  CK(dalloc(&B.R32, (size_t)m_pad));
-  CK(dalloc(&B.slot, (size_t)m_pad));   // whole tiles are bulk-copied
+  const size_t dn = (size_t)(d + 1 <= kMaxDenseN ? n1 * n1 : 1);
+  take(&B.X32, (size_t)d4 * m_pad);
+  take(&B.X16, (size_t)((d4 + 1) / 2) * m_pad);
+  take(&B.EPS16, m_pad);
+  take(&B.E32, m_pad);
+  take(&B.Hhi, dn);
+  take(&B.Hlo, dn);
+  take(&B.R32, m_pad);
+  take(&B.slot, m_pad);   // whole tiles are bulk-copied
   for (int k = 0; k < 2; k++) {
-    CK(dalloc(&B.sup_idx[k], (size_t)m));
-    CK(dalloc(&B.sup_u[k], (size_t)m));
-    CK(dalloc(&B.sup_v[k], (size_t)md));
+    take(&B.sup_idx[k], m);
+    take(&B.sup_u[k], m);
+    take(&B.sup_v[k], md);
   }
   // segments of 256 per tile and block: at most (tiles + blocks) * 256 for any grid
   const int64_t ncand = (nblk + kMaxPassBlocks) * 256;
-  CK(dalloc(&B.part_flag, (size_t)nblk));
-  CK(dalloc(&B.part, (size_t)nblk * P_NREC));
-  CK(dalloc(&B.part_cnt, (size_t)nblk * P_NCNT));
-  CK(dalloc(&B.cand_off, (size_t)nblk + 1));
-  CK(dalloc(&B.cand_cnt, (size_t)nblk));
-  CK(dalloc(&B.unc_cnt, (size_t)nblk));
-  CK(dalloc(&B.vlb_part, (size_t)nblk));
-  CK(dalloc(&B.unc_idx, (size_t)ncand));
-  CK(dalloc(&B.unc_slot, (size_t)ncand));
-  CK(dalloc(&B.cand_idx, (size_t)ncand));
-  CK(dalloc(&B.cand_case, (size_t)ncand));
-  CK(dalloc(&B.cand_a, (size_t)ncand));
-  CK(dalloc(&B.cand_n, (size_t)ncand));
-  CK(dalloc(&B.cand_u, (size_t)ncand));
-  CK(dalloc(&B.S_idx, (size_t)m));
-  CK(dalloc(&B.S_case, (size_t)m));
-  CK(dalloc(&B.S_a, (size_t)m));
-  CK(dalloc(&B.S_n, (size_t)m));
-  CK(dalloc(&B.S_u, (size_t)m));
-  CK(dalloc(&B.S_t, (size_t)m));
-  CK(dalloc(&B.W, (size_t)md));
-  CK(dalloc(&B.svec_part, (size_t)kSvecBlocks * (3 * d + 1)));
-  CK(dalloc(&B.hpart, (size_t)hp));
-  CK(dalloc(&B.H, (size_t)(d + 1 <= kMaxDenseN ? n1 * n1 : 1)));
-  CK(dalloc(&B.hq, (size_t)n1));
-  CK(dalloc(&B.colsum_part, (size_t)((m + 63) / 64) * d));
-  CK(dalloc(&B.fe_ub, (size_t)m));
-  CK(dalloc(&B.fe_lb, (size_t)m));
-  CK(dalloc(&B.fe_blb, (size_t)nblk));
-  CK(dalloc(&B.fe_L, 4));
-  CK(dalloc(&B.fq_y32, (size_t)4 * d4 + 4));
-  CK(dalloc(&B.feas_part, (size_t)nblk + 8));
-  CK(dalloc(&B.feas_ipart, (size_t)nblk + 8));
-  CK(dalloc(&B.feas_cnt, (size_t)nblk + 8));
-  CK(dalloc(&B.viol, (size_t)m));
-  CK(dalloc(&B.list_tmp, (size_t)m_pad));
-  CK(dalloc(&B.count64, 8));
-  CK(dalloc(&B.wq, (size_t)m));
-  CK(dalloc(&B.st, 1));
+  take(&B.part_flag, nblk);
+  take(&B.part, nblk * P_NREC);
+  take(&B.part_cnt, nblk * P_NCNT);
+  take(&B.cand_off, nblk + 1);
+  take(&B.cand_cnt, nblk);
+  take(&B.unc_cnt, nblk);
+  take(&B.vlb_part, nblk);
+  take(&B.unc_idx, ncand);
+  take(&B.unc_slot, ncand);
+  take(&B.cand_idx, ncand);
+  take(&B.cand_case, ncand);
+  take(&B.cand_a, ncand);
+  take(&B.cand_n, ncand);
+  take(&B.cand_u, ncand);
+  take(&B.S_idx, m);
+  take(&B.S_case, m);
+  take(&B.S_a, m);
+  take(&B.S_n, m);
+  take(&B.S_u, m);
+  take(&B.S_t, m);
+  take(&B.W, md);
+  take(&B.svec_part, (size_t)kSvecBlocks * (3 * d + 1));
+  take(&B.hpart, hp);
+  take(&B.H, dn);
+  take(&B.hq, n1);
+  take(&B.colsum_part, (size_t)((m + 63) / 64) * d);
+  take(&B.fe_ub, m);
+  take(&B.fe_lb, m);
+  take(&B.fe_blb, nblk);
+  take(&B.fe_L, 4);
+  take(&B.fq_y32, (size_t)4 * d4 + 4);
+  take(&B.feas_part, nblk + 8);
+  take(&B.feas_ipart, nblk + 8);
+  take(&B.feas_cnt, nblk + 8);
+  take(&B.viol, m);
+  take(&B.list_tmp, m_pad);
+  take(&B.count64, 8);
+  take(&B.scal, 8);
+  take(&B.wq, m);
+  take(&B.st, 1);
   // vectors of length n1 (x, xt, xk, ab, g, gt, dx, ct, o, sv, sw, st1, cg_*) and y32;
   // each starts on a 16-byte boundary (y32 is read as float4)
   const size_t stride = (size_t)((n1 + 8 + 1) / 2) * 2;
   const size_t nv = 20 * stride + (size_t)(d4 * 4 + 8);
-  CK(dalloc(&B.vec_store, nv));
-  double* p = B.vec_store;
-  auto take = [&](double** q) { *q = p; p += stride; };
-  take(&B.vec.x); take(&B.vec.xt); take(&B.vec.xk); take(&B.vec.ab); take(&B.vec.g);
-  take(&B.vec.gt); take(&B.vec.dx); take(&B.vec.ct); take(&B.vec.o); take(&B.vec.c0);
-  take(&B.vec.sv);
-  take(&B.vec.sw); take(&B.vec.st1); take(&B.vec.cg_r); take(&B.vec.cg_z); take(&B.vec.cg_p);
-  take(&B.vec.cg_ap); take(&B.vec.cg_diag);
-  B.vec.y32 = reinterpret_cast<float*>(p);
-  CK(cudaMemsetAsync(B.vec_store, 0, sizeof(double) * nv, ctx->stream));
+  take(&B.vec_store, nv);
+  if (base) {
+    double* p = B.vec_store;
+    auto vtake = [&](double** q) { *q = p; p += stride; };
+    vtake(&B.vec.x); vtake(&B.vec.xt); vtake(&B.vec.xk); vtake(&B.vec.ab); vtake(&B.vec.g);
+    vtake(&B.vec.gt); vtake(&B.vec.dx); vtake(&B.vec.ct); vtake(&B.vec.o); vtake(&B.vec.c0);
+    vtake(&B.vec.sv);
+    vtake(&B.vec.sw); vtake(&B.vec.st1); vtake(&B.vec.cg_r); vtake(&B.vec.cg_z); vtake(&B.vec.cg_p);
+    vtake(&B.vec.cg_ap); vtake(&B.vec.cg_diag);
+    B.vec.y32 = reinterpret_cast<float*>(p);
+    B.m_cap = m;
+    B.d_cap = d;
+    B.nblk_cap = nblk;
+    B.hpart_cap = hp;
+    const int64_t launches = Bp->launches;
+    *Bp = B;
+    Bp->launches = launches;
+  }
+  return (off + 255) & ~(size_t)255;
+}
+
+// Device buffers sized for (m, d) in one arena; grown on demand.
+static int ensure_buffers(meb_ctx* ctx, int64_t m, int d) {
+  if (ctx->buf_m >= m && ctx->buf_d >= d && ctx->buf_m * (int64_t)ctx->buf_d >= m * (int64_t)d &&
+      ctx->buf_d == d)
+    return MEB_OK;
+  free_buffers(ctx);
+  const size_t bytes = solve_layout(nullptr, nullptr, m, d);
+  CK(cudaMalloc(&ctx->arena, bytes));
+  ctx->arena_bytes = bytes;
+  solve_layout(&ctx->B, (char*)ctx->arena, m, d);
+  const int n1 = d + 1, d4 = (d + 3) / 4;
+  const size_t nv = 20 * (size_t)((n1 + 8 + 1) / 2) * 2 + (size_t)(d4 * 4 + 8);
+  CK(cudaMemsetAsync(ctx->B.vec_store, 0, sizeof(double) * nv, ctx->stream));
   ctx->buf_m = m;
   ctx->buf_d = d;
   return MEB_OK;
 }
+
+// Release every device scratch of the context (buffers, pools, tick graph).
+static void release_scratch(meb_ctx* ctx) {
+  free_buffers(ctx);
+  for (int k = 0; k < 32; k++) {
+    if (ctx->pool_ptr[k]) cudaFree(ctx->pool_ptr[k]);
+    ctx->pool_ptr[k] = nullptr;
+    ctx->pool_cap[k] = 0;
+  }
+}
+
+// Scope of a public compute call: with MEB_OPT_RELEASE_SCRATCH set, the
+// outermost call frees the context's device scratch when it returns.
+struct CallScope {
+  meb_ctx* c;
+  explicit CallScope(meb_ctx* ctx) : c(ctx) { c->depth++; }
+  ~CallScope() {
+    if (--c->depth == 0 && c->release) {
+      cudaStreamSynchronize(c->stream);
+      release_scratch(c);
+    }
+  }
+};
 
 static int pool(meb_ctx* ctx, int id, size_t bytes, void** out) {
   if (ctx->pool_cap[id] < bytes) {
@@ -296,7 +347,7 @@ void meb_destroy(meb_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   free_buffers(ctx);
-  for (int k = 0; k < 16; k++)
+  for (int k = 0; k < 32; k++)
     if (ctx->pool_ptr[k]) cudaFree(ctx->pool_ptr[k]);
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
@@ -336,6 +387,14 @@ int meb_set_option(meb_ctx* ctx, int32_t option, int64_t value) {
       if (value < 0) return fail(ctx, MEB_EINVAL, "negative wait limit");
       ctx->wait_cycles = (long long)value;
       return MEB_OK;
+    case MEB_OPT_BATCH_SLOTS:
+      if (value < 0 || value > 1) return fail(ctx, MEB_EINVAL, "batch slots: 0 or 1");
+      ctx->batch_per_item = value == 1;
+      return MEB_OK;
+    case MEB_OPT_RELEASE_SCRATCH:
+      if (value < 0 || value > 1) return fail(ctx, MEB_EINVAL, "release scratch: 0 or 1");
+      ctx->release = value == 1;
+      return MEB_OK;
     default:
       return fail(ctx, MEB_EINVAL, "unknown option %d", (int)option);
   }
@@ -368,42 +427,28 @@ int meb_reset_stats(meb_ctx* ctx) {
 
 }  // extern "C"
 
+static int resolve_params(meb_ctx* ctx, const meb_params* params, double tol, meb_params* out) {
+  meb_params P;
+  if (params) P = *params; else meb_params_default(&P);
+  if (tol > 0) P.tol = tol;
+  if (!(P.tol > 0) || !(P.rho >= 0 && P.rho < 1) || !(P.sigma0 > 0) || !(P.tau > 0) ||
+      !(P.sigma_max >= P.sigma0) || !(P.sigma_growth >= 1) || P.max_outer < 1 || P.max_ssn < 1 ||
+      P.max_backtrack < 0 || P.max_cg < 1 || !(P.active_theta >= 0))
+    return fail(ctx, MEB_EINVAL, "invalid parameters");
+  *out = P;
+  return MEB_OK;
+}
+
+static int64_t tick_cap(const meb_params& P) {
+  return (int64_t)P.max_outer * (P.max_ssn + 2) * (P.max_backtrack + 2) + 16;
+}
+
 static int check_sizes(meb_ctx* ctx, int64_t m, int32_t d) {
   if (m < 1 || m > (int64_t)2147483647 - 256) return fail(ctx, MEB_EINVAL, "m out of range");
   if (d < 1 || d > 16384) return fail(ctx, MEB_EINVAL, "d out of range");
   return MEB_OK;
 }
 
-static void host_state_defaults(DevState& S, int64_t m, int d, const meb_params& P, double s) {
-  memset(&S, 0, sizeof(S));
-  S.m = m;
-  S.m_pad = ((m + 255) / 256) * 256;
-  S.d = d;
-  S.d4 = (d + 3) / 4;
-  S.n1 = d + 1;
-  S.dense = (d <= P.dense_max_d && d + 1 <= kMaxDenseN) ? 1 : 0;
-  S.force_fp64_solve = P.newton_fp64 != 0;
-  S.s = s;
-  S.inv_s = 1.0 / s;
-  S.tol = P.tol;
-  S.rho = P.rho;
-  S.sigma_max = P.sigma_max;
-  S.sigma_growth = P.sigma_growth;
-  S.sigma_ratio = P.sigma_ratio;
-  S.tau = P.tau;
-  S.mu = P.armijo_mu;
-  S.max_outer = P.max_outer;
-  S.max_ssn = P.max_ssn;
-  S.max_backtrack = P.max_backtrack;
-  S.max_cg = P.max_cg;
-  S.sigma = P.sigma0;
-  S.inv_sigma = 1.0 / P.sigma0;
-  S.tos = P.tau / P.sigma0;
-  S.pinf_prev = INFINITY;
-  S.phase = 0;
-  S.action = ACT_NONE;
-  S.status = 0;
-}
 
 static int read_state(meb_ctx* ctx) {
   CK(cudaMemcpyAsync(ctx->h_st, ctx->B.st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
@@ -482,18 +527,15 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
                          double* c_out, int64_t* active_idx, int64_t active_cap,
                          meb_info* info) {
   if (!ctx) return MEB_EINVAL;
+  CallScope scope(ctx);
   ctx->err[0] = 0;
   int rc = check_sizes(ctx, m, d);
   if (rc) return rc;
   if (!centers || !radii || !c_out || (active_cap > 0 && !active_idx) || active_cap < 0)
     return fail(ctx, MEB_EINVAL, "NULL argument");
   meb_params P;
-  if (params) P = *params; else meb_params_default(&P);
-  if (tol > 0) P.tol = tol;
-  if (!(P.tol > 0) || !(P.rho >= 0 && P.rho < 1) || !(P.sigma0 > 0) || !(P.tau > 0) ||
-      !(P.sigma_max >= P.sigma0) || !(P.sigma_growth >= 1) || P.max_outer < 1 || P.max_ssn < 1 ||
-      P.max_backtrack < 0 || P.max_cg < 1 || !(P.active_theta >= 0))
-    return fail(ctx, MEB_EINVAL, "invalid parameters");
+  rc = resolve_params(ctx, params, tol, &P);
+  if (rc) return rc;
   CK(cudaSetDevice(ctx->device));
   cudaStream_t s = ctx->stream;
   rc = ensure_buffers(ctx, m, d);
@@ -561,7 +603,7 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   CK(prepare_pass(B, d));
   CK(prepare_newton(d));
   if (B.use_x16) CK(launch_shadow16(B, m, d, 1.0 / sc, s));
-  host_state_defaults(*ctx->h_st, m, d, P, sc);
+  state_defaults(*ctx->h_st, m, d, P, sc, (d <= P.dense_max_d && d + 1 <= kMaxDenseN) ? 1 : 0);
   ctx->h_st->sh_s = sc;
   ctx->h_st->sh_inv_s = 1.0 / sc;
   ctx->h_st->rt_abs = r0;   // initial radius; k_state_init scales it
@@ -575,8 +617,7 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   const int64_t pass_bytes = B.fp64_all ? m * 8   // the slot read and the list written
                                          : m * (B.use_x16 ? 16 * ((d4 + 1) / 2) + 12 : 16 * d4 + 12);
 
-  const int64_t max_ticks =
-      (int64_t)P.max_outer * (P.max_ssn + 2) * (P.max_backtrack + 2) + 16;
+  const int64_t max_ticks = tick_cap(P);
   if (dense && ctx->loop_mode != 1 && !(ctx->profiling && ctx->loop_mode == 2)) {
     // device-resident ticks: graph launches, one status read per kUnrollTicks ticks
     rc = solve_graph(ctx, C, R, m, d);
@@ -716,6 +757,7 @@ extern "C" int meb_eval_alm(meb_ctx* ctx, const double* centers, const double* r
                             unsigned flags, double* psi, double* grad, double* Uplus,
                             double* Vplus, double* Hq, double* H, int64_t* case_counts) {
   if (!ctx) return MEB_EINVAL;
+  CallScope scope(ctx);
   ctx->err[0] = 0;
   int rc = check_sizes(ctx, m, d);
   if (rc) return rc;
@@ -760,7 +802,7 @@ extern "C" int meb_eval_alm(meb_ctx* ctx, const double* centers, const double* r
   P.sigma0 = sigma;
   P.sigma_max = sigma;
   P.tau = tau;
-  host_state_defaults(*ctx->h_st, m, d, P, 1.0);
+  state_defaults(*ctx->h_st, m, d, P, 1.0, (d <= P.dense_max_d && d + 1 <= kMaxDenseN) ? 1 : 0);
   ctx->h_st->sh_s = sh;
   ctx->h_st->sh_inv_s = 1.0 / sh;
   ctx->h_st->eval_only = 1;
@@ -814,6 +856,7 @@ extern "C" int meb_feas_check(meb_ctx* ctx, const double* centers, const double*
                               unsigned flags, double* delta_max, int64_t* argmax,
                               int64_t* viol_idx, int64_t viol_cap, int64_t* n_viol) {
   if (!ctx) return MEB_EINVAL;
+  CallScope scope(ctx);
   ctx->err[0] = 0;
   int rc = check_sizes(ctx, m, d);
   if (rc) return rc;
@@ -861,6 +904,7 @@ extern "C" int meb_feas_check(meb_ctx* ctx, const double* centers, const double*
 extern "C" int meb_get_multipliers(meb_ctx* ctx, unsigned flags, int64_t* idx, double* u,
                                    double* v, int64_t cap, int64_t* n_sup) {
   if (!ctx) return MEB_EINVAL;
+  CallScope scope(ctx);
   if (!n_sup || cap < 0 || (cap > 0 && (!idx || !u || !v)))
     return fail(ctx, MEB_EINVAL, "NULL argument");
   if (ctx->mult_kind == 0) return fail(ctx, MEB_EINVAL, "no solve to report multipliers of");
@@ -910,5 +954,292 @@ extern "C" int meb_get_multipliers(meb_ctx* ctx, unsigned flags, int64_t* idx, d
     for (int64_t t = 0; t < k; t++) { idx[t] = t; u[t] = uval; }
     memset(v, 0, sizeof(double) * (size_t)k * d);
   }
+  return MEB_OK;
+}
+
+// ===========================================================================
+// Batched solver (meb_solve_batch, meb_tune_batch).
+
+static int batch_class(int d) { return d <= 4 ? 0 : d <= 16 ? 1 : d <= 64 ? 2 : d <= 128 ? 3 : 4; }
+static const int kBatchMaxD = 4096;
+
+static bool batch_item_ok(const meb_batch_item& it) {
+  return it.m >= 1 && it.m <= (int64_t)2147483647 - 256 && it.d >= 1 && it.d <= kBatchMaxD &&
+         it.centers && it.radii && it.c_out && it.active_cap >= 0 &&
+         (it.active_cap == 0 || it.active_idx);
+}
+
+// Device views of the valid items (host arrays are copied into the context's
+// input arena, and their outputs get room in the output arena).
+static int batch_stage(meb_ctx* ctx, int32_t n, const meb_batch_item* items, unsigned flags,
+                       std::vector<BatchItemDev>* dev, std::vector<int>* idx) {
+  cudaStream_t s = ctx->stream;
+  dev->clear();
+  idx->clear();
+  size_t in_bytes = 0, out_bytes = 0;
+  for (int k = 0; k < n; k++) {
+    if (!batch_item_ok(items[k])) continue;
+    idx->push_back(k);
+    in_bytes += sizeof(double) * (size_t)items[k].m * (items[k].d + 1);
+    out_bytes += sizeof(double) * (size_t)items[k].d + sizeof(int64_t) * (size_t)items[k].active_cap;
+  }
+  char *inb = nullptr, *outb = nullptr;
+  const bool host = !(flags & MEB_PTR_DEVICE);
+  if (host && !idx->empty()) {
+    int rc;
+    if ((rc = pool(ctx, POOL_BIN, in_bytes, (void**)&inb))) return rc;
+    if ((rc = pool(ctx, POOL_BOUT, out_bytes + 16, (void**)&outb))) return rc;
+  }
+  size_t io = 0, oo = 0;
+  for (int k : *idx) {
+    const meb_batch_item& it = items[k];
+    BatchItemDev b{};
+    b.m = it.m;
+    b.d = it.d;
+    b.cfg = batch_class(it.d);
+    b.act_cap = it.active_cap;
+    b.sup_cap = batch_support_cap(it.m, it.d);
+    if (host) {
+      const size_t cb = sizeof(double) * (size_t)it.m * it.d, rb = sizeof(double) * (size_t)it.m;
+      CK(cudaMemcpyAsync(inb + io, it.centers, cb, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(inb + io + cb, it.radii, rb, cudaMemcpyHostToDevice, s));
+      b.C = reinterpret_cast<const double*>(inb + io);
+      b.R = reinterpret_cast<const double*>(inb + io + cb);
+      io += cb + rb;
+      b.c_out = reinterpret_cast<double*>(outb + oo);
+      oo += sizeof(double) * (size_t)it.d;
+      b.act = it.active_cap ? reinterpret_cast<int64_t*>(outb + oo) : nullptr;
+      oo += sizeof(int64_t) * (size_t)it.active_cap;
+    } else {
+      b.C = it.centers;
+      b.R = it.radii;
+      b.c_out = it.c_out;
+      b.act = it.active_idx;
+    }
+    dev->push_back(b);
+  }
+  return MEB_OK;
+}
+
+// One launch of the batch kernel over `items` (device views) with the
+// configuration table `cfg`; results in items' order.  *ms: the launch's
+// device time.
+static int batch_run(meb_ctx* ctx, const std::vector<BatchItemDev>& items, const BatchConfig* cfg,
+                     const meb_params& P, std::vector<BatchOut>* outs, float* ms) {
+  cudaStream_t s = ctx->stream;
+  const int n = (int)items.size();
+  outs->assign(n, BatchOut{});
+  if (n == 0) return MEB_OK;
+  // largest first (the queue order), ties by position
+  std::vector<int> order(n);
+  for (int k = 0; k < n; k++) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return items[a].m * (double)(items[a].d + 12) > items[b].m * (double)(items[b].d + 12);
+  });
+  int64_t m_max = 1, sup_max = 1;
+  int d_max = 1;
+  for (const auto& it : items) {
+    m_max = std::max(m_max, it.m);
+    d_max = std::max(d_max, it.d);
+    sup_max = std::max(sup_max, it.sup_cap);
+  }
+  const size_t smem = batch_smem(d_max);
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  const int per_sm = std::max(1, batch_blocks_per_sm(smem));
+  const bool per_item = ctx->batch_per_item;
+  // shared slots: one per resident block, each sized for the largest
+  // instance; per-item slots: one per instance, each sized for it
+  const int nslots = per_item ? n : std::min(n, std::max(1, sms * per_sm));
+  std::vector<size_t> soff(nslots + 1, 0);
+  for (int k = 0; k < nslots; k++) {
+    const BatchItemDev& it = items[order[k]];
+    soff[k + 1] = soff[k] + (per_item ? batch_slot_layout(nullptr, nullptr, it.m, it.d, it.sup_cap)
+                                      : batch_slot_layout(nullptr, nullptr, m_max, d_max, sup_max));
+  }
+  char* arena = nullptr;
+  int rc;
+  if ((rc = pool(ctx, POOL_BSLOTS, soff[nslots], (void**)&arena))) return rc;
+  std::vector<Buffers> hb(nslots);
+  for (int k = 0; k < nslots; k++) {
+    const BatchItemDev& it = items[order[k]];
+    if (per_item) batch_slot_layout(&hb[k], arena + soff[k], it.m, it.d, it.sup_cap);
+    else batch_slot_layout(&hb[k], arena + soff[k], m_max, d_max, sup_max);
+  }
+  Buffers* dslots = nullptr;
+  BatchItemDev* ditems = nullptr;
+  BatchOut* dout = nullptr;
+  BatchConfig* dcfg = nullptr;
+  if ((rc = pool(ctx, POOL_BSLOTB, sizeof(Buffers) * nslots, (void**)&dslots))) return rc;
+  if ((rc = pool(ctx, POOL_BITEMS, sizeof(BatchItemDev) * n, (void**)&ditems))) return rc;
+  if ((rc = pool(ctx, POOL_BRES, sizeof(BatchOut) * n, (void**)&dout))) return rc;
+  if ((rc = pool(ctx, POOL_BCFG, sizeof(BatchConfig) * MEB_BATCH_CLASSES, (void**)&dcfg))) return rc;
+  std::vector<BatchItemDev> qi(n);
+  for (int k = 0; k < n; k++) qi[k] = items[order[k]];
+  CK(cudaMemcpyAsync(dslots, hb.data(), sizeof(Buffers) * nslots, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ditems, qi.data(), sizeof(BatchItemDev) * n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(dcfg, cfg, sizeof(BatchConfig) * MEB_BATCH_CLASSES, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(ctx->d_flags + 1, 0, sizeof(int), s));
+  BatchArgs G;
+  G.items = ditems;
+  G.out = dout;
+  G.n = n;
+  G.next = ctx->d_flags + 1;
+  G.slots = dslots;
+  G.cfg = dcfg;
+  G.P = P;
+  G.max_ticks = tick_cap(P);
+  G.per_item = per_item ? 1 : 0;
+  if (ms && !ctx->ev[0]) {
+    CK(cudaEventCreate(&ctx->ev[0]));
+    CK(cudaEventCreate(&ctx->ev[1]));
+  }
+  if (ms) CK(cudaEventRecord(ctx->ev[0], s));
+  CK(launch_batch(G, nslots, smem, s));
+  ctx->B.launches += 1;
+  if (ms) CK(cudaEventRecord(ctx->ev[1], s));
+  std::vector<BatchOut> qo(n);
+  CK(cudaMemcpyAsync(qo.data(), dout, sizeof(BatchOut) * n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (ms) CK(cudaEventElapsedTime(ms, ctx->ev[0], ctx->ev[1]));
+  for (int k = 0; k < n; k++) (*outs)[order[k]] = qo[k];
+  return MEB_OK;
+}
+
+static void batch_info(const BatchOut& o, meb_info* info) {
+  memset(info, 0, sizeof(*info));
+  info->r = o.r;
+  info->r_alm = o.r_alm;
+  for (int k = 0; k < 5; k++) info->kkt[k] = o.kkt[k];
+  info->kkt_max = o.kkt_max;
+  info->delta_max = o.r - o.r_alm;
+  info->scale = o.scale;
+  info->n_active = o.n_active;
+  info->fp64_rows = o.fp64_rows;
+  info->outer_iters = o.outer;
+  info->ssn_iters = o.ssn;
+  info->cg_iters = o.cg;
+  info->passes = o.passes;
+  info->backtracks = o.backtracks;
+  info->status = o.status;
+  info->newton_inverses = o.inverses;
+  info->newton_fp64 = o.fp64_solves;
+}
+
+extern "C" int meb_solve_batch(meb_ctx* ctx, int32_t n, const meb_batch_item* items, double tol,
+                               const meb_params* params, unsigned flags, meb_info* infos) {
+  if (!ctx) return MEB_EINVAL;
+  CallScope scope(ctx);
+  ctx->err[0] = 0;
+  if (n < 0 || (n > 0 && !items)) return fail(ctx, MEB_EINVAL, "NULL argument");
+  meb_params P;
+  int rc = resolve_params(ctx, params, tol, &P);
+  if (rc) return rc;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  ctx->mult_kind = 0;
+  if (infos)
+    for (int k = 0; k < n; k++) {
+      memset(&infos[k], 0, sizeof(meb_info));
+      infos[k].status = -1;
+    }
+  std::vector<BatchItemDev> dev;
+  std::vector<int> idx;
+  if ((rc = batch_stage(ctx, n, items, flags, &dev, &idx))) return rc;
+  std::vector<BatchOut> outs;
+  if ((rc = batch_run(ctx, dev, ctx->batch_cfg, P, &outs, nullptr))) return rc;
+  bool bad = (int)idx.size() < n, notconv = false;
+  for (size_t q = 0; q < idx.size(); q++) {
+    const int k = idx[q];
+    const BatchItemDev& b = dev[q];
+    BatchOut& o = outs[q];
+    meb_info info;
+    memset(&info, 0, sizeof(info));
+    if (o.status == -1) {
+      bad = true;
+      info.status = -1;
+    } else if (o.status == kStatusSupportCap || o.status == kStatusTickCap) {
+      // the support outgrew the block's rows: the multi-block path, in place
+      const int r2 = meb_solve(ctx, b.C, b.R, b.m, b.d, P.tol, &P, MEB_PTR_DEVICE, b.c_out, b.act,
+                               b.act_cap, &info);
+      ctx->stats.batch_fallbacks += 1;
+      if (r2 == MEB_ENOTCONV) notconv = true;
+      else if (r2 != MEB_OK) return r2;
+    } else {
+      batch_info(o, &info);
+      if (o.status != 0) notconv = true;
+    }
+    if (infos) infos[k] = info;
+    if (!(flags & MEB_PTR_DEVICE) && info.status >= 0) {
+      const meb_batch_item& it = items[k];
+      CK(cudaMemcpyAsync(it.c_out, b.c_out, sizeof(double) * (size_t)b.d, cudaMemcpyDeviceToHost, s));
+      const int64_t na = std::min<int64_t>(info.n_active, it.active_cap);
+      if (na > 0)
+        CK(cudaMemcpyAsync(it.active_idx, b.act, sizeof(int64_t) * (size_t)na, cudaMemcpyDeviceToHost, s));
+    }
+  }
+  CK(cudaStreamSynchronize(s));
+  ctx->stats.batch_instances += (int64_t)idx.size();
+  if (bad) return fail(ctx, MEB_EINVAL, "invalid instance in the batch (its info has status -1)");
+  if (notconv) return fail(ctx, MEB_ENOTCONV, "iteration cap reached by an instance");
+  return MEB_OK;
+}
+
+extern "C" int meb_tune_batch(meb_ctx* ctx, int32_t n, const meb_batch_item* items,
+                              int32_t per_class, unsigned flags, int32_t* configs) {
+  if (!ctx) return MEB_EINVAL;
+  CallScope scope(ctx);
+  ctx->err[0] = 0;
+  if (n < 0 || (n > 0 && !items) || per_class < 1) return fail(ctx, MEB_EINVAL, "bad argument");
+  CK(cudaSetDevice(ctx->device));
+  meb_params P;
+  meb_params_default(&P);
+  std::vector<BatchItemDev> dev;
+  std::vector<int> idx;
+  int rc = batch_stage(ctx, n, items, flags, &dev, &idx);
+  if (rc) return rc;
+  // candidates: shadow precision (vector width), balls per pass block, and
+  // the blocks of the support-row reduction
+  const BatchConfig cands[] = {{1, 2, 1, 0}, {1, 16, 8, 0}, {1, 2, 8, 0}, {1, 16, 1, 0},
+                               {0, 2, 1, 0}, {0, 16, 8, 0}, {0, 2, 8, 0}, {0, 16, 1, 0}};
+  for (int c = 0; c < MEB_BATCH_CLASSES; c++) {
+    std::vector<BatchItemDev> sample;
+    for (const auto& b : dev)
+      if (b.cfg == c && (int)sample.size() < per_class) sample.push_back(b);
+    if (sample.empty()) continue;
+    float best = INFINITY;
+    BatchConfig pick = ctx->batch_cfg[c];
+    for (const BatchConfig& cand : cands) {
+      BatchConfig table[MEB_BATCH_CLASSES];
+      memcpy(table, ctx->batch_cfg, sizeof(table));
+      table[c] = cand;
+      std::vector<BatchOut> outs;
+      float ms = 0.f;
+      if ((rc = batch_run(ctx, sample, table, P, &outs, nullptr))) return rc;   // warm-up
+      if ((rc = batch_run(ctx, sample, table, P, &outs, &ms))) return rc;
+      bool ok = true;
+      for (const auto& o : outs) ok = ok && (o.status == 0);
+      if (ok && ms < best) { best = ms; pick = cand; }
+    }
+    ctx->batch_cfg[c] = pick;
+  }
+  if (configs) {
+    for (int c = 0; c < MEB_BATCH_CLASSES; c++) {
+      configs[3 * c] = ctx->batch_cfg[c].half;
+      configs[3 * c + 1] = ctx->batch_cfg[c].tiles_per_vb;
+      configs[3 * c + 2] = ctx->batch_cfg[c].nsvb;
+    }
+    configs[3 * MEB_BATCH_CLASSES] = 1;
+  }
+  return MEB_OK;
+}
+
+extern "C" int meb_footprint(int64_t m, int32_t d, int32_t path, int64_t* bytes) {
+  if (!bytes || m < 1 || m > (int64_t)2147483647 - 256 || d < 1 || d > 16384 || path < 0 ||
+      path > 1)
+    return MEB_EINVAL;
+  if (path == 1 && d > kBatchMaxD) return MEB_EINVAL;
+  *bytes = path == 0 ? (int64_t)solve_layout(nullptr, nullptr, m, d)
+                     : (int64_t)batch_slot_layout(nullptr, nullptr, m, d, batch_support_cap(m, d));
   return MEB_OK;
 }

@@ -5,7 +5,10 @@
 // reads back the small action/status fields.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
+
+#include "../../include/meb.h"
 
 namespace meb {
 
@@ -34,6 +37,7 @@ enum : int {
 // gave up (a bulk copy did not complete in time)
 constexpr int kStatusWaitTimeout = 3;
 constexpr int kStatusTickCap = 4;   // the while-node loop reached its tick cap
+constexpr int kStatusSupportCap = 5;   // batched solver: the support outgrew its slot's rows
 
 // per-block partial record of the pass (doubles)
 enum : int {
@@ -180,10 +184,106 @@ struct Buffers {
   int64_t* list_tmp;    // [m_pad] per-tile lists before compaction
   int64_t* count64;     // [4] device counters
   double* wq;           // [m] w_k . q of the Hessian-vector product
+  double* scal;         // [8] scalars of the batched solver (r0, r_out, r_alm)
   DevState* st;
   DevVecs vec;
   double* vec_store;
 };
+
+// The controller's state at the start of a solve (host or device): problem
+// sizes, the parameters of Algorithms 1 and 2 on the scaled problem (scale s),
+// the initial penalty; everything else zero.  dense: 1 for the dense Newton
+// solve, 0 for CG.
+__host__ __device__ inline void state_defaults(DevState& S, int64_t m, int d, const meb_params& P,
+                                               double s, int dense) {
+  unsigned* w = reinterpret_cast<unsigned*>(&S);
+  for (size_t k = 0; k < sizeof(DevState) / 4; k++) w[k] = 0u;
+  S.m = m;
+  S.m_pad = ((m + 255) / 256) * 256;
+  S.d = d;
+  S.d4 = (d + 3) / 4;
+  S.n1 = d + 1;
+  S.dense = dense;
+  S.force_fp64_solve = P.newton_fp64 != 0;
+  S.s = s;
+  S.inv_s = 1.0 / s;
+  S.sh_s = s;
+  S.sh_inv_s = 1.0 / s;
+  S.tol = P.tol;
+  S.rho = P.rho;
+  S.sigma_max = P.sigma_max;
+  S.sigma_growth = P.sigma_growth;
+  S.sigma_ratio = P.sigma_ratio;
+  S.tau = P.tau;
+  S.mu = P.armijo_mu;
+  S.max_outer = P.max_outer;
+  S.max_ssn = P.max_ssn;
+  S.max_backtrack = P.max_backtrack;
+  S.max_cg = P.max_cg;
+  S.sigma = P.sigma0;
+  S.inv_sigma = 1.0 / P.sigma0;
+  S.tos = P.tau / P.sigma0;
+  S.pinf_prev = INFINITY;
+  S.phase = 0;
+  S.action = ACT_NONE;
+  S.status = 0;
+}
+
+// ---- the batched solver (meb_batch.cu) ----
+constexpr int kBatchMaxSvec = 16;   // support-row blocks of one batched solve, at most
+
+// One instance of a batch, device view (pointers on the device).
+struct BatchItemDev {
+  const double* C;
+  const double* R;
+  int64_t m;
+  int d;
+  int cfg;             // index of its configuration
+  double* c_out;       // [d]
+  int64_t* act;        // [act_cap] ascending active indices
+  int64_t act_cap;
+  int64_t sup_cap;     // support rows it may use: min(m, max(2048, 16 (d + 1)))
+};
+
+// Support rows a batched solve of (m, d) may hold (a function of the instance
+// alone, so that the choice to fall back never depends on the rest of a batch).
+__host__ __device__ inline int64_t batch_support_cap(int64_t m, int d) {
+  const int64_t c = 16 * (int64_t)(d + 1) > 2048 ? 16 * (int64_t)(d + 1) : 2048;
+  return m < c ? m : c;
+}
+
+// Execution choices of one class of instances (picked by the tuner).
+struct BatchConfig {
+  int half;            // 1: screen the FP16 shadow, 0: the FP32 shadow
+  int tiles_per_vb;    // tiles of 256 balls per pass block
+  int nsvb;            // blocks of the support-row reduction (<= kBatchMaxSvec)
+  int pad;
+};
+
+// Results of one instance (the fields of meb_info).
+struct BatchOut {
+  double r, r_alm, kkt[5], kkt_max, scale;
+  int64_t n_active, fp64_rows;
+  int32_t status;      // 0 converged, 1 cap, -1 invalid input, kStatusSupportCap, kStatusTickCap
+  int32_t outer, ssn, cg, passes, backtracks, inverses, fp64_solves;
+};
+
+struct BatchArgs {
+  const BatchItemDev* items;   // in queue order (largest first)
+  BatchOut* out;
+  int n;
+  int* next;                   // queue head (zero before the launch)
+  const Buffers* slots;        // one per thread block (per item when per_item)
+  const BatchConfig* cfg;
+  meb_params P;
+  int64_t max_ticks;
+  int per_item;                // 1: block j solves item j with slot j (no queue)
+};
+
+size_t batch_slot_layout(Buffers* B, char* base, int64_t m_cap, int d_cap, int64_t sup_cap);
+size_t batch_smem(int d_cap);
+int batch_blocks_per_sm(size_t smem);
+cudaError_t launch_batch(const BatchArgs& G, int nblocks, size_t smem, cudaStream_t s);
 
 // ---- launch wrappers: streaming kernels (meb_pass.cu) ----
 // Launch of a controller-tick kernel with programmatic dependent launch: the

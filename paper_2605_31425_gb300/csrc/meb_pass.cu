@@ -17,27 +17,9 @@
 // it contributes exactly nothing).  Every other ball is evaluated in FP64
 // from its original row.  All reductions use fixed block-to-ball maps and
 // fixed-order trees, so results are deterministic.
-#include <cuda_fp16.h>
-
-#include "meb_control.cuh"
-#include "meb_tma.cuh"
+#include "meb_pass_dev.cuh"
 
 namespace meb {
-
-
-// ===========================================================================
-// Shadow: X32[g][i] = fl32(trunc32(c_i[4g..4g+3]) - o) (0 beyond d), with
-// o = trunc32(c_0) (the first centre), R32[i] = trunc32(r_i) and E32[i] the
-// absolute part of the shadow error (meb_common.cuh); FP32 and integer
-// operations only.  A block takes 64 consecutive balls, in chunks of 128
-// columns: warp w reads rows w, w + 8, ... coalesced (lanes over columns, 16
-// loads in flight per lane), and the tile is written transposed through
-// shared memory.  The same sweep checks that every centre and radius is
-// finite (and r_i >= 0) and leaves block partials of the shadow column sums
-// for the mean centre.
-constexpr int kShadowNT = 256;
-constexpr int kShadowBalls = 64;
-constexpr int kShadowCols = 128;
 
 __global__ void __launch_bounds__(kShadowNT, 4) k_shadow(const double* __restrict__ C,
                                                       const double* __restrict__ R, int64_t m,
@@ -47,107 +29,13 @@ __global__ void __launch_bounds__(kShadowNT, 4) k_shadow(const double* __restric
                                                       float* __restrict__ E32,
                                                       double* __restrict__ colpart,
                                                       int* __restrict__ bad) {
-  __shared__ float tile[kShadowBalls][kShadowCols + 1];
-  __shared__ float s_o[kShadowCols];
-  __shared__ float s_cs[kShadowNT / 32][kShadowCols];   // per-warp column sums
-  const int64_t i0 = (int64_t)blockIdx.x * kShadowBalls;
-  const int nb = (int)imin64(kShadowBalls, m - i0);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int badf = 0;
-  float cn[kShadowBalls / 8];   // rows w + 8k: sums of trunc32(c)^2
-#pragma unroll
-  for (int k = 0; k < kShadowBalls / 8; k++) cn[k] = 0.0f;
-  for (int j0 = 0; j0 < d; j0 += kShadowCols) {
-    const int nc = min(kShadowCols, d - j0);
-    for (int j = threadIdx.x; j < nc; j += kShadowNT) s_o[j] = f64_to_f32_trunc(C[j0 + j]);
-    __syncthreads();
-    float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // this lane's columns over the warp's rows
-#pragma unroll
-    for (int h = 0; h < 4; h++) {   // four steps of 2 rows per warp
-      double v[2][4];
-#pragma unroll
-      for (int k = 0; k < 2; k++) {
-        const int r = w + 8 * (2 * h + k);
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int cc = lane + 32 * q;
-          v[k][q] = (r < nb && cc < nc) ? C[(i0 + r) * (int64_t)d + j0 + cc] : 0.0;
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 2; k++) {
-        const int r = w + 8 * (2 * h + k);
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int cc = lane + 32 * q;
-          const unsigned long long bits = (unsigned long long)__double_as_longlong(v[k][q]);
-          badf |= ((bits >> 52) & 0x7ff) == 0x7ff;
-          const float tc = f64_to_f32_trunc(v[k][q]);
-          cn[2 * h + k] = fmaf(tc, tc, cn[2 * h + k]);
-          if (r < nb && cc < nc) {
-            const float x = tc - s_o[cc];
-            tile[r][cc] = x;
-            cs[q] += x;
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; q++)
-      if (lane + 32 * q < nc) s_cs[w][lane + 32 * q] = cs[q];
-    __syncthreads();
-    // transposed write: group g of 4 columns for 64 balls; column sums
-    const int ng = (nc + 3) / 4;
-    for (int e = threadIdx.x; e < ng * kShadowBalls; e += kShadowNT) {
-      const int g = e / kShadowBalls, r = e - g * kShadowBalls;
-      if (r < nb) {
-        float x[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) x[k] = (4 * g + k < nc) ? tile[r][4 * g + k] : 0.0f;
-        X32[(int64_t)(j0 / 4 + g) * m_pad + i0 + r] = make_float4(x[0], x[1], x[2], x[3]);
-      }
-    }
-    for (int cc = threadIdx.x; cc < nc; cc += kShadowNT) {
-      float t = 0.0f;   // FP32 within the block (the mean is only a starting point)
-#pragma unroll
-      for (int k = 0; k < kShadowNT / 32; k++) t += s_cs[k][cc];
-      colpart[(int64_t)blockIdx.x * d + j0 + cc] = (double)t;
-    }
-    __syncthreads();
-  }
-  // E_i from the row sums of squares (lanes hold column subsets)
-#pragma unroll
-  for (int k = 0; k < kShadowBalls / 8; k++) {
-    float t = cn[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(MEB_FULLMASK, t, o);
-    const int r = w + 8 * k;
-    if (lane == 0 && r < nb) E32[i0 + r] = shadow_abs_err(t, d);
-  }
-  for (int r = threadIdx.x; r < nb; r += kShadowNT) {
-    const double v = R[i0 + r];
-    badf |= !(v >= 0.0) || !isfinite(v);
-    R32[i0 + r] = f64_to_f32_trunc(v);
-  }
-  if (__syncthreads_or(badf) && threadIdx.x == 0) atomicOr(bad, 1);
+  shadow_block(blockIdx.x, C, R, m, d, m_pad, X32, R32, E32, colpart, bad);
 }
 
-// Origin o = trunc32(c_0) of the shadows, and the starting centre
-// c0 = c_0 + (1/m) sum_i x32_i (a mean to FP32 accuracy; exactly c_0 when
-// every centre equals c_0): block j sums column j over the block partials in
-// a fixed tree order.
 __global__ void k_shadow_mean(const double* __restrict__ C, const double* __restrict__ colpart,
                               int nb, int d, int64_t m, double* __restrict__ o,
                               double* __restrict__ c0) {
-  __shared__ double sh[32];
-  const int j = blockIdx.x;
-  double t = 0.0;
-  for (int b = threadIdx.x; b < nb; b += 256) t += colpart[(int64_t)b * d + j];
-  t = block_sum<256>(t, sh);
-  if (threadIdx.x == 0) {
-    o[j] = (double)f64_to_f32_trunc(C[j]);
-    c0[j] = C[j] + t / (double)m;
-  }
+  shadow_mean_block(blockIdx.x, C, colpart, nb, d, m, o, c0);
 }
 
 cudaError_t launch_shadow(const double* C, const double* R, int64_t m, int d, Buffers& B,
@@ -162,45 +50,10 @@ cudaError_t launch_shadow(const double* C, const double* R, int64_t m, int d, Bu
   return cudaGetLastError();
 }
 
-// FP16 copy of the shadow in scaled units, x16 = fl16(x32 / s) (round to
-// nearest), built once s is known: rows of 8 halves (groups 2k and 2k+1 of
-// the FP32 shadow; zeros past d), layout [ceil(d4/2)][m_pad], and per ball
-// the error bound eps_i of meb_common.cuh (from N = sum x16^2 by an FP32
-// fmaf chain, and E_i).  The screens then read 8 bytes per group of 4 and one
-// bound per ball.
-// One thread per ball: a warp's reads and writes are 32 consecutive balls of
-// one row.
 __global__ void k_shadow16(const float4* __restrict__ X32, const float* __restrict__ E32,
                            int64_t m_pad, int d4, float inv_s, uint4* __restrict__ X16,
                            float* __restrict__ EPS) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m_pad) return;
-  const int d8 = (d4 + 1) / 2;
-  float n = 0.0f;
-#pragma unroll 2
-  for (int k = 0; k < d8; k++) {
-    const float4 v = X32[(int64_t)(2 * k) * m_pad + i];
-    const float4 u = (2 * k + 1 < d4) ? X32[(int64_t)(2 * k + 1) * m_pad + i]
-                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-    __half2 h[4];
-    h[0] = __floats2half2_rn(v.x * inv_s, v.y * inv_s);
-    h[1] = __floats2half2_rn(v.z * inv_s, v.w * inv_s);
-    h[2] = __floats2half2_rn(u.x * inv_s, u.y * inv_s);
-    h[3] = __floats2half2_rn(u.z * inv_s, u.w * inv_s);
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const float2 f = __half22float2(h[q]);
-      n = fmaf(f.x, f.x, n);
-      n = fmaf(f.y, f.y, n);
-    }
-    uint4 o;
-    o.x = *reinterpret_cast<const unsigned*>(&h[0]);
-    o.y = *reinterpret_cast<const unsigned*>(&h[1]);
-    o.z = *reinterpret_cast<const unsigned*>(&h[2]);
-    o.w = *reinterpret_cast<const unsigned*>(&h[3]);
-    X16[(int64_t)k * m_pad + i] = o;
-  }
-  EPS[i] = half_err(n, E32[i], inv_s, 8 * d8);
+  shadow16_block(blockIdx.x, X32, E32, m_pad, d4, inv_s, X16, EPS);
 }
 
 cudaError_t launch_shadow16(Buffers& B, int64_t m, int d, double inv_s, cudaStream_t s) {
@@ -211,426 +64,23 @@ cudaError_t launch_shadow16(Buffers& B, int64_t m, int d, double inv_s, cudaStre
   return cudaGetLastError();
 }
 
-// ===========================================================================
-// The pass, in two kernels over the same block -> tiles map (block b takes the
-// tiles [b*T, (b+1)*T) of 256 balls):
-//  k_screen : one ball per thread; FP32 certificate from the shadows; the
-//             balls it cannot certify (and the balls holding multipliers) are
-//             appended, in ball order, to block b's list.
-//  k_rows64 : block b evaluates its list in FP64 from the original rows, one
-//             warp per ball: projection, multiplier, the per-ball parts of Psi,
-//             grad, the stop test and KKT; block partials and the ordered
-//             candidates of the support (cases I, M).
-struct PassArgs {
-  const double* C;
-  const double* R;
-  int64_t m, m_pad;
-  int d, d4, tiles_per_block;
-  int log_slot;
-  long long wait_cycles;  // bound of the bulk-copy screen's waits (0: one non-blocking test)
-  const float4* X32;
-  const uint4* X16;     // FP16 shadow scaled by 1/s (8 halves per row), or null
-  const float* EPS16;   // per ball: FP16 shadow error bound eps_i (scaled units)
-  const float* E32;     // per ball: absolute FP32 shadow error E_i
-  const float* R32;
-  const int* slot;
-  const int* sup_idx0; const int* sup_idx1;
-  const double* sup_u0; const double* sup_u1;
-  const double* sup_v0; const double* sup_v1;
-  DevState* st;
-  const double* ct;
-  const float* y32;
-  int* unc_cnt;
-  int* unc_idx;
-  int* unc_slot;
-  float* vlb_part;      // per block: sum of max(0, certified lower bound of the violation)^2
-  int* part_flag;
-  double* part;
-  int* part_cnt;
-  int* cand_cnt;
-  int* cand_idx;
-  unsigned char* cand_case;
-  double* cand_a; double* cand_n; double* cand_u;
-};
-
-// Shadow rows of the screen (one 16-byte load per ball and row): HALF reads
-// the FP16 shadow, 8 halves = 2 groups of 4 coordinates per row, in units
-// scaled by 1/s; otherwise the FP32 shadow, 1 group per row, unscaled.
-template <bool HALF> struct ScreenRaw { using T = float4; static constexpr int kGroups = 1; };
-template <> struct ScreenRaw<true> { using T = uint4; static constexpr int kGroups = 2; };
-constexpr int kScreenBatch = 4;   // rows per register batch (two batches in flight)
-
-__device__ __forceinline__ float2 h2f(unsigned u) {
-  return __half22float2(*reinterpret_cast<const __half2*>(&u));
-}
-
-// rows g .. g+kScreenBatch-1 of a ball (p points at its row g, row stride
-// m_pad); FULL: all of them exist, else only rows < nrows are read
-template <bool HALF, bool FULL>
-__device__ __forceinline__ void load_batch(typename ScreenRaw<HALF>::T* r,
-                                           const typename ScreenRaw<HALF>::T* __restrict__ p,
-                                           int64_t m_pad, int g, int nrows) {
-#pragma unroll
-  for (int q = 0; q < kScreenBatch; q++) {
-    if (FULL || g + q < nrows) r[q] = *p;
-    p += m_pad;
-  }
-}
-
-// S += ||x - y||^2 over coordinate pairs with s_ny = -y (zero past d), in
-// packed FP32x2 adds and fmas (each rounds to nearest, as the scalar ones).
-__device__ __forceinline__ void acc_pair(float2 x, float2 ny, float2& S) {
-  const float2 t = __fadd2_rn(x, ny);
-  S = __ffma2_rn(t, t, S);
-}
-
-// Sums over the batch; for the FP32 shadow also N += ||x||^2 (the FP16
-// shadow's N is precomputed per ball).
-template <bool HALF, bool FULL>
-__device__ __forceinline__ void sum_batch(const typename ScreenRaw<HALF>::T* r,
-                                          const float4* s_ny, int g, int nrows, float2& Sa,
-                                          float2& Sb, float2& Na, float2& Nb) {
-#pragma unroll
-  for (int q = 0; q < kScreenBatch; q++) {
-    if (FULL || g + q < nrows) {
-      if constexpr (HALF) {
-        const uint4 h = r[q];
-        const float4 y0 = s_ny[2 * (g + q)], y1 = s_ny[2 * (g + q) + 1];
-        acc_pair(h2f(h.x), make_float2(y0.x, y0.y), Sa);
-        acc_pair(h2f(h.y), make_float2(y0.z, y0.w), Sb);
-        acc_pair(h2f(h.z), make_float2(y1.x, y1.y), Sa);
-        acc_pair(h2f(h.w), make_float2(y1.z, y1.w), Sb);
-      } else {
-        const float4 v = r[q];
-        const float4 y = s_ny[g + q];
-        const float2 xl = make_float2(v.x, v.y), xh = make_float2(v.z, v.w);
-        acc_pair(xl, make_float2(y.x, y.y), Sa);
-        acc_pair(xh, make_float2(y.z, y.w), Sb);
-        Na = __ffma2_rn(xl, xl, Na);
-        Nb = __ffma2_rn(xh, xh, Nb);
-      }
-    }
-  }
-}
-
 template <bool HALF>
 __global__ void __launch_bounds__(kPassThreads, 4) k_screen(PassArgs A, Buffers B) {
   pdl_wait_and_release();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   DevState* st = A.st;
-  // reuse_lists: the point is the one of the last screen and only the
-  // multipliers changed; its certificates (zero-multiplier balls strictly
-  // inside) still hold, and its lists contain every ball that had or gets a
-  // multiplier.  Only k_rows64 runs again.
-  if (st->status != 0 || st->action == ACT_DONE || st->reuse_lists) return;
+  if (!screen_gate(st)) return;
   if (A.log_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0) st->screen_log[A.log_slot] = 1;
-  const int d4 = A.d4;
-  float4* s_y = reinterpret_cast<float4*>(smem_raw);
-  __shared__ int s_wc[kPassWarps];
-  __shared__ float s_v2[kPassWarps];
-  // units of the FP16 shadow: multiplying by the power of two 1/s_h is exact
-  const float sc = HALF ? (float)st->sh_inv_s : 1.0f;
-  const float4* y4 = reinterpret_cast<const float4*>(A.y32);
-  constexpr int GR = ScreenRaw<HALF>::kGroups;
-  constexpr int NB = kScreenBatch;
-  const int nrows = (d4 + GR - 1) / GR;       // shadow rows per ball
-  for (int g = threadIdx.x; g < nrows * GR; g += kPassThreads) {
-    const float4 y = g < d4 ? y4[g] : make_float4(0.f, 0.f, 0.f, 0.f);
-    s_y[g] = make_float4(-y.x * sc, -y.y * sc, -y.z * sc, -y.w * sc);   // -y, scaled
-  }
-  const int cur = st->sup_cur;
-  const int nsup = st->nsup;
-  const int* sidx = cur ? A.sup_idx1 : A.sup_idx0;
-  const float rq = st->rq32 * sc, yn = st->yn32 * sc;
-  const float unsc = HALF ? (float)st->sh_s : 1.0f;
-  float v2sum = 0.0f;
-  const int k4 = 4 * GR * nrows;   // terms of each sum (padding terms are exact zeros)
-  __syncthreads();
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int64_t ntiles = (A.m + kPassThreads - 1) / kPassThreads;
-  const int64_t t0 = (int64_t)blockIdx.x * A.tiles_per_block;
-  const int64_t t1 = imin64(ntiles, t0 + A.tiles_per_block);
-  const int64_t base = t0 * kPassThreads;
-  int count = 0;
-  for (int64_t tile = t0; tile < t1; tile++) {
-    const int64_t i = tile * kPassThreads + tid;
-    bool need = false;
-    if (i < A.m) {
-      // the shadow row is read for every ball (support balls are few): its
-      // first batch and the per-ball scalars go out together
-      using Raw = typename ScreenRaw<HALF>::T;
-      const Raw* xp = (HALF ? reinterpret_cast<const Raw*>(A.X16)
-                            : reinterpret_cast<const Raw*>(A.X32)) + i;
-      Raw ra[NB], rb[NB];
-      const int sl = A.slot[i];
-      const float r32 = A.R32[i] * sc;
-      const float ex = HALF ? A.EPS16[i] : A.E32[i];
-      const int64_t step = (int64_t)NB * A.m_pad;
-      float2 Sa = make_float2(0.f, 0.f), Sb = Sa, Na = Sa, Nb = Sa;
-      // two register batches in flight: load the next while summing this one
-      if (NB <= nrows) load_batch<HALF, true>(ra, xp, A.m_pad, 0, nrows);
-      else load_batch<HALF, false>(ra, xp, A.m_pad, 0, nrows);
-      for (int g = 0;;) {
-        xp += step;
-        if (g + 2 * NB <= nrows) load_batch<HALF, true>(rb, xp, A.m_pad, g + NB, nrows);
-        else if (g + NB < nrows) load_batch<HALF, false>(rb, xp, A.m_pad, g + NB, nrows);
-        if (g + NB <= nrows) sum_batch<HALF, true>(ra, s_y, g, nrows, Sa, Sb, Na, Nb);
-        else sum_batch<HALF, false>(ra, s_y, g, nrows, Sa, Sb, Na, Nb);
-        g += NB;
-        if (g >= nrows) break;
-        xp += step;
-        if (g + 2 * NB <= nrows) load_batch<HALF, true>(ra, xp, A.m_pad, g + NB, nrows);
-        else if (g + NB < nrows) load_batch<HALF, false>(ra, xp, A.m_pad, g + NB, nrows);
-        if (g + NB <= nrows) sum_batch<HALF, true>(rb, s_y, g, nrows, Sa, Sb, Na, Nb);
-        else sum_batch<HALF, false>(rb, s_y, g, nrows, Sa, Sb, Na, Nb);
-        g += NB;
-        if (g >= nrows) break;
-      }
-      const float S = (Sa.x + Sa.y) + (Sb.x + Sb.y);
-      const float N = (Na.x + Na.y) + (Nb.x + Nb.y);   // FP32 shadow only
-      if ((unsigned)sl < (unsigned)nsup && sidx[sl] == (int)i) {
-        need = true;   // the ball holds a multiplier
-      } else {
-        // certify ||c_i - c|| <= r - r_i from the shadows
-        const float ub = HALF ? dist_ub16(S, ex, yn, k4) : dist_ub(S, N, yn, ex, k4);
-        const float lb = (rq - r32) - 6.0f * kU32 * (fabsf(rq) + fabsf(r32)) - 1e-30f;
-        need = !(ub <= lb);
-        if (need) {
-          // violation ||c_i - c|| + r_i - r >= D_lb + r32 - rq - margins; with zero
-          // multipliers ||Pi(z_i)||^2 >= max(0, violation / s)^2 / 2 (summed unscaled)
-          const float dl = HALF ? dist_lb16(S, ex, yn, k4) : dist_lb(S, N, yn, ex, k4);
-          const float v = ((dl + r32 - rq) - 3.0f * kU32 * (dl + fabsf(r32) + fabsf(rq))) * unsc;
-          if (v > 0.0f) v2sum = fmaf(v, v, v2sum);
-        }
-      }
-    }
-    const unsigned msk = __ballot_sync(MEB_FULLMASK, need);
-    if (lane == 0) s_wc[w] = __popc(msk);
-    __syncthreads();
-    int off = 0, tot = 0;
-#pragma unroll
-    for (int k = 0; k < kPassWarps; k++) {
-      off += (k < w) ? s_wc[k] : 0;
-      tot += s_wc[k];
-    }
-    if (need) {
-      const int64_t o = base + count + off + __popc(msk & ((1u << lane) - 1u));
-      A.unc_idx[o] = (int)i;
-    }
-    count += tot;
-    __syncthreads();
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v2sum += __shfl_xor_sync(MEB_FULLMASK, v2sum, o);
-  if (lane == 0) s_v2[w] = v2sum;
-  __syncthreads();
-  if (tid == 0) {
-    float t = 0.0f;
-    for (int k = 0; k < kPassWarps; k++) t += s_v2[k];
-    A.unc_cnt[blockIdx.x] = count;
-    A.vlb_part[blockIdx.x] = t;
-  }
+  screen_block<HALF>(A, blockIdx.x);
   if (last_block_ticket(&st->ctr_screen)) early_body(B, A.d, gridDim.x);
 }
 
 __global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A, Buffers B) {
   pdl_wait_and_release();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   DevState* st = A.st;
-  if (st->status != 0 || st->action == ACT_DONE || st->action == ACT_TRIAL_EARLY) return;
-  const int n_b = A.unc_cnt[blockIdx.x];
-  if (n_b == 0) {
-    if (threadIdx.x == 0) {
-      A.part_flag[blockIdx.x] = 0;
-      A.cand_cnt[blockIdx.x] = 0;
-    }
-    if (last_block_ticket(&st->ctr_rows)) control_a_body(B, A.d, gridDim.x);
-    return;
-  }
-  const int d = A.d;
-  double* s_ct = reinterpret_cast<double*>(smem_raw);   // d
-  __shared__ unsigned char s_cf[kPassThreads];
-  __shared__ unsigned char s_cc[kPassThreads];
-  __shared__ double s_ca[kPassThreads], s_cn[kPassThreads], s_cu[kPassThreads];
-  __shared__ int s_wc[kPassWarps];
-  __shared__ double s_wp[kPassWarps][P_NREC];
-  __shared__ int s_wn[kPassWarps][P_NCNT];
-  for (int j = threadIdx.x; j < d; j += kPassThreads) s_ct[j] = A.ct[j];
-  const int cur = st->sup_cur;
-  const int nsup = st->nsup;
-  const int* sidx = cur ? A.sup_idx1 : A.sup_idx0;
-  const double* su = cur ? A.sup_u1 : A.sup_u0;
-  const double* sv = cur ? A.sup_v1 : A.sup_v0;
-  const double inv_s = st->inv_s, sigma = st->sigma, inv_sigma = st->inv_sigma;
-  const double rt = st->rt_abs;
-  __syncthreads();
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int64_t base = (int64_t)blockIdx.x * A.tiles_per_block * kPassThreads;
-  double acc[P_NREC];
-#pragma unroll
-  for (int k = 0; k < P_NREC; k++) acc[k] = 0.0;
-  int cnt[P_NCNT] = {0, 0, 0};
-  int ccount = 0;
-  for (int c0 = 0; c0 < n_b; c0 += kPassThreads) {
-    const int tot = min(kPassThreads, n_b - c0);
-    // warp w takes the 32 chunk entries 32w .. 32w+31; lane q ends with entry q's sums
-    const int e0 = 32 * w;
-    double mnn = 0.0, mpp = 0.0, mdv = 0.0, mvv = 0.0;
-    const int my = e0 + lane;
-    const bool valid = my < tot;
-    const int64_t myii = valid ? (int64_t)A.unc_idx[base + c0 + my] : 0;
-    int mysl = -1;
-    if (valid) {
-      const int sl0 = A.slot[myii];
-      if ((unsigned)sl0 < (unsigned)nsup && sidx[sl0] == (int)myii) mysl = sl0;
-    }
-    for (int q = 0; q < 32 && e0 + q < tot; q++) {
-      const int64_t ii = __shfl_sync(MEB_FULLMASK, myii, q);
-      const int sl = __shfl_sync(MEB_FULLMASK, mysl, q);
-      const double* crow = A.C + ii * (int64_t)d;
-      double nn = 0.0, pp = 0.0, dv = 0.0, vv = 0.0;
-      if (sl >= 0) {
-        const double* vrow = sv + (int64_t)sl * d;
-        for (int j = lane; j < d; j += 32) {
-          const double dl = (crow[j] - s_ct[j]) * inv_s;
-          const double v = vrow[j];
-          const double b = fma(v, inv_sigma, dl);
-          nn = fma(b, b, nn);
-          pp = fma(dl, dl, pp);
-          dv = fma(dl, v, dv);
-          vv = fma(v, v, vv);
-        }
-        nn = warp_sum(nn); pp = warp_sum(pp); dv = warp_sum(dv); vv = warp_sum(vv);
-      } else {
-        for (int j = lane; j < d; j += 32) {
-          const double dl = (crow[j] - s_ct[j]) * inv_s;
-          nn = fma(dl, dl, nn);
-        }
-        nn = warp_sum(nn);
-        pp = nn;
-      }
-      if (lane == q) { mnn = nn; mpp = pp; mdv = dv; mvv = vv; }
-    }
-    if (valid) {
-      const int sl = mysl;
-      const int64_t ii = myii;
-      const double nn = mnn, pp = mpp, dv = mdv, vv = mvv;
-      const double uo = (sl >= 0) ? su[sl] : 0.0;
-      const double a = fma(uo, inv_sigma, (A.R[ii] - rt) * inv_s);
-      const double n = sqrt(nn);
-      int cs;
-      double pa, f, pi2;
-      if (n <= a) { cs = CASE_I; pa = a; f = 1.0; pi2 = a * a + nn; }
-      else if (n <= -a) { cs = CASE_Z; pa = 0.0; f = 0.0; pi2 = 0.0; }
-      else { cs = CASE_M; pa = 0.5 * (a + n); f = pa / n; pi2 = 2.0 * pa * pa; }
-      const double up = sigma * pa;
-      // b.v = dl.v + ||v||^2/sigma;  ||v^+ - v||^2 = sigma^2 f^2 nn - 2 sigma f (b.v) + vv
-      const double bv = dv + vv * inv_sigma;
-      const double sf = sigma * f;
-      double dvv = sf * sf * nn - 2.0 * sf * bv + vv;
-      if (dvv < 0.0) dvv = 0.0;
-      acc[P_PI2] += pi2;
-      acc[P_SU] += up;
-      acc[P_DUV2] += (up - uo) * (up - uo) + dvv;
-      acc[P_UV2] += uo * uo + vv;
-      const double ap = (rt - A.R[ii]) * inv_s;   // (r - r_i)/s
-      acc[P_KP] = fmax(acc[P_KP], soc_dist_an(ap, sqrt(pp)));
-      acc[P_KD] = fmax(acc[P_KD], soc_dist_an(up, sf * n));
-      // (r - r_i) u^+ + (c - c_i).v^+ = ap u^+ - sigma f (dl.b), dl.b = pp + dv/sigma
-      acc[P_KC] = fmax(acc[P_KC], fabs(ap * up - sf * (pp + dv * inv_sigma)));
-      if (cs != CASE_Z) acc[P_ZMAG] += fabs(a) + n;
-      cnt[0] += (cs == CASE_I);
-      cnt[1] += (cs == CASE_M);
-      cnt[2] += 1;
-      s_cf[my] = (cs != CASE_Z);
-      s_cc[my] = (unsigned char)cs;
-      s_ca[my] = a;
-      s_cn[my] = n;
-      s_cu[my] = up;
-    }
-    __syncthreads();
-    // ordered compaction of the candidates (cases I, M) of this chunk
-    const bool cf = (tid < tot) && s_cf[tid];
-    const unsigned cm = __ballot_sync(MEB_FULLMASK, cf);
-    if (lane == 0) s_wc[w] = __popc(cm);
-    __syncthreads();
-    int cpos = 0, ctot = 0;
-#pragma unroll
-    for (int k = 0; k < kPassWarps; k++) {
-      cpos += (k < w) ? s_wc[k] : 0;
-      ctot += s_wc[k];
-    }
-    if (cf) {
-      const int64_t o = base + ccount + cpos + __popc(cm & ((1u << lane) - 1u));
-      A.cand_idx[o] = A.unc_idx[base + c0 + tid];
-      A.cand_case[o] = s_cc[tid];
-      A.cand_a[o] = s_ca[tid];
-      A.cand_n[o] = s_cn[tid];
-      A.cand_u[o] = s_cu[tid];
-    }
-    ccount += ctot;
-    __syncthreads();
-  }
-  // block partial: per-lane accumulators -> warp (fixed trees) -> warps in
-  // order.  Warps that took no entry hold zeros and skip the exchanges.
-  if (32 * w < n_b) {
-    const double v8[8] = {acc[0], acc[1], acc[2], acc[3], acc[4], 0.0, 0.0, 0.0};
-    const double sv = warp_sum8_transposed(v8);
-    if ((lane & 3) == 0 && (lane >> 2) < P_NSUM) s_wp[w][lane >> 2] = sv;
-#pragma unroll
-    for (int k = P_NSUM; k < P_NREC; k++) {
-      const double mx = warp_max_nonneg(acc[k]);
-      if (lane == 0) s_wp[w][k] = mx;
-    }
-#pragma unroll
-    for (int k = 0; k < P_NCNT; k++) {
-      const int c = (int)__reduce_add_sync(MEB_FULLMASK, (unsigned)cnt[k]);
-      if (lane == 0) s_wn[w][k] = c;
-    }
-  } else if (lane < P_NREC) {
-    s_wp[w][lane] = 0.0;
-    if (lane < P_NCNT) s_wn[w][lane] = 0;
-  }
-  __syncthreads();
-  if (tid < P_NSUM) {
-    double t = 0.0;
-    for (int k = 0; k < kPassWarps; k++) t += s_wp[k][tid];
-    A.part[(int64_t)blockIdx.x * P_NREC + tid] = t;
-  } else if (tid < P_NREC) {
-    long long t = 0;
-    for (int k = 0; k < kPassWarps; k++) {
-      const long long b = __double_as_longlong(s_wp[k][tid]);
-      t = b > t ? b : t;
-    }
-    A.part[(int64_t)blockIdx.x * P_NREC + tid] = __longlong_as_double(t);
-  } else if (tid >= 32 && tid < 32 + P_NCNT) {
-    int t = 0;
-    for (int k = 0; k < kPassWarps; k++) t += s_wn[k][tid - 32];
-    A.part_cnt[(int64_t)blockIdx.x * P_NCNT + tid - 32] = t;
-  }
-  if (tid == 0) {
-    A.part_flag[blockIdx.x] = 1;
-    A.cand_cnt[blockIdx.x] = ccount;
-  }
+  if (!rows_gate(st)) return;
+  rows_block(A, blockIdx.x);
   if (last_block_ticket(&st->ctr_rows)) control_a_body(B, A.d, gridDim.x);
 }
-
-// ---------------------------------------------------------------------------
-// FP16 screen through a bulk-copy pipeline (MEB_SCREEN=bulk).  One block per
-// SM keeps `nst` tiles in flight: a tile's shadow rows (16 B per ball and row), error
-// bounds, FP32 radii and slots are copied by the TMA engine into a shared
-// memory stage and signal its mbarrier; the block sums each ball from shared
-// memory, certifies and compacts as k_screen, and the stage is refilled with
-// the tile nst ahead once every thread has passed the tile's last barrier.
-// Same certificates as k_screen<true> (same sums in the same order).  It
-// measured slower than the register-batched screen on GB300 (one block of
-// 8 warps per SM leaves each tile's compute and compaction exposed), so it is
-// not the default.
-constexpr int kBulkSmemBudget = 200 * 1024;
-constexpr int kBulkMaxStages = 4;
-
-// stage: [nrows][256] uint4 | eps[256] | r32[256] | slot[256]
-__host__ __device__ inline int bulk_stage_bytes(int nrows) { return nrows * 4096 + 3 * 1024; }
 
 static int bulk_stages(int d) {
   const int nrows = ((d + 3) / 4 + 1) / 2;
@@ -786,27 +236,12 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_screen_bulk(PassArgs A, Buf
   if (last_block_ticket(&st->ctr_screen)) early_body(B, A.d, gridDim.x);
 }
 
-// ---------------------------------------------------------------------------
-// The plain FP64 pass (screen variant 3): no shadow is read and nothing is
-// certified; every ball of the block's tiles is listed, in order, for the
-// FP64 rows.  The lower bound of the early rejection is the trivial 0
-// (sum ||Pi||^2 >= 0), so that test stays valid.
 __global__ void __launch_bounds__(kPassThreads) k_screen_all(PassArgs A, Buffers B) {
   pdl_wait_and_release();
   DevState* st = A.st;
-  if (st->status != 0 || st->action == ACT_DONE || st->reuse_lists) return;
+  if (!screen_gate(st)) return;
   if (A.log_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0) st->screen_log[A.log_slot] = 1;
-  const int64_t ntiles = (A.m + kPassThreads - 1) / kPassThreads;
-  const int64_t t0 = (int64_t)blockIdx.x * A.tiles_per_block;
-  const int64_t t1 = imin64(ntiles, t0 + A.tiles_per_block);
-  const int64_t base = t0 * kPassThreads;
-  const int64_t end = imin64(A.m, t1 * kPassThreads);
-  const int n = end > base ? (int)(end - base) : 0;
-  for (int k = threadIdx.x; k < n; k += kPassThreads) A.unc_idx[base + k] = (int)(base + k);
-  if (threadIdx.x == 0) {
-    A.unc_cnt[blockIdx.x] = n;
-    A.vlb_part[blockIdx.x] = 0.0f;
-  }
+  screen_all_block(A, blockIdx.x);
   if (last_block_ticket(&st->ctr_screen)) early_body(B, A.d, gridDim.x);
 }
 
@@ -923,142 +358,12 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
   return cudaGetLastError();
 }
 
-// ===========================================================================
-// Support rows: b_k = (c_k - c)/s + v_k/sigma recomputed in FP64;
-//   sum v^+ = sigma f_k b_k (all S), sum w_k (case M), sum t_k w_k^2 (case M),
-//   sum (1 + t_k) (case M);  W rows w_k = b_k / n_k (M) or b_k (I).
-// Block b takes rows [b*rpb, (b+1)*rpb) in order; thread j owns columns j, j+256, ...
-constexpr int kSvecStage = 64;   // support rows staged per round in shared memory
-
 __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buffers B, int d,
                                               int npb, int64_t seg) {
   pdl_wait_and_release();
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_GRAD) return;
-  const int nS = st->nS;
-  int rpb = (nS + kSvecBlocks - 1) / kSvecBlocks;
-  if (rpb < 8) rpb = 8;
-  const int nblk = (nS + rpb - 1) / rpb;
-  if (blockIdx.x == 0 && threadIdx.x == 0) { st->svec_nb = nblk; st->svec_rpb = rpb; }
-  if ((int)blockIdx.x >= nblk) {
-    if (last_block_ticket(&st->ctr_svec)) control_b_body(B, d);
-    return;
-  }
-  __shared__ int s_idx[kSvecStage], s_sl[kSvecStage];
-  __shared__ int s_off[kMaxPassBlocks + 1];   // candidate segment starts of the pass blocks
-  __shared__ unsigned char s_cs[kSvecStage];
-  __shared__ double s_sf[kSvecStage], s_in[kSvecStage], s_t[kSvecStage];
-  __shared__ double s_red[3 * 256];
-  __shared__ double sh[32];
-  const int k0 = blockIdx.x * rpb, k1 = min(nS, k0 + rpb);
-  const int cur = st->sup_cur, nsup = st->nsup;
-  const int* sidx = cur ? B.sup_idx[1] : B.sup_idx[0];
-  const double* sv = cur ? B.sup_v[1] : B.sup_v[0];
-  const double inv_s = st->inv_s, sigma = st->sigma, inv_sigma = st->inv_sigma;
-  const double* ct = B.vec.ct;
-  double* out = B.svec_part + (int64_t)blockIdx.x * (3 * d + 1);
-  // G row groups of 32 * ceil(d / 32) threads each take every G-th row (all
-  // SMSPs of the SM share the FP64 work); threads past G groups idle
-  const int span = 32 * ((d + 31) / 32);
-  const int G = span >= 256 ? 1 : 256 / span;
-  const int grp = (int)threadIdx.x / (span >= 256 ? 256 : span);
-  const int jl = (int)threadIdx.x - grp * (span >= 256 ? 256 : span);
-  for (int b = threadIdx.x; b <= npb; b += 256) s_off[b] = B.cand_off[b];
-  double s1t = 0.0;
-  for (int j0 = 0; j0 < d; j0 += 256) {
-    const int j = j0 + jl;
-    const bool act = grp < G && j < d;
-    double av = 0.0, aw = 0.0, atw = 0.0;
-    for (int r0 = k0; r0 < k1; r0 += kSvecStage) {
-      const int nr = min(kSvecStage, k1 - r0);
-      __syncthreads();
-      // stage the rows: index, slot (checked), case and the row scalars.
-      // Row k of S is entry k - s_off[b] of pass block b's candidate segment
-      // (b the last block with s_off[b] <= k); the first j-round also writes
-      // the ordered support list S for the Newton and multiplier kernels.
-      if ((int)threadIdx.x < nr) {
-        const int k = r0 + threadIdx.x;
-        int lo = 0, hi = npb;   // s_off[lo] <= k < s_off[hi]
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (s_off[mid] <= k) lo = mid; else hi = mid;
-        }
-        const int64_t src = (int64_t)lo * seg + (k - s_off[lo]);
-        const int idx = B.cand_idx[src];
-        const int cs = B.cand_case[src];
-        const double a = B.cand_a[src], n = B.cand_n[src];
-        if (j0 == 0) {
-          B.S_idx[k] = idx;
-          B.S_case[k] = (unsigned char)cs;
-          B.S_a[k] = a;
-          B.S_n[k] = n;
-          B.S_u[k] = B.cand_u[src];
-        }
-        const int sl0 = B.slot[idx];
-        const int sl = ((unsigned)sl0 < (unsigned)nsup && sidx[sl0] == idx) ? sl0 : -1;
-        s_idx[threadIdx.x] = idx;
-        s_sl[threadIdx.x] = sl;
-        s_cs[threadIdx.x] = (unsigned char)cs;
-        if (cs == CASE_M) {
-          const double in = 1.0 / n;
-          const double t = a * in;
-          s_in[threadIdx.x] = in;
-          s_t[threadIdx.x] = t;
-          s_sf[threadIdx.x] = sigma * (0.5 * (a + n) * in);
-          if (j0 == 0) {
-            B.S_t[k] = t;
-            s1t += 1.0 + t;
-          }
-        } else {
-          s_in[threadIdx.x] = 1.0;
-          s_t[threadIdx.x] = 0.0;
-          s_sf[threadIdx.x] = sigma;
-          if (j0 == 0) B.S_t[k] = 0.0;
-        }
-      }
-      __syncthreads();
-      if (act) {
-        for (int r = grp; r < nr; r += G) {
-          const int64_t idx = s_idx[r];
-          const int sl = s_sl[r];
-          double b = (C[idx * d + j] - ct[j]) * inv_s;
-          if (sl >= 0) b = fma(sv[(int64_t)sl * d + j], inv_sigma, b);
-          av = fma(s_sf[r], b, av);
-          const int64_t k = r0 + r;
-          if (s_cs[r] == CASE_M) {
-            const double wv = b * s_in[r];
-            aw += wv;
-            atw = fma(s_t[r] * wv, wv, atw);
-            B.W[k * d + j] = wv;
-          } else {
-            B.W[k * d + j] = b;
-          }
-        }
-      }
-    }
-    // the groups' sums, in group order
-    __syncthreads();
-    if (act) {
-      s_red[3 * threadIdx.x] = av;
-      s_red[3 * threadIdx.x + 1] = aw;
-      s_red[3 * threadIdx.x + 2] = atw;
-    }
-    __syncthreads();
-    if (grp == 0 && j < d) {
-      const int gs = span >= 256 ? 256 : span;
-      for (int g = 1; g < G; g++) {
-        const int tt = g * gs + jl;
-        av += s_red[3 * tt];
-        aw += s_red[3 * tt + 1];
-        atw += s_red[3 * tt + 2];
-      }
-      out[j] = av;
-      out[d + j] = aw;
-      out[2 * d + j] = atw;
-    }
-  }
-  s1t = block_sum<256>(s1t, sh);
-  if (threadIdx.x == 0) out[3 * d] = s1t;
+  svec_block(C, B, d, npb, seg, blockIdx.x, kSvecBlocks);
   if (last_block_ticket(&st->ctr_svec)) control_b_body(B, d);
 }
 
@@ -1072,260 +377,23 @@ cudaError_t launch_support_rows(const double* C, Buffers& B, int64_t m, int d, c
   return cudaGetLastError();
 }
 
-// ===========================================================================
-// Certified feasibility pass (Sec. 4.2).  For every ball, e_i = r_i + ||c - c_i||
-// (FP64, by definition) and
-//   mode 0: val_i = e_i - r;  max val (lowest index on ties), list {val_i > eps}
-//   mode 1: val_i = (r - r_i) - ||c - c_i|| (slack);  list {val_i <= eps}
-//   mode 2: the maximum of mode 0 only
-// Sweep A bounds e_i from the shadows (FP32, rigorous) and keeps the block
-// maxima of the lower bounds; sweep B evaluates in FP64 exactly the balls that
-// could be the maximum or whose list membership the bounds do not decide.
-constexpr int kFeasNT = 256;
-
-struct FeasArgs {
-  const double* C; const double* R;
-  int64_t m, m_pad;
-  int d, d4;
-  const float4* X32; const float* R32; const float* E32;
-  const double* c;      // query centre (unscaled)
-  const float* y32;     // trunc32(c - o), 4*d4 floats
-  const float* ynp;     // device: upper bound on ||y32||
-  double r, eps;
-  int mode;
-  int want_max;
-  int all64;            // no bounds: every ball evaluated in FP64 (the plain FP64 pass)
-  float* eub;           // [m] upper bound on e_i
-  float* elb;           // [m] lower bound on e_i
-  float* blb;           // [nb] block max of the lower bounds
-  double* bmax; int64_t* barg; int* bcnt; int64_t* blist;
-  const float* L;       // device: max over blocks of blb
-};
-
-__global__ void __launch_bounds__(kFeasNT) k_feas_a(FeasArgs A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4* s_y = reinterpret_cast<float4*>(smem_raw);
-  __shared__ float s_m[kFeasNT / 32];
-  const float4* y4 = reinterpret_cast<const float4*>(A.y32);
-  for (int g = threadIdx.x; g < A.d4; g += kFeasNT) s_y[g] = y4[g];
-  __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * kFeasNT + threadIdx.x;
-  float lbv = -INFINITY;
-  if (i < A.m) {
-    const float4* xp = A.X32 + i;
-    float S = 0.f, N = 0.f;
-    for (int g = 0; g < A.d4; g++) {
-      const float4 xa = xp[(int64_t)g * A.m_pad];
-      const float4 ya = s_y[g];
-      float t;
-      t = xa.x - ya.x; S = fmaf(t, t, S); N = fmaf(xa.x, xa.x, N);
-      t = xa.y - ya.y; S = fmaf(t, t, S); N = fmaf(xa.y, xa.y, N);
-      t = xa.z - ya.z; S = fmaf(t, t, S); N = fmaf(xa.z, xa.z, N);
-      t = xa.w - ya.w; S = fmaf(t, t, S); N = fmaf(xa.w, xa.w, N);
-    }
-    const int k4 = 4 * A.d4;
-    const float yn = *A.ynp;
-    const float r32 = A.R32[i];   // r32 <= r_i <= r32 (1 + 2^-23)/(1 - 2^-23)
-    const float E = A.E32[i];
-    const float eu = (r32 * (1.0f + 5.0f * kU32) + dist_ub(S, N, yn, E, k4)) * (1.0f + 2.0f * kU32);
-    const float el = (r32 + dist_lb(S, N, yn, E, k4)) * (1.0f - 2.0f * kU32);
-    A.eub[i] = eu;
-    A.elb[i] = el;
-    lbv = el;
-  }
-  float t = lbv;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(MEB_FULLMASK, t, o));
-  if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = t;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float v = s_m[0];
-    for (int k = 1; k < kFeasNT / 32; k++) v = fmaxf(v, s_m[k]);
-    A.blb[blockIdx.x] = v;
-  }
-}
+__global__ void __launch_bounds__(kFeasNT) k_feas_a(FeasArgs A) { feas_a_block(A, blockIdx.x); }
 
 __global__ void k_feas_L(const float* __restrict__ blb, int nb, float* __restrict__ L) {
-  __shared__ float sm[256];
-  float v = -INFINITY;
-  for (int b = threadIdx.x; b < nb; b += 256) v = fmaxf(v, blb[b]);
-  sm[threadIdx.x] = v;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sm[threadIdx.x] = fmaxf(sm[threadIdx.x], sm[threadIdx.x + o]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *L = sm[0];
+  feas_L_body(blb, nb, L);
 }
 
-__global__ void __launch_bounds__(kFeasNT) k_feas_b(FeasArgs A) {
-  extern __shared__ double s_c[];
-  __shared__ int s_list[kFeasNT];
-  __shared__ unsigned char s_in[kFeasNT];     // list membership
-  __shared__ double s_v[kFeasNT];
-  __shared__ int64_t s_i[kFeasNT];
-  __shared__ int s_wc[kFeasNT / 32];
-  for (int j = threadIdx.x; j < A.d; j += kFeasNT) s_c[j] = A.c[j];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int64_t i = (int64_t)blockIdx.x * kFeasNT + tid;
-  const double L = (A.want_max && !A.all64) ? (double)*A.L : INFINITY;
-  // decide from the bounds; 'need' = evaluate in FP64
-  bool need = false;
-  unsigned char in = 0;
-  if (i < A.m && A.all64) {
-    need = true;
-  } else if (i < A.m) {
-    const double eu = (double)A.eub[i], el = (double)A.elb[i];
-    const double ae = isinf(A.eps) ? 0.0 : fabs(A.eps);
-    const double tolr = 4.0 * DBL_EPSILON * (fabs(eu) + fabs(A.r) + ae);
-    if (A.want_max && eu >= L) need = true;
-    if (A.mode == 0) {
-      if (el - A.r > A.eps + tolr) in = 1;
-      else if (!(eu - A.r <= A.eps - tolr)) need = true;
-    } else if (A.mode == 1) {
-      // slack in [r - eu, r - el]
-      if ((A.r - el) <= A.eps - tolr) in = 1;
-      else if (!((A.r - eu) > A.eps + tolr)) need = true;
-    }   // mode 2: maximum only
-  }
-  s_in[tid] = in;
-  const unsigned msk = __ballot_sync(MEB_FULLMASK, need);
-  if (lane == 0) s_wc[w] = __popc(msk);
-  __syncthreads();
-  int off = 0, tot = 0;
-  for (int k = 0; k < kFeasNT / 32; k++) {
-    off += (k < w) ? s_wc[k] : 0;
-    tot += s_wc[k];
-  }
-  if (need) s_list[off + __popc(msk & ((1u << lane) - 1u))] = tid;
-  s_v[tid] = -INFINITY;
-  s_i[tid] = INT64_MAX;
-  __syncthreads();
-  // FP64 rows, warp per ball
-  for (int k = w; k < tot; k += kFeasNT / 32) {
-    const int loc = s_list[k];
-    const int64_t ii = (int64_t)blockIdx.x * kFeasNT + loc;
-    const double* row = A.C + ii * (int64_t)A.d;
-    double acc = 0.0;
-    for (int j = lane; j < A.d; j += 32) {
-      const double t = s_c[j] - row[j];
-      acc = fma(t, t, acc);
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      const double n = sqrt(acc);
-      if (A.mode != 1) {
-        const double val = (A.R[ii] + n) - A.r;
-        s_in[loc] = (A.mode == 0) && (val > A.eps);
-        s_v[loc] = val;
-        s_i[loc] = ii;
-      } else {
-        const double val = (A.r - A.R[ii]) - n;
-        s_in[loc] = val <= A.eps;
-      }
-    }
-  }
-  __syncthreads();
-  // block max (lowest index on ties) among the FP64-evaluated balls
-  for (int o = kFeasNT / 2; o > 0; o >>= 1) {
-    if (tid < o) {
-      const double v2 = s_v[tid + o];
-      const int64_t i2 = s_i[tid + o];
-      if (v2 > s_v[tid] || (v2 == s_v[tid] && i2 < s_i[tid])) { s_v[tid] = v2; s_i[tid] = i2; }
-    }
-    __syncthreads();
-  }
-  // ordered list of members of this tile
-  const bool fl = (i < A.m) && s_in[tid];
-  const unsigned lm = __ballot_sync(MEB_FULLMASK, fl);
-  __syncthreads();
-  if (lane == 0) s_wc[w] = __popc(lm);
-  __syncthreads();
-  int loff = 0, ltot = 0;
-  for (int k = 0; k < kFeasNT / 32; k++) {
-    loff += (k < w) ? s_wc[k] : 0;
-    ltot += s_wc[k];
-  }
-  if (fl) A.blist[(int64_t)blockIdx.x * kFeasNT + loff + __popc(lm & ((1u << lane) - 1u))] = i;
-  if (tid == 0) {
-    A.bmax[blockIdx.x] = s_v[0];
-    A.barg[blockIdx.x] = s_i[0];
-    A.bcnt[blockIdx.x] = ltot;
-  }
-}
+__global__ void __launch_bounds__(kFeasNT) k_feas_b(FeasArgs A) { feas_b_block(A, blockIdx.x); }
 
-// One block: max over blocks (lowest index on ties), total count.
 __global__ void k_feas_final(const double* __restrict__ bmax, const int64_t* __restrict__ barg,
                              const int* __restrict__ bcnt, int nb, double* out_max,
                              int64_t* out_arg, int64_t* out_cnt) {
-  __shared__ double sv[256];
-  __shared__ int64_t si[256];
-  __shared__ long long sc[256];
-  double best = -INFINITY;
-  int64_t bi = INT64_MAX;
-  long long cnt = 0;
-  for (int b = threadIdx.x; b < nb; b += 256) {
-    const double v = bmax[b];
-    const int64_t ix = barg[b];
-    if (v > best || (v == best && ix < bi)) { best = v; bi = ix; }
-    cnt += bcnt[b];
-  }
-  sv[threadIdx.x] = best; si[threadIdx.x] = bi; sc[threadIdx.x] = cnt;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      const double v2 = sv[threadIdx.x + o];
-      const int64_t i2 = si[threadIdx.x + o];
-      if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
-        sv[threadIdx.x] = v2; si[threadIdx.x] = i2;
-      }
-      sc[threadIdx.x] += sc[threadIdx.x + o];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    if (out_max) *out_max = sv[0];
-    if (out_arg) *out_arg = si[0];
-    if (out_cnt) *out_cnt = sc[0];
-  }
+  feas_final_body(bmax, barg, bcnt, nb, out_max, out_arg, out_cnt);
 }
 
-// Ordered gather of per-tile lists (tile t holds cnt[t] entries at t*T).
 __global__ void k_gather_lists(const int* __restrict__ cnt, const int64_t* __restrict__ lists,
                                int nb, int T, int64_t* __restrict__ out, int64_t cap) {
-  __shared__ long long sh[256];
-  const int b0 = blockIdx.x * 256;
-  long long pre = 0;
-  for (int t = threadIdx.x; t < b0; t += 256) pre += cnt[t];
-  sh[threadIdx.x] = pre;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  const long long base = sh[0];
-  __syncthreads();
-  const int t = b0 + threadIdx.x;
-  const long long my = (t < nb) ? cnt[t] : 0;
-  sh[threadIdx.x] = my;
-  __syncthreads();
-  for (int o = 1; o < 256; o <<= 1) {
-    const long long v = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
-    __syncthreads();
-    sh[threadIdx.x] += v;
-    __syncthreads();
-  }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int k = w; k < 256; k += 8) {
-    const int tt = b0 + k;
-    if (tt >= nb) break;
-    const long long n = cnt[tt];
-    const long long st0 = base + sh[k] - n;
-    for (long long e = lane; e < n; e += 32) {
-      const long long pos = st0 + e;
-      if (pos < cap) out[pos] = lists[(int64_t)tt * T + e];
-    }
-  }
+  gather_lists_block(blockIdx.x, cnt, lists, nb, T, out, cap);
 }
 
 // Sum of per-tile counts into *out (one block).
@@ -1342,27 +410,9 @@ __global__ void k_count_sum(const int* __restrict__ cnt, int nb, int64_t* __rest
   if (threadIdx.x == 0) *out = sh[0];
 }
 
-// Query shadow for the feasibility pass: y32 = trunc32(c - o), yn >= ||y32||;
-// a non-finite query centre sets *bad (when given).
 __global__ void k_query_shadow(const double* __restrict__ c, const double* __restrict__ o, int d,
                                float* __restrict__ y32, float* __restrict__ yn, int* bad) {
-  __shared__ double sh[32];
-  const int d4 = (d + 3) / 4;
-  double q = 0.0;
-  int nf = 0;
-  for (int j = threadIdx.x; j < 4 * d4; j += blockDim.x) {
-    float y = 0.0f;
-    if (j < d) {
-      const double cj = c[j];
-      nf |= !isfinite(cj);
-      y = f64_to_f32_trunc(cj - o[j]);
-    }
-    y32[j] = y;
-    q += (double)y * (double)y;
-  }
-  if (__syncthreads_or(nf) && threadIdx.x == 0 && bad) atomicOr(bad, 1);
-  q = block_sum<256>(q, sh);
-  if (threadIdx.x == 0) *yn = __double2float_ru(sqrt(q) * (1.0 + 1e-12));
+  query_shadow_body(c, o, d, y32, yn, bad);
 }
 
 cudaError_t launch_feas_cert(const double* C, const double* R, int64_t m, int d, const double* c,

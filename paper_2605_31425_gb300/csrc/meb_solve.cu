@@ -7,18 +7,9 @@
 // The iterate lives on the scaled problem (data divided by the power of two
 // s); the streaming kernels read the unscaled input.  The controller kernels
 // run on one block; their vector work (length d + 1) is spread over it.
-#include <cuda_runtime.h>
-#include <float.h>
-#include <math.h>
-#include <stdint.h>
-
-#include "meb_control.cuh"
+#include "meb_solve_dev.cuh"
 
 namespace meb {
-
-// ===========================================================================
-// Controller (one block): reduces the pass, forms grad and Psi, and takes the
-// decisions of Algorithms 1 and 2.  Vector work is spread over the block.
 
 cudaError_t launch_tick_control(Buffers& B, int64_t m, int d, cudaStream_t s) {
   // the line-search controller runs in the last block of k_rows64 and the
@@ -26,198 +17,16 @@ cudaError_t launch_tick_control(Buffers& B, int64_t m, int d, cudaStream_t s) {
   return launch_support_rows(B.C_in, B, m, d, s);
 }
 
-// ===========================================================================
-// Dense Newton system (d + 1 <= kMaxDenseN):
-//   H = tau/sigma I + sigma (n_I I + sum_M P_k),
-//   sum_M P_k = 1/2 [[n_M, sum w^T], [sum w, sum(1+t) I - sum t w w^T]].
-// k_syrk: partial tiles of sum_M t_k w_k w_k^T over row groups.
-constexpr int kSyrkGroups = 24;
-
 __global__ void __launch_bounds__(256) k_syrk(Buffers B, int d, int force) {
   pdl_wait_and_release();
-  DevState* st = B.st;
-  if (!force && (st->status != 0 || st->action != ACT_NEWTON)) return;
-  const int nt = (d + kSyrkTile - 1) / kSyrkTile;
-  const int ntri = nt * (nt + 1) / 2;
-  const int tri = blockIdx.x, grp = blockIdx.y;
-  if (tri >= ntri) return;
-  // tile (ti >= tj) from the linear lower-triangle index
-  int ti = 0;
-  while ((ti + 1) * (ti + 2) / 2 <= tri) ti++;
-  const int tj = tri - ti * (ti + 1) / 2;
-  const int nS = st->nS;
-  const int rpg = (nS + kSyrkGroups - 1) / kSyrkGroups;
-  const int k0 = grp * rpg, k1 = min(nS, k0 + rpg);
-  __shared__ double sa[kSyrkRows][kSyrkTile + 1];
-  __shared__ double sb[kSyrkRows][kSyrkTile + 1];
-  __shared__ double stw[kSyrkRows];
-  // thread -> 4 outputs: rows (ty*4 .. ty*4+3)? use (r = tid/32 + 8q, c = tid%32)
-  const int cc = threadIdx.x & 31, r0 = threadIdx.x >> 5;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int kb = k0; kb < k1; kb += kSyrkRows) {
-    const int nr = min(kSyrkRows, k1 - kb);
-    for (int e = threadIdx.x; e < kSyrkRows * kSyrkTile; e += 256) {
-      const int rr = e / kSyrkTile, c2 = e % kSyrkTile;
-      double va = 0.0, vb = 0.0;
-      if (rr < nr) {
-        const int k = kb + rr;
-        const int ja = ti * kSyrkTile + c2, jb = tj * kSyrkTile + c2;
-        const bool m = B.S_case[k] == CASE_M;
-        if (m && ja < d) va = B.W[(int64_t)k * d + ja];
-        if (m && jb < d) vb = B.W[(int64_t)k * d + jb];
-      }
-      sa[rr][c2] = va;
-      sb[rr][c2] = vb;
-    }
-    if (threadIdx.x < kSyrkRows) {
-      const int k = kb + threadIdx.x;
-      stw[threadIdx.x] = (threadIdx.x < nr && B.S_case[k] == CASE_M) ? B.S_t[k] : 0.0;
-    }
-    __syncthreads();
-    for (int rr = 0; rr < nr; rr++) {
-      const double t = stw[rr];
-      const double bv = sb[rr][cc] * t;
-#pragma unroll
-      for (int q = 0; q < 4; q++) acc[q] = fma(sa[rr][r0 + 8 * q], bv, acc[q]);
-    }
-    __syncthreads();
-  }
-  double* out = B.hpart + ((int64_t)grp * ntri + tri) * (kSyrkTile * kSyrkTile);
-#pragma unroll
-  for (int q = 0; q < 4; q++) out[(r0 + 8 * q) * kSyrkTile + cc] = acc[q];
+  if (!force && !newton_gate(B.st)) return;
+  syrk_block(B, d, blockIdx.x, blockIdx.y);
 }
 
-// Sum the group partials (in group order) into B.H's lower triangle block (rows/cols 1..d).
 __global__ void k_syrk_reduce(Buffers B, int d, int force) {
   pdl_wait_and_release();
-  DevState* st = B.st;
-  if (!force && (st->status != 0 || st->action != ACT_NEWTON)) return;
-  // H = tau/sigma I + sigma (n_I I + 1/2 [[n_M, sum w^T], [sum w, sum(1+t) I - SY]]),
-  // SY = sum_M t w w^T from the group partials (summed in group order)
-  const DevVecs& V = B.vec;
-  const int nt = (d + kSyrkTile - 1) / kSyrkTile;
-  const int ntri = nt * (nt + 1) / 2;
-  const int n1 = d + 1;
-  const double sigma = st->sigma, tos = st->tos;
-  const double nI = st->last[P_NI], nM = st->last[P_NM], s1t = V.st1[0];
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)n1 * n1;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / n1), l = (int)(e % n1);
-    if (l > i) continue;   // the thread of (i, l) writes (i, l) and (l, i)
-    double h;
-    if (i == 0) {
-      h = tos + sigma * (nI + 0.5 * nM);
-    } else if (l == 0) {
-      h = sigma * 0.5 * V.sw[i - 1];
-    } else {
-      const int j = i - 1, k = l - 1;   // k <= j
-      const int ti = j / kSyrkTile, tj = k / kSyrkTile;
-      const int tri = ti * (ti + 1) / 2 + tj;
-      const int loc = (j % kSyrkTile) * kSyrkTile + (k % kSyrkTile);
-      double sy = 0.0;
-      for (int g = 0; g < kSyrkGroups; g++)
-        sy += B.hpart[((int64_t)g * ntri + tri) * (kSyrkTile * kSyrkTile) + loc];
-      h = -0.5 * sigma * sy;
-      if (i == l) h += tos + sigma * (nI + 0.5 * s1t);
-    }
-    B.H[(int64_t)i * n1 + l] = h;
-    B.H[(int64_t)l * n1 + i] = h;
-    // the FP32 pair hi + lo = h to 2^-48 relative (Gauss-Jordan and its
-    // double-float residual)
-    const float hi = __double2float_rn(h);
-    const float lo = __double2float_rn(h - (double)hi);
-    B.Hhi[(int64_t)i * n1 + l] = hi;
-    B.Hhi[(int64_t)l * n1 + i] = hi;
-    B.Hlo[(int64_t)i * n1 + l] = lo;
-    B.Hlo[(int64_t)l * n1 + i] = lo;
-  }
-}
-
-// One block: assemble H (packed lower, smem), Cholesky, solve H dx = -g,
-// then set the first line-search trial x + dx.
-// FP64 Cholesky solve of H dx = -g by one block of 256 threads, with Lp
-// (n(n+1)/2 doubles, packed lower: row i at i(i+1)/2) in shared memory.
-__device__ void newton_chol_body(const Buffers& B, int d, double* Lp) {
-  DevState* st = B.st;
-  __shared__ double sh[32];
-  __shared__ int s_fail;
-  const DevVecs& V = B.vec;
-  const int n = d + 1;
-  const double sigma = st->sigma, tos = st->tos;
-  const double nI = st->last[P_NI], nM = st->last[P_NM];
-  const double s1t = V.st1[0];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  (void)tos; (void)nI; (void)nM; (void)s1t;
-  for (int i = wid; i < n; i += 8) {
-    const int64_t ri = (int64_t)i * (i + 1) / 2;
-    for (int l = lane; l <= i; l += 32) Lp[ri + l] = B.H[(int64_t)i * n + l];   // assembled H
-  }
-  if (threadIdx.x == 0) s_fail = 0;
-  __syncthreads();
-  // right-looking Cholesky on the packed lower triangle
-  for (int j = 0; j < n; j++) {
-    const int64_t jj = (int64_t)j * (j + 1) / 2 + j;
-    if (threadIdx.x == 0) {
-      const double p = Lp[jj];
-      if (!(p > 0.0)) s_fail = 1;
-      Lp[jj] = sqrt(fmax(p, DBL_MIN));
-    }
-    __syncthreads();
-    if (s_fail) break;
-    const double ljj = Lp[jj];
-    for (int i = j + 1 + threadIdx.x; i < n; i += 256) Lp[(int64_t)i * (i + 1) / 2 + j] /= ljj;
-    __syncthreads();
-    // trailing update: rows i > j, cols j < l <= i (warp per row)
-    for (int i = j + 1 + wid; i < n; i += 8) {
-      const int64_t ri = (int64_t)i * (i + 1) / 2;
-      const double lij = Lp[ri + j];
-      for (int l = j + 1 + lane; l <= i; l += 32)
-        Lp[ri + l] -= lij * Lp[(int64_t)l * (l + 1) / 2 + j];
-    }
-    __syncthreads();
-  }
-  if (s_fail) {
-    // Cholesky broke down: end the inner loop here (outer update at x)
-    if (threadIdx.x == 0) st->chol_fail += 1;
-    do_outer(st, V, d, sh);
-    return;
-  }
-  // forward / backward substitution (single warp; n <= 225)
-  double* y = V.dx;
-  if (threadIdx.x < 32) {
-    for (int i = 0; i < n; i++) {
-      const int64_t ri = (int64_t)i * (i + 1) / 2;
-      double t = 0.0;
-      for (int k = threadIdx.x; k < i; k += 32) t += Lp[ri + k] * y[k];
-      t = warp_sum(t);
-      if (threadIdx.x == 0) y[i] = (-V.g[i] - t) / Lp[ri + i];
-      __syncwarp();
-    }
-    for (int i = n - 1; i >= 0; i--) {
-      double t = 0.0;
-      for (int k = i + 1 + threadIdx.x; k < n; k += 32) t += Lp[(int64_t)k * (k + 1) / 2 + i] * y[k];
-      t = warp_sum(t);
-      if (threadIdx.x == 0) y[i] = (y[i] - t) / Lp[(int64_t)i * (i + 1) / 2 + i];
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  double gd = 0.0;
-  for (int k = threadIdx.x; k < n; k += 256) {
-    gd += V.g[k] * V.dx[k];
-    V.xt[k] = V.x[k] + V.dx[k];
-  }
-  gd = block_sum<256>(gd, sh);
-  if (threadIdx.x == 0) {
-    st->fp64_solves += 1;
-    st->gdx = gd;
-    st->eta = 1.0;
-    st->phase = 1;
-    st->bt = 0;
-    st->action = ACT_TRIAL;
-  }
-  __syncthreads();
-  set_trial(st, V, d, sh);
+  if (!force && !newton_gate(B.st)) return;
+  syrk_reduce_block(B, d, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(256) k_newton_chol(Buffers B, int d) {
@@ -228,379 +37,16 @@ __global__ void __launch_bounds__(256) k_newton_chol(Buffers B, int d) {
   newton_chol_body(B, d, Lp);
 }
 
-// The Newton direction dx (in shared memory) becomes the first line-search
-// trial: dx, gdx = g.dx, xt = x + dx and the trial's query shadow.
-__device__ void newton_accept(DevState* st, const DevVecs& V, int d, const double* s_x,
-                              double* sh) {
-  const int n = d + 1;
-  double gd = 0.0;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    V.dx[k] = s_x[k];
-    gd += V.g[k] * s_x[k];
-    V.xt[k] = V.x[k] + s_x[k];
-  }
-  gd = block_sum<256>(gd, sh);
-  if (threadIdx.x == 0) {
-    st->need_fp64_solve = 0;
-    st->gdx = gd;
-    st->eta = 1.0;
-    st->phase = 1;
-    st->bt = 0;
-    st->action = ACT_TRIAL;
-  }
-  __syncthreads();
-  set_trial(st, V, d, sh);
-}
-
-// One block: FP32 Gauss-Jordan inverse of H (SPD, no pivoting needed), then
-// dx = -H^{-1} g refined in FP64: r = -g - H dx (FP64), dx += H32^{-1} r.
-// Sets need_fp64_solve when a pivot is not positive or the refinement does
-// not converge; otherwise sets up the first line-search trial.
 __global__ void __launch_bounds__(256) k_newton_gj(Buffers B, int d) {
   pdl_wait_and_release();
-  DevState* st = B.st;
-  if (st->status != 0 || st->action != ACT_NEWTON) return;
-  if (st->force_fp64_solve) {   // k_newton_chol follows
-    if (threadIdx.x == 0) st->need_fp64_solve = 1;
-    return;
-  }
-  extern __shared__ float A[];    // n x n, row-major
-  __shared__ double sh[32];
-  __shared__ int s_fail;
-  __shared__ float s_prow[kMaxDenseN];
-  __shared__ float s_rf[kMaxDenseN];
-  const DevVecs& V = B.vec;
-  const int n = d + 1;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int e = tid; e < n * n; e += 256) A[e] = (float)B.H[e];
-  if (tid == 0) s_fail = 0;
-  __syncthreads();
-  for (int k = 0; k < n; k++) {
-    const float p = A[k * n + k];
-    if (!(p > 0.0f) || !isfinite(p)) { if (tid == 0) s_fail = 1; }
-    __syncthreads();
-    if (s_fail) break;
-    const float ip = 1.0f / p;
-    for (int j = tid; j < n; j += 256) {
-      const float v = (j == k) ? ip : A[k * n + j] * ip;
-      s_prow[j] = v;
-    }
-    __syncthreads();
-    for (int j = tid; j < n; j += 256) A[k * n + j] = s_prow[j];
-    // rows i != k: A[i][j] -= A[i][k] * prow[j]; A[i][k] = -A[i][k] * ip
-    for (int i = wid; i < n; i += 8) {
-      if (i == k) continue;
-      const float f = A[i * n + k];
-      __syncwarp();
-      for (int j = lane; j < n; j += 32) {
-        if (j == k) continue;
-        A[i * n + j] = fmaf(-f, s_prow[j], A[i * n + j]);
-      }
-      __syncwarp();
-      if (lane == 0) A[i * n + k] = -f * ip;
-    }
-    __syncthreads();
-  }
-  bool ok = !s_fail;
-  if (ok) {
-    // dx = A (-g), then refinement: r = -g - H dx (FP64), dx += A r (FP32).
-    // Thread i owns component i; A and H are read by columns (H symmetric,
-    // A ~ H^{-1} symmetric up to rounding), which coalesces.
-    double* x = V.dx;
-    for (int i = tid; i < n; i += 256) s_rf[i] = (float)(-V.g[i]);
-    __syncthreads();
-    double rn0 = 0.0;
-    for (int it = 0; it < 5; it++) {
-      double dn = 0.0, xn = 0.0;
-      for (int i = tid; i < n; i += 256) {
-        float t = 0.0f;
-        for (int j = 0; j < n; j++) t = fmaf(A[j * n + i], s_rf[j], t);
-        const double xi = (it == 0 ? 0.0 : x[i]) + (double)t;
-        x[i] = xi;
-        dn += (double)t * (double)t;
-        xn += xi * xi;
-      }
-      dn = block_sum<256>(dn, sh);
-      xn = block_sum<256>(xn, sh);
-      if (dn <= 1e-22 * xn) break;
-      double rn = 0.0;
-      for (int i = tid; i < n; i += 256) {
-        double t = -V.g[i];
-        for (int j = 0; j < n; j++) t = fma(-B.H[(int64_t)j * n + i], x[j], t);
-        s_rf[i] = (float)t;
-        rn += t * t;
-      }
-      rn = block_sum<256>(rn, sh);
-      if (it == 0) rn0 = rn;
-      else if (!(rn <= rn0)) { ok = false; break; }   // refinement diverges
-      if (it == 4) ok = rn <= 1e-16 * rn0;
-    }
-  }
-  if (tid == 0) st->gj_inverses += 1;
-  if (!ok) {
-    if (tid == 0) st->need_fp64_solve = 1;
-    return;
-  }
-  double gd = 0.0;
-  for (int k = tid; k < n; k += 256) {
-    gd += V.g[k] * V.dx[k];
-    V.xt[k] = V.x[k] + V.dx[k];
-  }
-  gd = block_sum<256>(gd, sh);
-  if (tid == 0) {
-    st->need_fp64_solve = 0;
-    st->gdx = gd;
-    st->eta = 1.0;
-    st->phase = 1;
-    st->bt = 0;
-    st->action = ACT_TRIAL;
-  }
-  __syncthreads();
-  set_trial(st, V, d, sh);
-}
-
-// Register-blocked variant for n = d + 1 <= 112, on a 16 x 16 thread grid:
-// thread (ty, tx) holds rows ty + 16 i and columns tx + 16 j (i, j < 7) of the
-// matrix in registers, as column pairs for packed FP32x2 arithmetic.  Each
-// Gauss-Jordan pivot publishes the old pivot row and column through shared
-// memory (double-buffered: one barrier per pivot) and updates every entry.
-// H is SPD: no pivoting.
-//
-// FP64 instructions are few on this GPU's FP64 pipe, so the refinement runs
-// in double-float arithmetic: dx = A (-g) is refined with the residual
-// r = -g - H dx, where H = Hhi + Hlo, dx = xh + xl and -g = bh + bl are FP32
-// pairs, products are split exactly with fmaf and sums taken by TwoSum
-// (about 2^-48 relative).
-constexpr int kGjTile = 7;
-constexpr int kGjRegN = 16 * kGjTile;
-
-// exact a + b = s + e (Knuth's TwoSum)
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-// s + l += (hh + hl)(xh + xl), dropping hl xl (2^-48 relative)
-__device__ __forceinline__ void df_mac(float hh, float hl, float xh, float xl, float& s,
-                                       float& l) {
-  const float p = hh * xh;
-  const float e = fmaf(hh, xh, -p);   // exact rounding error of p
-  const float c = fmaf(hh, xl, fmaf(hl, xh, e));
-  float t, err;
-  two_sum(s, p, t, err);
-  s = t;
-  l += err + c;
-}
-
-// block-wide FP32 sums of two values in a fixed order (every thread gets them)
-__device__ __forceinline__ float2 block_sum2f(float a, float b, float2* sh8) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(MEB_FULLMASK, a, o);
-    b += __shfl_xor_sync(MEB_FULLMASK, b, o);
-  }
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) sh8[threadIdx.x >> 5] = make_float2(a, b);
-  __syncthreads();
-  float2 t = sh8[0];
-#pragma unroll
-  for (int k = 1; k < 8; k++) { t.x += sh8[k].x; t.y += sh8[k].y; }
-  return t;
+  if (!newton_gate(B.st)) return;
+  newton_gj_body(B, d);
 }
 
 __global__ void __launch_bounds__(256, 1) k_newton_gj_reg(Buffers B, int d) {
   pdl_wait_and_release();
-  DevState* st = B.st;
-  if (st->status != 0 || st->action != ACT_NEWTON) return;
-  extern __shared__ double dyn_Lp[];   // the Cholesky fallback's factor
-  if (st->force_fp64_solve) {
-    newton_chol_body(B, d, dyn_Lp);
-    return;
-  }
-  __shared__ float s_row[2][kGjRegN], s_col[2][kGjRegN];
-  __shared__ float s_b[kGjRegN], s_bh[kGjRegN], s_bl[kGjRegN], s_xh[kGjRegN], s_xl[kGjRegN];
-  __shared__ float2 s_red[8];
-  __shared__ double sh[32];
-  __shared__ double s_x[kGjRegN];
-  const DevVecs& V = B.vec;
-  const int n = d + 1;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  // a[i][q] = (A[ty+16i][tx+32q], A[ty+16i][tx+32q+16]); column tx+112 is a zero dummy
-  float2 a[kGjTile][4];
-#pragma unroll
-  for (int i = 0; i < kGjTile; i++)
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-      const int row = ty + 16 * i, col = tx + 16 * j;
-      const float v = (j == 7) ? 0.0f
-                               : (row < n && col < n) ? B.Hhi[(int64_t)row * n + col]
-                                                      : (row == col ? 1.0f : 0.0f);
-      if (j & 1) a[i][j >> 1].y = v; else a[i][j >> 1].x = v;
-    }
-  for (int i = tid; i < kGjRegN; i += 256) {
-    const double b = (i < n) ? -V.g[i] : 0.0;   // solve H dx = -g
-    const float bh = __double2float_rn(b);
-    s_bh[i] = bh;
-    s_bl[i] = __double2float_rn(b - (double)bh);
-    s_b[i] = bh;
-    s_xh[i] = 0.0f;
-    s_xl[i] = 0.0f;
-  }
-  bool ok = true;
-#pragma unroll
-  for (int kb = 0; kb < kGjTile; kb++) {
-    for (int kk = 0; kk < 16; kk++) {
-      const int k = 16 * kb + kk;
-      if (k < n && ok) {
-        const int bf = k & 1;
-        if (ty == kk) {
-#pragma unroll
-          for (int j = 0; j < kGjTile; j++)
-            s_row[bf][tx + 16 * j] = (j & 1) ? a[kb][j >> 1].y : a[kb][j >> 1].x;
-        }
-        if (tx == kk) {
-#pragma unroll
-          for (int i = 0; i < kGjTile; i++)
-            s_col[bf][ty + 16 * i] = (kb & 1) ? a[i][kb >> 1].y : a[i][kb >> 1].x;
-        }
-        __syncthreads();
-        const float p = s_row[bf][k];
-        ok = (p > 0.0f) && isfinite(p);   // the same for every thread
-        const float ip = __fdividef(1.0f, p);
-        float2 rc[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const float lo = s_row[bf][tx + 32 * q];
-          const float hi = (q < 3) ? s_row[bf][tx + 32 * q + 16] : 0.0f;
-          rc[q] = __fmul2_rn(make_float2(lo, hi), make_float2(ip, ip));
-        }
-        float cr[kGjTile];
-#pragma unroll
-        for (int i = 0; i < kGjTile; i++) cr[i] = s_col[bf][ty + 16 * i];
-#pragma unroll
-        for (int i = 0; i < kGjTile; i++)
-#pragma unroll
-          for (int q = 0; q < 4; q++)
-            a[i][q] = __ffma2_rn(make_float2(-cr[i], -cr[i]), rc[q], a[i][q]);
-        if (ty == kk) {   // pivot row: A[k][j] / p, and 1/p on the diagonal
-#pragma unroll
-          for (int j = 0; j < kGjTile; j++) {
-            const float rj = (j & 1) ? rc[j >> 1].y : rc[j >> 1].x;
-            const float v = (tx + 16 * j == k) ? ip : rj;
-            if (j & 1) a[kb][j >> 1].y = v; else a[kb][j >> 1].x = v;
-          }
-        }
-        if (tx == kk) {   // pivot column: -A[i][k] / p off the diagonal
-#pragma unroll
-          for (int i = 0; i < kGjTile; i++) {
-            if (ty + 16 * i != k) {
-              const float v = -cr[i] * ip;
-              if (kb & 1) a[i][kb >> 1].y = v; else a[i][kb >> 1].x = v;
-            }
-          }
-        }
-      }
-    }
-  }
-  __syncthreads();
-  if (ok) {
-    // x0 = A (-g) and at most two corrections dx += A r: the Newton direction
-    // needs a small relative error, not FP64 accuracy (the stop test, Armijo
-    // and KKT use the FP64 gradient and Psi)
-    float rn0 = 0.0f;
-    for (int it = 0; it < 3; it++) {
-      // t = A s_b : partial rows over this thread's columns, reduced over tx
-      float tv[kGjTile];
-#pragma unroll
-      for (int i = 0; i < kGjTile; i++) {
-        float2 t2 = make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const float lo = s_b[tx + 32 * q];
-          const float hi = (q < 3) ? s_b[tx + 32 * q + 16] : 0.0f;
-          t2 = __ffma2_rn(a[i][q], make_float2(lo, hi), t2);
-        }
-        tv[i] = t2.x + t2.y;
-      }
-#pragma unroll
-      for (int o = 8; o > 0; o >>= 1)
-#pragma unroll
-        for (int i = 0; i < kGjTile; i++) tv[i] += __shfl_xor_sync(MEB_FULLMASK, tv[i], o);
-      float dn = 0.0f, xn = 0.0f;
-      if (tx == 0) {
-#pragma unroll
-        for (int i = 0; i < kGjTile; i++) {
-          const int row = ty + 16 * i;
-          if (row < n) {
-            float h, e;
-            two_sum(s_xh[row], tv[i], h, e);
-            const float l = s_xl[row] + e;
-            const float h2 = h + l;               // renormalise the pair
-            s_xl[row] = l - (h2 - h);
-            s_xh[row] = h2;
-            dn = fmaf(tv[i], tv[i], dn);
-            xn = fmaf(h2, h2, xn);
-          }
-        }
-      }
-      const float2 dx2 = block_sum2f(dn, xn, s_red);   // (barriers: s_xh, s_xl visible)
-      if (dx2.x <= 1e-16f * dx2.y || it == 2) break;
-      // r = -g - H x in double-float, rows reduced over tx
-      float sa[kGjTile], la[kGjTile];
-#pragma unroll
-      for (int i = 0; i < kGjTile; i++) {
-        const int row = ty + 16 * i;
-        sa[i] = 0.0f;
-        la[i] = 0.0f;
-#pragma unroll
-        for (int j = 0; j < kGjTile; j++) {
-          const int col = tx + 16 * j;
-          if (row < n && col < n)
-            df_mac(B.Hhi[(int64_t)row * n + col], B.Hlo[(int64_t)row * n + col], s_xh[col],
-                   s_xl[col], sa[i], la[i]);
-        }
-      }
-#pragma unroll
-      for (int o = 8; o > 0; o >>= 1)
-#pragma unroll
-        for (int i = 0; i < kGjTile; i++) {
-          const float so = __shfl_xor_sync(MEB_FULLMASK, sa[i], o);
-          const float lo = __shfl_xor_sync(MEB_FULLMASK, la[i], o);
-          float t, err;
-          two_sum(sa[i], so, t, err);
-          sa[i] = t;
-          la[i] += lo + err;
-        }
-      float rn = 0.0f;
-      if (tx == 0) {
-#pragma unroll
-        for (int i = 0; i < kGjTile; i++) {
-          const int row = ty + 16 * i;
-          if (row < n) {
-            float h, e;
-            two_sum(s_bh[row], -sa[i], h, e);   // exact leading difference
-            const float r = h + ((e + s_bl[row]) - la[i]);
-            s_b[row] = r;
-            rn = fmaf(r, r, rn);
-          }
-        }
-      }
-      const float rr = block_sum2f(rn, 0.0f, s_red).x;   // (barriers: s_b visible)
-      if (it == 0) rn0 = rr;
-      else if (!(rr <= 0.25f * rn0)) { ok = false; break; }   // not contracting
-    }
-  }
-  if (tid == 0) st->gj_inverses += 1;
-  if (!ok) {
-    // the FP64 Cholesky in the same launch (dynamic shared memory n(n+1)/2 doubles)
-    __syncthreads();
-    newton_chol_body(B, d, dyn_Lp);
-    return;
-  }
-  for (int i = tid; i < kGjRegN; i += 256) s_x[i] = (double)s_xh[i] + (double)s_xl[i];
-  __syncthreads();
-  newton_accept(st, V, d, s_x, sh);
+  if (!newton_gate(B.st)) return;
+  newton_gj_reg_body(B, d);
 }
 
 // Launches per Newton step of the dense path: SYRK, its reduction and the
@@ -648,163 +94,32 @@ cudaError_t launch_newton_dense(Buffers& B, int d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// ===========================================================================
-// Matrix-free Newton system (Sec. 4.1): CG with the Jacobi preconditioner,
-//   Hq = tau/sigma q + sigma (n_I q + sum_M P_k q),
-//   P_k q = 1/2 (q0 + w.q1 ; q0 w + (1+t) q1 - t w (w.q1)).
-// k_hvp_dot: wq_k = w_k . q1 (warp per row); k_hvp_acc: -1/2 sum_k t_k wq_k w_k
-// and 1/2 sum_k wq_k; hvp_finish adds the terms in q0 sum w and sum(1+t) q1.
 __global__ void __launch_bounds__(256) k_hvp_dot(Buffers B, int d, const double* __restrict__ q,
                                                   double* __restrict__ wq, int force) {
-  DevState* st = B.st;
-  if (!force && (st->status != 0 || st->action != ACT_NEWTON || st->cg_done)) return;
-  const int nS = st->nS;
-  const int lane = threadIdx.x & 31;
-  for (int k = (blockIdx.x * 256 + threadIdx.x) >> 5; k < nS; k += (gridDim.x * 256) >> 5) {
-    double t = 0.0;
-    if (B.S_case[k] == CASE_M) {
-      const double* w = B.W + (int64_t)k * d;
-      for (int j = lane; j < d; j += 32) t = fma(w[j], q[1 + j], t);
-      t = warp_sum(t);
-    }
-    if (lane == 0) wq[k] = t;
-  }
+  if (!force && !cg_gate(B.st)) return;
+  hvp_dot_block(B, d, q, wq, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(256) k_hvp_acc(Buffers B, int d, const double* __restrict__ q,
                                                   const double* __restrict__ wq,
                                                   double* __restrict__ part, int force) {
-  DevState* st = B.st;
-  if (!force && (st->status != 0 || st->action != ACT_NEWTON || st->cg_done)) return;
-  const int nS = st->nS;
-  const int rpb = (nS + gridDim.x - 1) / gridDim.x;
-  const int k0 = blockIdx.x * rpb, k1 = min(nS, k0 + rpb);
-  double* out = part + (int64_t)blockIdx.x * (d + 1);
-  double s0 = 0.0;
-  for (int j0 = 0; j0 < d; j0 += 256) {
-    const int j = j0 + threadIdx.x;
-    double acc = 0.0;
-    for (int k = k0; k < k1; k++) {
-      if (B.S_case[k] != CASE_M) continue;
-      const double coef = -0.5 * B.S_t[k] * wq[k];   // the q0 w part is 1/2 q0 sum w
-      if (j < d) acc = fma(coef, B.W[(int64_t)k * d + j], acc);
-      if (j0 == 0 && threadIdx.x == 0) s0 += 0.5 * wq[k];
-    }
-    if (j < d) out[1 + j] = acc;
-  }
-  if (threadIdx.x == 0) out[0] = s0;
+  if (!force && !cg_gate(B.st)) return;
+  hvp_acc_block(B, d, q, wq, part, blockIdx.x, gridDim.x);
 }
-
-// y = tau/sigma q + sigma (n_I q + 1/2 [n_M q0 + S0 ; q0 sum w + sum(1+t) q1] + acc)
-__device__ void hvp_finish(DevState* st, const DevVecs& V, int d, const double* q,
-                           const double* part, int nblk, double* y) {
-  const int n1 = d + 1;
-  const double sigma = st->sigma, tos = st->tos;
-  const double nI = st->last[P_NI], nM = st->last[P_NM], s1t = V.st1[0];
-  for (int k = threadIdx.x; k < n1; k += blockDim.x) {
-    double a = 0.0;
-    for (int b = 0; b < nblk; b++) a += part[(int64_t)b * n1 + k];
-    double pk;
-    if (k == 0) pk = nI * q[0] + 0.5 * nM * q[0] + a;
-    else pk = nI * q[k] + 0.5 * q[0] * V.sw[k - 1] + 0.5 * s1t * q[k] + a;
-    y[k] = tos * q[k] + sigma * pk;
-  }
-}
-
-constexpr int kHvpBlocks = 152;
 
 __global__ void __launch_bounds__(256) k_cg_setup(Buffers B, int d) {
-  DevState* st = B.st;
-  if (st->status != 0 || st->action != ACT_NEWTON) return;
-  __shared__ double sh[32];
-  const DevVecs& V = B.vec;
-  const int n1 = d + 1;
-  const double sigma = st->sigma, tos = st->tos;
-  const double nI = st->last[P_NI], nM = st->last[P_NM], s1t = V.st1[0];
-  double rz = 0.0, bn = 0.0;
-  for (int k = threadIdx.x; k < n1; k += 256) {
-    // diag(H): k = 0: tos + sigma (nI + nM/2); k > 0: tos + sigma (nI + (s1t - sum t w_k^2)/2)
-    const double dg = (k == 0) ? tos + sigma * (nI + 0.5 * nM)
-                               : tos + sigma * (nI + 0.5 * (s1t - V.cg_diag[k]));
-    V.cg_diag[k] = dg;   // overwrite in place (k > 0 held sum t w^2)
-    const double r = -V.g[k];
-    V.cg_r[k] = r;
-    V.dx[k] = 0.0;
-    const double z = r / dg;
-    V.cg_z[k] = z;
-    V.cg_p[k] = z;
-    rz += r * z;
-    bn += r * r;
-  }
-  rz = block_sum<256>(rz, sh);
-  bn = block_sum<256>(bn, sh);
-  if (threadIdx.x == 0) {
-    st->cg_rz = rz;
-    st->cg_bn = sqrt(bn);
-    double gn = sqrt(bn);
-    st->cg_rtol = gn < 0.01 ? sqrt(gn) : 0.1;
-    st->cg_it = 0;
-    st->cg_done = (bn == 0.0);
-  }
+  if (!newton_gate(B.st)) return;
+  cg_setup_body(B, d);
 }
 
-// One CG iteration after the HVP partials of p are in place.
 __global__ void __launch_bounds__(256) k_cg_update(Buffers B, int d, int nblk) {
-  DevState* st = B.st;
-  if (st->status != 0 || st->action != ACT_NEWTON || st->cg_done) return;
-  __shared__ double sh[32];
-  const DevVecs& V = B.vec;
-  const int n1 = d + 1;
-  hvp_finish(st, V, d, V.cg_p, B.hpart, nblk, V.cg_ap);
-  __syncthreads();
-  double pap = 0.0;
-  for (int k = threadIdx.x; k < n1; k += 256) pap += V.cg_p[k] * V.cg_ap[k];
-  pap = block_sum<256>(pap, sh);
-  const double alpha = st->cg_rz / pap;
-  double rr = 0.0, rz1 = 0.0;
-  for (int k = threadIdx.x; k < n1; k += 256) {
-    V.dx[k] += alpha * V.cg_p[k];
-    const double r = V.cg_r[k] - alpha * V.cg_ap[k];
-    V.cg_r[k] = r;
-    const double z = r / V.cg_diag[k];
-    V.cg_z[k] = z;
-    rr += r * r;
-    rz1 += r * z;
-  }
-  rr = block_sum<256>(rr, sh);
-  rz1 = block_sum<256>(rz1, sh);
-  const double beta = rz1 / st->cg_rz;
-  for (int k = threadIdx.x; k < n1; k += 256) V.cg_p[k] = V.cg_z[k] + beta * V.cg_p[k];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    st->cg_rz = rz1;
-    st->cg_it += 1;
-    st->tot_cg += 1;
-    if (sqrt(rr) <= st->cg_rtol * st->cg_bn || st->cg_it >= st->max_cg) st->cg_done = 1;
-  }
+  if (!cg_gate(B.st)) return;
+  cg_update_body(B, d, nblk);
 }
 
 __global__ void __launch_bounds__(256) k_cg_finish(Buffers B, int d) {
-  DevState* st = B.st;
-  if (st->status != 0 || st->action != ACT_NEWTON) return;
-  __shared__ double sh[32];
-  const DevVecs& V = B.vec;
-  const int n1 = d + 1;
-  double gd = 0.0;
-  for (int k = threadIdx.x; k < n1; k += 256) {
-    gd += V.g[k] * V.dx[k];
-    V.xt[k] = V.x[k] + V.dx[k];
-  }
-  gd = block_sum<256>(gd, sh);
-  if (threadIdx.x == 0) {
-    st->gdx = gd;
-    st->eta = 1.0;
-    st->phase = 1;
-    st->bt = 0;
-    st->action = ACT_TRIAL;
-  }
-  __syncthreads();
-  set_trial(st, V, d, sh);
+  if (!newton_gate(B.st)) return;
+  cg_finish_body(B, d);
 }
 
 cudaError_t launch_cg_setup(Buffers& B, int d, cudaStream_t s) {
@@ -827,52 +142,14 @@ cudaError_t launch_cg_finish(Buffers& B, int d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// ===========================================================================
-// Multiplier update (Algorithm 1): (u, v)^{k+1} = sigma_k Pi(z_k) on the
-// support of the accepted point, written to the other buffer, with the
-// ball->slot map; the last block flips the buffer parity.
 __global__ void __launch_bounds__(256) k_mult_rows(const double* __restrict__ C, Buffers B,
                                                    int d) {
   pdl_wait_and_release();
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_OUTER) return;
-  const int nS = st->nS;
-  const int cur = st->sup_cur, nxt = cur ^ 1, nsup = st->nsup;
-  const int* sidx = B.sup_idx[cur];
-  const double* sv = B.sup_v[cur];
-  double* nv = B.sup_v[nxt];
-  const double sigma = st->sigma_prev;   // sigma_k of the finished outer step
-  const double inv_sigma = 1.0 / sigma;
-  const double inv_s = st->inv_s;
-  const double* ct = B.vec.ct;        // == s * x (the accepted point)
-  const int lane = threadIdx.x & 31;
-  for (int k = (blockIdx.x * 256 + threadIdx.x) >> 5; k < nS; k += (gridDim.x * 256) >> 5) {
-    const int idx = B.S_idx[k];
-    const int sl0 = B.slot[idx];
-    const int sl = ((unsigned)sl0 < (unsigned)nsup && sidx[sl0] == idx) ? sl0 : -1;
-    const double a = B.S_a[k], n = B.S_n[k];
-    const double f = (B.S_case[k] == CASE_I) ? 1.0 : 0.5 * (a + n) / n;
-    for (int j = lane; j < d; j += 32) {
-      double b = (C[(int64_t)idx * d + j] - ct[j]) * inv_s;
-      if (sl >= 0) b = fma(sv[(int64_t)sl * d + j], inv_sigma, b);
-      nv[(int64_t)k * d + j] = sigma * f * b;
-    }
-    __syncwarp();   // every lane has read the old slot of ball idx
-    if (lane == 0) {
-      B.sup_idx[nxt][k] = idx;
-      B.sup_u[nxt][k] = B.S_u[k];
-      // the new slot: each ball is in S once, so no other warp reads or
-      // writes slot[idx]; balls that left the support keep stale slots that
-      // fail the check against the new buffer
-      B.slot[idx] = k;
-    }
-  }
+  mult_rows_block(C, B, d, blockIdx.x, gridDim.x);
   // the last block switches to the new multiplier buffers
-  if (last_block_ticket(&st->ctr_slots) && threadIdx.x == 0) {
-    st->sup_cur ^= 1;
-    st->nsup = st->nS;
-    st->action = ACT_NONE;
-  }
+  if (last_block_ticket(&st->ctr_slots) && threadIdx.x == 0) mult_flip(st);
 }
 
 cudaError_t launch_mult_update(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s) {
@@ -883,22 +160,7 @@ cudaError_t launch_mult_update(const double* C, Buffers& B, int64_t m, int d, cu
   return cudaGetLastError();
 }
 
-// ===========================================================================
-// Solve initialisation (state fields set by the host beforehand): x = xt =
-// xk = ab = (r0, c0)/s, trial shadow.
-__global__ void k_state_init(Buffers B, int d) {
-  __shared__ double sh[32];
-  DevState* st = B.st;
-  const DevVecs& V = B.vec;
-  const double inv_s = st->inv_s;
-  for (int k = threadIdx.x; k <= d; k += blockDim.x) {
-    const double v = (k == 0) ? st->rt_abs * inv_s : V.c0[k - 1] * inv_s;
-    V.x[k] = v; V.xt[k] = v; V.xk[k] = v; V.ab[k] = v;
-    V.g[k] = 0.0; V.dx[k] = 0.0;
-  }
-  __syncthreads();
-  set_trial(st, V, d, sh);
-}
+__global__ void k_state_init(Buffers B, int d) { state_init_body(B, d); }
 
 cudaError_t launch_state_init(Buffers& B, int d, cudaStream_t s) {
   k_state_init<<<1, 256, 0, s>>>(B, d);
@@ -968,13 +230,9 @@ cudaError_t launch_eval_outputs(const double* C, Buffers& B, int64_t m, int d, c
   return cudaGetLastError();
 }
 
-// Final centre and ALM radius (unscaled) from the accepted point.
 __global__ void k_final_point(Buffers B, int d, double* __restrict__ c_out,
                               double* __restrict__ r_alm) {
-  DevState* st = B.st;
-  const double s = st->s;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) c_out[j] = B.vec.x[1 + j] * s;
-  if (threadIdx.x == 0) *r_alm = B.vec.x[0] * s;
+  final_point_body(B, d, c_out, r_alm);
 }
 
 // Loop condition of the device-resident solve (CUDA graph while-node): one

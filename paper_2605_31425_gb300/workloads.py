@@ -20,6 +20,9 @@ the benchmark configurations):
                   random centre, half at centre + N(0, 0.3^2/d I) (norm < 0.99)
                   (m=2e5, d=2000)
 * ``lcg``       - the deterministic instance family of Sec. 5 (test instances)
+* ``ragged``    - a batch of independent instances: m log-uniform in
+                  [100, 100000], d drawn from {2, 3, 16, 64, 256}, centres
+                  N(0,1), radii U[0, 0.1]; instance k depends only on (seed, k)
 """
 from __future__ import annotations
 
@@ -110,6 +113,33 @@ def lcg_psi(n: int) -> np.ndarray:
         p = (445 * p + 1) % 4096
         out[j] = p
     return out
+
+
+RAGGED_DIMS = (2, 3, 16, 64, 256)
+
+
+def ragged_shape(k: int, seed: int):
+    """(m, d) of instance k of the ragged batch: m = round(10^(2 + 3u)) (log-uniform
+    in [100, 100000]), d uniform over RAGGED_DIMS; from its own stream."""
+    rng = np.random.Generator(np.random.PCG64([seed, k]))
+    u = _u01(rng, 2)
+    m = int(round(10.0 ** (2.0 + 3.0 * u[0])))
+    d = RAGGED_DIMS[min(int(u[1] * len(RAGGED_DIMS)), len(RAGGED_DIMS) - 1)]
+    return m, d
+
+
+def ragged_instance(k: int, seed: int):
+    """Instance k of the ragged batch: centres N(0,1)^d, radii U[0, 0.1]."""
+    m, d = ragged_shape(k, seed)
+    rng = np.random.Generator(np.random.PCG64([seed, k, 1]))
+    C = rng.standard_normal((m, d))
+    R = _u01(rng, m) * 0.1
+    return C, R
+
+
+def ragged(n: int, seed: int = 1004):
+    """The first n instances of the ragged batch (a list of (C, R))."""
+    return [ragged_instance(k, seed) for k in range(n)]
 
 
 def digest(*arrays) -> str:
