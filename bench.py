@@ -17,9 +17,15 @@ The same JSON line carries, besides the headline:
              every ball of every pass through the FP64 rows), the baseline the
              reduced-precision screens are measured against;
   workloads  the small latency-bound instance (m = 1e4, d = 10: solves/s and
-             microseconds per semismooth Newton step) and the large
+             microseconds per semismooth Newton step); the large
              high-dimensional one (m = 2e5, d = 2000, points on a sphere:
-             solves/s, checked against the closed form r* = 1);
+             solves/s, checked against the closed form r* = 1); the ragged
+             batch (the first --batch-instances of 4096 independent instances,
+             m log-uniform in [100, 1e5], d in {2, 3, 16, 64, 256}) solved by
+             one persistent launch; and serving (Poisson arrivals at 2000
+             requests/s for --serve-seconds from a pool of such instances plus
+             1% with m = 5e5, d = 128, under an 80 GB device budget: solves/s,
+             p50/p99 latency);
   roofline   of the screen kernel (the full pass over all balls), from a few
              more solves with CUDA event nodes around every screen (the nodes
              slow a solve by about 6%, so the timed region runs without them);
@@ -243,6 +249,86 @@ def extra_workloads(meb, torch, local, stream, workloads):
     return out
 
 
+def ragged_batch(meb, torch, local, stream, workloads, n_inst):
+    """The ragged batch (m log-uniform in [100, 1e5], d in {2,3,16,64,256}),
+    its first n_inst instances resident on the device, solved by one
+    meb_solve_batch launch per step after the tuner picked its configuration
+    on a sample; aggregate solves/s, per-solve passes and the algorithmic
+    bytes of the shadow passes (FP16 rows, bound, radius and slot per ball and
+    pass)."""
+    t0 = time.perf_counter()
+    inst = workloads.ragged(n_inst, 1004)
+    gen_s = time.perf_counter() - t0
+    dinst = [(torch.from_numpy(C).cuda(), torch.from_numpy(R).cuda()) for C, R in inst]
+    balls = sum(C.shape[0] for C, _ in inst)
+    in_bytes = sum(C.nbytes + R.nbytes for C, R in inst)
+    del inst
+    ctx = meb.Context(local, stream.cuda_stream)
+    table = meb.tune_batch(dinst, per_class=8, ctx=ctx)
+    res = meb.solve_batch(dinst, ctx=ctx)                      # warm-up
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(3)]
+    for a, b in ev:
+        a.record(stream)
+        res = meb.solve_batch(dinst, ctx=ctx)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ok = sum(1 for r in res if r["status"] == 0)
+    # algorithmic bytes: every pass streams, per ball, 16*ceil(d/8) + 12 bytes (FP16
+    # shadow) or 16*ceil(d/4) + 12 (FP32 shadow, d <= 4 class) -- a lower bound
+    # that leaves out the one FP64 read of the setup and the FP64 rows
+    passes_bytes = 0
+    for (C, _R), r in zip(dinst, res):
+        m, d = C.shape
+        row = 16 * ((d + 3) // 4) if d <= 4 else 16 * ((d + 7) // 8)
+        passes_bytes += r["passes"] * m * (row + 12)
+    del dinst
+    torch.cuda.empty_cache()
+    return {"value": ok / (statistics.median(ms) / 1e3), "unit": UNIT, "instances": n_inst,
+            "steps": len(ms), "ms_per_step": statistics.median(ms), "balls": balls,
+            "input_gb": in_bytes / 1e9, "generate_s": gen_s,
+            "shadow_pass_gb_per_s": passes_bytes / (statistics.median(ms) / 1e3) / 1e9,
+            "passes_per_solve": statistics.mean(r["passes"] for r in res),
+            "tuned_table": table, "solved_ok": ok,
+            "sample": f"the first {n_inst} of the 4096-instance batch (seed 1004)"}
+
+
+def serving(meb, workloads, seconds, rate=2000.0, n_pool=256):
+    """Poisson arrivals at `rate` requests/s for `seconds`, instances drawn from
+    a pool of ragged instances (1% large: m = 5e5, d = 128), under an 80 GB
+    device-memory budget; every request's latency from submission to result.
+    Host inputs are pinned (torch)."""
+    import torch
+    pool = [tuple(torch.from_numpy(a).pin_memory() for a in workloads.ragged_instance(k, 1005))
+            for k in range(n_pool)]
+    big = [tuple(torch.from_numpy(a).pin_memory() for a in workloads.cube(500_000, 128, 1005 + k, 0.05))
+           for k in range(2)]
+    t_arr, pick = workloads.poisson_arrivals(rate, seconds, n_pool, 1005, 0.01, len(big))
+    sv = meb.Server(budget_bytes=80 * 10 ** 9)
+    tickets = [None] * len(t_arr)
+    t0 = time.perf_counter()
+    for k, (ta, p) in enumerate(zip(t_arr, pick)):
+        while time.perf_counter() - t0 < ta:
+            time.sleep(0.0001)
+        C, R = big[-1 - p] if p < 0 else pool[p]
+        tickets[k] = sv.submit(C, R, active_cap=256)
+    res = [sv.wait(t) for t in tickets]
+    wall = time.perf_counter() - t0
+    st = sv.stats()
+    sv.close()
+    lat = np.array([r["latency_s"] for r in res]) * 1e3
+    ok = sum(1 for r in res if r["rc"] == 0)
+    small_lat = lat[pick >= 0]
+    return {"value": ok / wall, "unit": UNIT, "offered_rate": rate, "requests": len(res),
+            "arrival_window_s": seconds, "wall_s": wall, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "p50_small_ms": float(np.percentile(small_lat, 50)),
+            "p99_small_ms": float(np.percentile(small_lat, 99)),
+            "large_requests": int(np.sum(pick < 0)), "launches": st["launches"],
+            "peak_device_gb": st["peak_bytes"] / 1e9, "budget_gb": 80,
+            "pool": f"{n_pool} ragged instances (seed 1005) + 2 large (m=5e5, d=128), pinned host memory"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -254,6 +340,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="headline only (no FP64 arm, no other workloads)")
+    ap.add_argument("--batch-instances", type=int, default=1024)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -373,6 +461,11 @@ def main():
         del dC, dR
         torch.cuda.empty_cache()
         extra = extra_workloads(meb, torch, local, stream, workloads)
+        if args.batch_instances > 0:
+            extra["ragged_batch"] = ragged_batch(meb, torch, local, stream, workloads,
+                                                 args.batch_instances)
+        if args.serve_seconds > 0:
+            extra["serving"] = serving(meb, workloads, args.serve_seconds)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

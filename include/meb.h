@@ -247,6 +247,55 @@ int meb_solve_batch(meb_ctx *ctx, int32_t n, const meb_batch_item *items, double
 int meb_tune_batch(meb_ctx *ctx, int32_t n, const meb_batch_item *items, int32_t per_class,
                    unsigned flags, int32_t *configs);
 
+/* Serving (no counterpart in the paper): a request loop that solves MEB
+ * instances as they arrive, with continuous batching.  Requests are admitted
+ * in arrival order while their device footprint (inputs, outputs and solver
+ * scratch, meb_footprint) fits in budget_bytes; admitted small requests are
+ * grouped into meb_solve_batch launches by several workers, each on its own
+ * context and stream, so a group launched while others run shares the GPU
+ * with them; requests with m*d >= large_balls take meb_solve's multi-block
+ * path on their own workers.  Each request is solved by exactly the steps it
+ * would take alone: its results do not depend on the mix.
+ * Zero fields of cfg take the defaults: 4 small workers, 1 large worker,
+ * large_balls 2^24, groups of at most 152 requests. */
+typedef struct {
+    int64_t budget_bytes;     /* device memory for admitted requests (required, > 0) */
+    int64_t large_balls;      /* m*d at or above which a request is "large"          */
+    int32_t small_workers;
+    int32_t large_workers;
+    int32_t max_group;
+    int32_t reserved;
+} meb_server_config;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t launches;         /* batch launches and multi-block solves             */
+    int64_t in_use_bytes;     /* footprint of admitted, unfinished requests        */
+    int64_t peak_bytes;       /* its maximum since the server started             */
+    int64_t pending;          /* submitted, not yet admitted                       */
+} meb_server_stats;
+
+typedef struct meb_server meb_server;
+
+/* Create a server on `device` (params may be NULL: defaults). */
+int meb_server_create(meb_server **out, int device, const meb_server_config *cfg,
+                      const meb_params *params);
+/* Queue one instance (host arrays: centers m x d, radii m; outputs c_out (d),
+ * active_idx (first active_cap ascending indices), info).  Returns at once
+ * with a ticket; every array must stay valid until the request completes.
+ * MEB_EINVAL for bad sizes or NULL pointers; MEB_ENOMEM when the request alone
+ * exceeds the budget. */
+int meb_server_submit(meb_server *sv, const double *centers, const double *radii, int64_t m,
+                      int32_t d, double *c_out, int64_t *active_idx, int64_t active_cap,
+                      meb_info *info, int64_t *ticket);
+/* Wait up to timeout_s seconds (< 0: no limit) for a request: its return code
+ * (as meb_solve's) in *rc and its latency, submit to completion, in
+ * *latency_s.  MEB_ETIMEOUT if it has not completed in time (wait again). */
+int meb_server_wait(meb_server *sv, int64_t ticket, double timeout_s, int *rc, double *latency_s);
+int meb_server_get_stats(meb_server *sv, meb_server_stats *out);
+/* Finish every queued request, stop the workers and free the server. */
+void meb_server_destroy(meb_server *sv);
+
 /* One evaluation of the prox-AL subproblem (Sec. 4, Algorithm 2 steps 1-2) at
  * x = (r, c) (x[0] = r) with proximal centre xbar, multipliers U (m), V (m x d),
  * penalty sigma > 0, proximal weight tau > 0, on the unscaled data:

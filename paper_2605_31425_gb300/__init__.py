@@ -7,7 +7,8 @@ the CUDA library).
 """
 _API = ("MEB_PTR_DEVICE", "Context", "MebError", "MebInfo", "MebParams", "default_context",
         "eval_alm", "feas_check", "feas_check_noalloc", "load", "params_default", "solve", "stats", "reset_stats",
-        "solve_batch", "tune_batch", "MEB_ETIMEOUT", "MEB_ENOTCONV", "MEB_EINVAL")
+        "solve_batch", "tune_batch", "MEB_ETIMEOUT", "MEB_ENOTCONV", "MEB_EINVAL", "Server",
+        "footprint")
 
 
 def __getattr__(name):

@@ -55,6 +55,21 @@ class MebBatchItem(ct.Structure):
     ]
 
 
+class MebServerConfig(ct.Structure):
+    _fields_ = [
+        ("budget_bytes", ct.c_int64), ("large_balls", ct.c_int64), ("small_workers", ct.c_int32),
+        ("large_workers", ct.c_int32), ("max_group", ct.c_int32), ("reserved", ct.c_int32),
+    ]
+
+
+class MebServerStats(ct.Structure):
+    _fields_ = [
+        ("submitted", ct.c_int64), ("completed", ct.c_int64), ("failed", ct.c_int64),
+        ("launches", ct.c_int64), ("in_use_bytes", ct.c_int64), ("peak_bytes", ct.c_int64),
+        ("pending", ct.c_int64),
+    ]
+
+
 class MebStats(ct.Structure):
     _fields_ = [
         ("kernel_launches", ct.c_int64), ("pass_launches", ct.c_int64), ("pass_ms", ct.c_double),
@@ -114,6 +129,20 @@ def load():
             lib.meb_tune_batch.argtypes = [ct.c_void_p, ct.c_int32, ct.POINTER(MebBatchItem),
                                            ct.c_int32, ct.c_uint, ct.POINTER(ct.c_int32)]
             lib.meb_tune_batch.restype = ct.c_int
+            lib.meb_footprint.argtypes = [ct.c_int64, ct.c_int32, ct.c_int32, _I64]
+            lib.meb_footprint.restype = ct.c_int
+            lib.meb_server_create.argtypes = [ct.POINTER(ct.c_void_p), ct.c_int,
+                                              ct.POINTER(MebServerConfig), ct.POINTER(MebParams)]
+            lib.meb_server_create.restype = ct.c_int
+            lib.meb_server_submit.argtypes = [ct.c_void_p, _D, _D, ct.c_int64, ct.c_int32, _D, _I64,
+                                              ct.c_int64, ct.POINTER(MebInfo), _I64]
+            lib.meb_server_submit.restype = ct.c_int
+            lib.meb_server_wait.argtypes = [ct.c_void_p, ct.c_int64, ct.c_double,
+                                            ct.POINTER(ct.c_int), ct.POINTER(ct.c_double)]
+            lib.meb_server_wait.restype = ct.c_int
+            lib.meb_server_get_stats.argtypes = [ct.c_void_p, ct.POINTER(MebServerStats)]
+            lib.meb_server_get_stats.restype = ct.c_int
+            lib.meb_server_destroy.argtypes = [ct.c_void_p]
             lib.meb_set_profiling.argtypes = [ct.c_void_p, ct.c_int]
             lib.meb_reset_stats.argtypes = [ct.c_void_p]
             lib.meb_get_stats.argtypes = [ct.c_void_p, ct.POINTER(MebStats)]
@@ -506,3 +535,82 @@ def tune_batch(instances, per_class: int = 16, ctx: Context | None = None):
     cfg = (ct.c_int32 * 16)()
     cx._check(cx._lib.meb_tune_batch(cx._h, n, items, int(per_class), flags, cfg))
     return [tuple(cfg[3 * c:3 * c + 3]) for c in range(5)] + [cfg[15]]
+
+
+def footprint(m: int, d: int, batched: bool) -> int:
+    """meb_footprint: device scratch bytes of one solve (batched: one instance
+    of a batch with per-instance slots)."""
+    b = ct.c_int64()
+    rc = load().meb_footprint(int(m), int(d), 1 if batched else 0, ct.byref(b))
+    if rc != MEB_OK:
+        raise MebError(rc, "meb_footprint: size out of range")
+    return b.value
+
+
+class Server:
+    """meb_server_*: continuous batching of requests under a device-memory
+    budget.  submit() takes host float64 arrays and returns a ticket at once;
+    wait(ticket) returns the result dict with its latency (seconds)."""
+
+    def __init__(self, budget_bytes: int, device: int = 0, small_workers: int = 0,
+                 large_workers: int = 0, large_balls: int = 0, max_group: int = 0,
+                 params: MebParams | None = None):
+        self._lib = load()
+        cfg = MebServerConfig(int(budget_bytes), int(large_balls), int(small_workers),
+                              int(large_workers), int(max_group), 0)
+        h = ct.c_void_p()
+        rc = self._lib.meb_server_create(ct.byref(h), int(device), ct.byref(cfg),
+                                         ct.byref(params) if params is not None else None)
+        if rc != MEB_OK:
+            raise MebError(rc, "meb_server_create failed")
+        self._h = h
+        self._req = {}
+
+    def submit(self, centers, radii, active_cap: int | None = None) -> int:
+        C = _host_f64(centers)
+        R = _host_f64(radii)
+        m, d = C.shape
+        if R.shape[0] != m:
+            raise ValueError("radii must have m entries")
+        cap = m if active_cap is None else min(active_cap, m)
+        c_out = np.empty(d)
+        act = np.empty(max(cap, 1), dtype=np.int64)
+        info = MebInfo()
+        t = ct.c_int64()
+        rc = self._lib.meb_server_submit(self._h, _as_d(_ptr(C)[0]), _as_d(_ptr(R)[0]), m, d,
+                                         _as_d(c_out.ctypes.data), _as_i(act.ctypes.data), cap,
+                                         ct.byref(info), ct.byref(t))
+        if rc != MEB_OK:
+            raise MebError(rc, "meb_server_submit failed")
+        self._req[t.value] = (C, R, c_out, act, cap, info)   # alive until wait()
+        return t.value
+
+    def wait(self, ticket: int, timeout: float = -1.0):
+        rc = ct.c_int()
+        lat = ct.c_double()
+        w = self._lib.meb_server_wait(self._h, int(ticket), float(timeout), ct.byref(rc), ct.byref(lat))
+        if w == MEB_ETIMEOUT:
+            return None
+        if w != MEB_OK:
+            raise MebError(w, "meb_server_wait: unknown ticket")
+        _C, _R, c_out, act, cap, info = self._req.pop(ticket)
+        res = _info_dict(info)
+        res.update(c=c_out, active=act[:min(res["n_active"], cap)], rc=rc.value,
+                   latency_s=lat.value)
+        return res
+
+    def stats(self) -> dict:
+        st = MebServerStats()
+        self._lib.meb_server_get_stats(self._h, ct.byref(st))
+        return {k: getattr(st, k) for k, _ in MebServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.meb_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmeb.so")
-SOURCES = ["meb_pass.cu", "meb_solve.cu", "meb_batch.cu", "meb_api.cu", "meb_noalloc.cu"]
+SOURCES = ["meb_pass.cu", "meb_solve.cu", "meb_batch.cu", "meb_api.cu", "meb_noalloc.cu",
+           "meb_serve.cpp"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 
@@ -57,7 +58,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".{os.getpid()}.tmp"
-    r = subprocess.run([nvcc, "-gencode", GENCODE, "-shared", "-o", tmp, *objs, "-lcudart"],
+    r = subprocess.run([nvcc, "-gencode", GENCODE, "-shared", "-o", tmp, *objs, "-lcudart",
+                        "-lpthread"],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

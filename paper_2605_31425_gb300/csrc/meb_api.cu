@@ -104,9 +104,22 @@ static int fail(meb_ctx* ctx, int code, const char* fmt, ...) {
                   "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
   } while (0)
 
+// Device allocations of the context's scratch.  With MEB_OPT_RELEASE_SCRATCH
+// they are stream-ordered on the context's stream (cudaMallocAsync /
+// cudaFreeAsync), so that allocating and freeing on one context never waits
+// for work of another; otherwise plain cudaMalloc / cudaFree.
+static cudaError_t dev_alloc(meb_ctx* ctx, void** p, size_t bytes) {
+  return ctx->release ? cudaMallocAsync(p, bytes, ctx->stream) : cudaMalloc(p, bytes);
+}
+static void dev_free(meb_ctx* ctx, void* p) {
+  if (!p) return;
+  if (ctx->release) cudaFreeAsync(p, ctx->stream);
+  else cudaFree(p);
+}
+
 static void free_buffers(meb_ctx* ctx) {
   Buffers& B = ctx->B;
-  if (ctx->arena) cudaFree(ctx->arena);
+  dev_free(ctx, ctx->arena);
   ctx->arena = nullptr;
   ctx->arena_bytes = 0;
   const int64_t launches = B.launches;
@@ -227,7 +240,7 @@ static int ensure_buffers(meb_ctx* ctx, int64_t m, int d) {
     return MEB_OK;
   free_buffers(ctx);
   const size_t bytes = solve_layout(nullptr, nullptr, m, d);
-  CK(cudaMalloc(&ctx->arena, bytes));
+  CK(dev_alloc(ctx, &ctx->arena, bytes));
   ctx->arena_bytes = bytes;
   solve_layout(&ctx->B, (char*)ctx->arena, m, d);
   const int n1 = d + 1, d4 = (d + 3) / 4;
@@ -242,7 +255,7 @@ static int ensure_buffers(meb_ctx* ctx, int64_t m, int d) {
 static void release_scratch(meb_ctx* ctx) {
   free_buffers(ctx);
   for (int k = 0; k < 32; k++) {
-    if (ctx->pool_ptr[k]) cudaFree(ctx->pool_ptr[k]);
+    dev_free(ctx, ctx->pool_ptr[k]);
     ctx->pool_ptr[k] = nullptr;
     ctx->pool_cap[k] = 0;
   }
@@ -263,10 +276,10 @@ struct CallScope {
 
 static int pool(meb_ctx* ctx, int id, size_t bytes, void** out) {
   if (ctx->pool_cap[id] < bytes) {
-    if (ctx->pool_ptr[id]) cudaFree(ctx->pool_ptr[id]);
+    dev_free(ctx, ctx->pool_ptr[id]);
     ctx->pool_ptr[id] = nullptr;
     ctx->pool_cap[id] = 0;
-    CK(cudaMalloc(&ctx->pool_ptr[id], bytes ? bytes : 8));
+    CK(dev_alloc(ctx, &ctx->pool_ptr[id], bytes ? bytes : 8));
     ctx->pool_cap[id] = bytes;
   }
   *out = ctx->pool_ptr[id];
@@ -346,9 +359,8 @@ void meb_destroy(meb_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  free_buffers(ctx);
-  for (int k = 0; k < 32; k++)
-    if (ctx->pool_ptr[k]) cudaFree(ctx->pool_ptr[k]);
+  release_scratch(ctx);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
   if (ctx->d_flags) cudaFree(ctx->d_flags);

@@ -142,6 +142,25 @@ def ragged(n: int, seed: int = 1004):
     return [ragged_instance(k, seed) for k in range(n)]
 
 
+def poisson_arrivals(rate: float, duration: float, n_pool: int, seed: int,
+                     large_frac: float = 0.0, n_large: int = 0):
+    """Arrival times (seconds, increasing, < duration) of a Poisson stream at
+    `rate` requests/s, and for each the index of the instance it carries: with
+    probability large_frac one of n_large large instances (returned as
+    -1 - k), else one of n_pool ragged instances."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_max = int(rate * duration * 1.5 + 50)
+    gaps = -np.log1p(-_u01(rng, n_max)) / rate
+    t = np.cumsum(gaps)
+    t = t[t < duration]
+    u = _u01(rng, 2 * len(t)).reshape(-1, 2) if len(t) else np.zeros((0, 2))
+    pick = np.minimum((u[:, 1] * n_pool).astype(np.int64), n_pool - 1)
+    if n_large > 0 and large_frac > 0:
+        big = u[:, 0] < large_frac
+        pick = np.where(big, -1 - np.minimum((u[:, 1] * n_large).astype(np.int64), n_large - 1), pick)
+    return t, pick
+
+
 def digest(*arrays) -> str:
     """SHA-256 of the raw bytes of the given arrays (for stored expected values)."""
     h = hashlib.sha256()

@@ -16,8 +16,37 @@ import oracle  # noqa: E402
 from paper_2605_31425_gb300 import workloads  # noqa: E402
 
 
+# The paper's test instances (Sec. 5): its LCG family at the sizes of Fig. 2
+# (d in {20, 30, 40, 50}, m in {1e3, 5e3, 1e4, 5e4, 1e5}) and of Fig. 3
+# (d in {1e2, 5e2, 1e3, 5e3, 1e4}, m in {1e3, 5e3}).
+PAPER_SWEEP = ([(m, d) for d in (20, 30, 40, 50) for m in (1000, 5000, 10_000, 50_000, 100_000)]
+               + [(m, d) for d in (100, 500, 1000, 5000, 10_000) for m in (1000, 5000)])
+
+
+def paper_sweep():
+    """tests/golden/paper_sweep.json: the oracle's radius (tol 1e-12) and
+    active-set size for every instance of PAPER_SWEEP."""
+    out = []
+    for m, d in PAPER_SWEEP:
+        C, R = workloads.lcg(m, d)
+        t = time.time()
+        res = oracle.solve(C, R, tol=1e-12)
+        dt = time.time() - t
+        out.append(dict(m=m, d=d, input_sha256=workloads.digest(C, R), r=res["r"],
+                        n_active=int(len(res["active"])), status=res["status"],
+                        passes=res["passes"], oracle_seconds=dt))
+        print(m, d, res["r"], res["status"], f"{dt:.1f}s", flush=True)
+    with open(os.path.join(HERE, "paper_sweep.json"), "w") as f:
+        json.dump(dict(tol=1e-12, note="written by tests/golden/make_golden.py from oracle.solve; "
+                       "inputs from paper_2605_31425_gb300.workloads.lcg(m, d)", instances=out),
+                  f, indent=1)
+
+
 def main(names):
     for name in names:
+        if name == "paper_sweep":
+            paper_sweep()
+            continue
         C, R = workloads.workload(name)
         t = time.time()
         res = oracle.solve(C, R, tol=1e-12)
