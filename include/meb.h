@@ -66,7 +66,18 @@ typedef struct {
     int32_t newton_fp64; /* 1: solve every dense Newton system by the FP64 Cholesky   */
                          /* (the reference path; default 0: FP32 Gauss-Jordan with   */
                          /* refinement, FP64 Cholesky only as the fallback)          */
-    int32_t reserved[2];
+    /* The mixed-precision reduction pipeline of Sec. 4.2 (mixed = 1): a
+     * low-precision ripALM (FP32 rows from the FP32 shadow) to tol_lp on all
+     * balls; the reduced set I_red = {i : r - r_i - ||c - c_i|| <= tol_red r}
+     * at its point (certified, plus every ball with a multiplier); the FP64
+     * ripALM on I_red, warm-started from the low-precision point, penalty and
+     * multipliers; then the FP64 feasibility pass over all balls, adding the
+     * violated ones to I_red and solving again, at most max_readd times.  The
+     * result is an FP64 solve to tol of the whole instance. */
+    int32_t mixed;       /* 0 */
+    int32_t max_readd;   /* 8 */
+    double tol_lp;       /* KKT_max tolerance of the low-precision run; 1e-2 (Sec. 5) */
+    double tol_red;      /* relative screening threshold; 0 means max(10 KKT_lp, 1e-3) */
 } meb_params;
 
 typedef struct {
@@ -82,6 +93,9 @@ typedef struct {
     int32_t status;      /* 0 converged, 1 iteration cap                               */
     int32_t newton_inverses; /* dense Newton systems: FP32 Gauss-Jordan inverses of H  */
     int32_t newton_fp64; /* dense Newton systems that fell back to FP64 Cholesky       */
+    int64_t n_reduced;   /* balls of the FP64 solve (m unless params->mixed)           */
+    int32_t readd_rounds; /* mixed: FP64 solves after the first (violated balls added) */
+    int32_t lowp_passes; /* mixed: passes of the low-precision run                     */
 } meb_info;
 
 /* Measurement counters of a context (no counterpart in the paper: they

@@ -33,7 +33,8 @@ class MebParams(ct.Structure):
         ("tau", ct.c_double), ("armijo_mu", ct.c_double), ("active_theta", ct.c_double),
         ("max_outer", ct.c_int32), ("max_ssn", ct.c_int32), ("max_backtrack", ct.c_int32),
         ("dense_max_d", ct.c_int32), ("max_cg", ct.c_int32), ("newton_fp64", ct.c_int32),
-        ("reserved", ct.c_int32 * 2),
+        ("mixed", ct.c_int32), ("max_readd", ct.c_int32), ("tol_lp", ct.c_double),
+        ("tol_red", ct.c_double),
     ]
 
 
@@ -45,6 +46,7 @@ class MebInfo(ct.Structure):
         ("outer_iters", ct.c_int32), ("ssn_iters", ct.c_int32), ("cg_iters", ct.c_int32),
         ("passes", ct.c_int32), ("backtracks", ct.c_int32), ("status", ct.c_int32),
         ("newton_inverses", ct.c_int32), ("newton_fp64", ct.c_int32),
+        ("n_reduced", ct.c_int64), ("readd_rounds", ct.c_int32), ("lowp_passes", ct.c_int32),
     ]
 
 
@@ -345,7 +347,8 @@ def solve(centers, radii, tol: float = 0.0, params: MebParams | None = None,
         fp64_rows=int(info.fp64_rows), outer_iters=info.outer_iters, ssn_iters=info.ssn_iters,
         cg_iters=info.cg_iters, passes=info.passes, backtracks=info.backtracks,
         status=info.status, rc=rc, newton_inverses=info.newton_inverses,
-        newton_fp64=info.newton_fp64,
+        newton_fp64=info.newton_fp64, n_reduced=int(info.n_reduced),
+        readd_rounds=info.readd_rounds, lowp_passes=info.lowp_passes,
     )
 
 
@@ -459,7 +462,9 @@ def _info_dict(info):
                 fp64_rows=int(info.fp64_rows), outer_iters=info.outer_iters,
                 ssn_iters=info.ssn_iters, cg_iters=info.cg_iters, passes=info.passes,
                 backtracks=info.backtracks, status=info.status,
-                newton_inverses=info.newton_inverses, newton_fp64=info.newton_fp64)
+                newton_inverses=info.newton_inverses, newton_fp64=info.newton_fp64,
+                n_reduced=int(info.n_reduced), readd_rounds=info.readd_rounds,
+                lowp_passes=info.lowp_passes)
 
 
 def _batch_items(instances, active_cap):

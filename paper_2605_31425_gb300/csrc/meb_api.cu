@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <iterator>
 #include <type_traits>
 #include <vector>
 
@@ -41,18 +42,23 @@ struct meb_ctx {
   double* d_scal = nullptr;     // device scalars
   int64_t* d_i64 = nullptr;     // device int64 scalars
   int profiling = 0;            // time every pass launch with CUDA events
-  // device-resident solve loop: a CUDA graph whose while-node runs controller
-  // ticks until the controller stops; rebuilt when the problem or buffers change
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};
-  int64_t gm = 0;
-  int gd = 0;
-  int gmode = -1;
-  int gvar = -1;
-  int gprof = -1;
+  // device-resident solve loops: CUDA graphs of controller ticks, one per
+  // buffer set in use (the full instance and, in the mixed-precision
+  // pipeline, the reduced one); rebuilt when the problem or buffers change
+  struct TickGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const void* key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int64_t m = 0;
+    int d = 0, mode = -1, var = -1, prof = -1, lowp = -1;
+    long long wait = -1;
+  } tg[2];
+  int tg_next = 0;
   cudaEvent_t gev[2 * 8] = {};
-  long long gwait = -1;
+  // the reduced instance of the mixed-precision pipeline
+  Buffers Bred{};
+  void* red_arena = nullptr;
+  size_t red_bytes = 0;
   // options (meb_set_option)
   // tick loop: 0 = graph of kUnrollTicks ticks relaunched until the controller
   // stops (default), 1 = host-driven ticks, 2 = graph with a while-node
@@ -62,8 +68,10 @@ struct meb_ctx {
   int eval_shadow_exp = 0;                // FP16 shadow scale 2^exp of meb_eval_alm
   long long wait_cycles = 2000000000LL;   // bound of the bulk-copy screen's waits
   // multipliers of the last solve (meb_get_multipliers): 0 none, 1 the
-  // support arrays of the final point, 2 one ball, 3 all balls the same point
+  // support arrays of the final point, 2 one ball, 3 all balls the same point,
+  // 4 the reduced instance's support arrays (indices mapped back to the balls)
   int mult_kind = 0;
+  const int64_t* mult_map = nullptr;
   int64_t mult_n = 0, mult_m = 0;
   int mult_d = 0;
   // batched solver: configuration per class of d (meb_tune_batch)
@@ -83,7 +91,8 @@ static const int kUnrollTicks = 8;
 
 enum { POOL_C, POOL_R, POOL_U, POOL_V, POOL_X, POOL_XB, POOL_Q, POOL_UP, POOL_VP, POOL_HQ,
        POOL_H, POOL_G, POOL_COUT, POOL_ACT, POOL_BIN, POOL_BOUT, POOL_BITEMS, POOL_BRES,
-       POOL_BSLOTS, POOL_BSLOTB, POOL_BCFG, POOL_N };
+       POOL_BSLOTS, POOL_BSLOTB, POOL_BCFG, POOL_RED_IDX, POOL_RED_C, POOL_RED_R, POOL_WIDX,
+       POOL_WU, POOL_WV, POOL_WX, POOL_N };
 static_assert(POOL_N <= 32, "pool table");
 
 static int fail(meb_ctx* ctx, int code, const char* fmt, ...) {
@@ -117,8 +126,20 @@ static void dev_free(meb_ctx* ctx, void* p) {
   else cudaFree(p);
 }
 
+static void drop_graphs(meb_ctx* ctx) {
+  for (auto& g : ctx->tg) {
+    if (g.gexec) cudaGraphExecDestroy(g.gexec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g = meb_ctx::TickGraph{};
+  }
+}
+
 static void free_buffers(meb_ctx* ctx) {
   Buffers& B = ctx->B;
+  dev_free(ctx, ctx->red_arena);
+  ctx->red_arena = nullptr;
+  ctx->red_bytes = 0;
+  ctx->Bred = Buffers{};
   dev_free(ctx, ctx->arena);
   ctx->arena = nullptr;
   ctx->arena_bytes = 0;
@@ -127,9 +148,8 @@ static void free_buffers(meb_ctx* ctx) {
   B.launches = launches;
   ctx->buf_m = 0;
   ctx->buf_d = 0;
-  // the captured tick graph holds the freed pointers: rebuild it on next use
-  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
-  if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+  // captured tick graphs hold freed pointers: rebuild them on next use
+  drop_graphs(ctx);
 }
 
 // The scratch of a multi-block solve of (m, d), laid out in one arena
@@ -328,6 +348,10 @@ void meb_params_default(meb_params* p) {
   p->max_backtrack = 40;
   p->dense_max_d = kMaxDenseN - 1;
   p->max_cg = 500;
+  p->mixed = 0;
+  p->max_readd = 8;
+  p->tol_lp = 1e-2;
+  p->tol_red = 0.0;
 }
 
 int meb_create(meb_ctx** out, int device, void* cuda_stream) {
@@ -369,8 +393,7 @@ void meb_destroy(meb_ctx* ctx) {
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   for (int k = 0; k < 2; k++)
     if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
-  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
-  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  drop_graphs(ctx);
   for (int k = 0; k < 16; k++)
     if (ctx->gev[k]) cudaEventDestroy(ctx->gev[k]);
   delete ctx;
@@ -445,7 +468,8 @@ static int resolve_params(meb_ctx* ctx, const meb_params* params, double tol, me
   if (tol > 0) P.tol = tol;
   if (!(P.tol > 0) || !(P.rho >= 0 && P.rho < 1) || !(P.sigma0 > 0) || !(P.tau > 0) ||
       !(P.sigma_max >= P.sigma0) || !(P.sigma_growth >= 1) || P.max_outer < 1 || P.max_ssn < 1 ||
-      P.max_backtrack < 0 || P.max_cg < 1 || !(P.active_theta >= 0))
+      P.max_backtrack < 0 || P.max_cg < 1 || !(P.active_theta >= 0) ||
+      (P.mixed && (!(P.tol_lp > 0) || !(P.tol_red >= 0) || P.max_readd < 0)))
     return fail(ctx, MEB_EINVAL, "invalid parameters");
   *out = P;
   return MEB_OK;
@@ -462,34 +486,42 @@ static int check_sizes(meb_ctx* ctx, int64_t m, int32_t d) {
 }
 
 
-static int read_state(meb_ctx* ctx) {
-  CK(cudaMemcpyAsync(ctx->h_st, ctx->B.st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
+static int read_state(meb_ctx* ctx, const Buffers& B) {
+  CK(cudaMemcpyAsync(ctx->h_st, B.st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return MEB_OK;
 }
 
-// Build (or reuse) the graph: while (status == 0) { pass; controller; Newton
-// (dense); multiplier update; loop condition }.  Every kernel of the tick is
-// gated on the controller's action, so the tick is a fixed sequence.
-static int solve_graph(meb_ctx* ctx, const double* C, const double* R, int64_t m, int d) {
-  Buffers& B = ctx->B;
+// Build (or reuse) the tick graph of buffer set B: kUnrollTicks ticks of
+// { pass; controller; Newton (dense); multiplier update } (mode 0), or a
+// while-node running ticks until the controller stops (mode 2).  Every kernel
+// of the tick is gated on the controller's action, so the tick is a fixed
+// sequence.  *out: the cached entry.
+static int solve_graph(meb_ctx* ctx, Buffers& B, const double* C, const double* R, int64_t m,
+                       int d, meb_ctx::TickGraph** out) {
   const int mode = ctx->loop_mode;
   const int prof = ctx->profiling;
-  if (ctx->gexec && ctx->gkey[0] == C && ctx->gkey[1] == R && ctx->gkey[2] == B.st &&
-      ctx->gkey[3] == (const void*)(B.use_x16 ? (const void*)B.X16 : (const void*)B.X32) &&
-      ctx->gvar == screen_variant(B, d) && ctx->gwait == B.wait_cycles &&
-      ctx->gm == m && ctx->gd == d && ctx->gmode == mode && ctx->gprof == prof)
-    return MEB_OK;
+  const void* xs = B.use_x16 ? (const void*)B.X16 : (const void*)B.X32;
+  for (auto& g : ctx->tg) {
+    if (g.gexec && g.key[0] == C && g.key[1] == R && g.key[2] == B.st && g.key[3] == xs &&
+        g.key[4] == B.W && g.var == screen_variant(B, d) && g.wait == B.wait_cycles &&
+        g.m == m && g.d == d && g.mode == mode && g.prof == prof && g.lowp == (int)B.lowp) {
+      *out = &g;
+      return MEB_OK;
+    }
+  }
   if (prof && !ctx->gev[0])
     for (int k = 0; k < 16; k++) CK(cudaEventCreate(&ctx->gev[k]));
-  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
-  if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+  meb_ctx::TickGraph& g = ctx->tg[ctx->tg_next];
+  ctx->tg_next ^= 1;
+  if (g.gexec) { cudaGraphExecDestroy(g.gexec); g.gexec = nullptr; }
+  if (g.graph) { cudaGraphDestroy(g.graph); g.graph = nullptr; }
   cudaStream_t s = ctx->stream;
   cudaError_t e = cudaSuccess;
   if (mode == 2) {
-    CK(cudaGraphCreate(&ctx->graph, 0));
+    CK(cudaGraphCreate(&g.graph, 0));
     cudaGraphConditionalHandle h;
-    CK(cudaGraphConditionalHandleCreate(&h, ctx->graph, 1, cudaGraphCondAssignDefault));
+    CK(cudaGraphConditionalHandleCreate(&h, g.graph, 1, cudaGraphCondAssignDefault));
     // cudaGraphNodeParams holds a union without a default constructor: zeroed storage
     alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
     memset(npbuf, 0, sizeof(npbuf));
@@ -499,7 +531,7 @@ static int solve_graph(meb_ctx* ctx, const double* C, const double* R, int64_t m
     np->conditional.type = cudaGraphCondTypeWhile;
     np->conditional.size = 1;
     cudaGraphNode_t node;
-    CK(cudaGraphAddNode(&node, ctx->graph, nullptr, nullptr, 0, np));
+    CK(cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, np));
     cudaGraph_t body = np->conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     e = launch_pass(C, R, B, m, d, s);
@@ -521,18 +553,207 @@ static int solve_graph(meb_ctx* ctx, const double* C, const double* R, int64_t m
       if (e == cudaSuccess) e = launch_newton_dense(B, d, s);
       if (e == cudaSuccess) e = launch_mult_update(C, B, m, d, s);
     }
-    cudaError_t e2 = cudaStreamEndCapture(s, &ctx->graph);
+    cudaError_t e2 = cudaStreamEndCapture(s, &g.graph);
     if (e != cudaSuccess) return fail(ctx, MEB_ECUDA, "graph capture: %s", cudaGetErrorString(e));
     CK(e2);
   }
-  CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
-  ctx->gkey[0] = C; ctx->gkey[1] = R; ctx->gkey[2] = B.st;
-  ctx->gkey[3] = B.use_x16 ? (const void*)B.X16 : (const void*)B.X32;
-  ctx->gvar = screen_variant(B, d);
-  ctx->gwait = B.wait_cycles;
-  ctx->gm = m; ctx->gd = d; ctx->gmode = mode; ctx->gprof = prof;
+  CK(cudaGraphInstantiate(&g.gexec, g.graph, 0));
+  g.key[0] = C; g.key[1] = R; g.key[2] = B.st; g.key[3] = xs; g.key[4] = B.W;
+  g.var = screen_variant(B, d);
+  g.wait = B.wait_cycles;
+  g.m = m; g.d = d; g.mode = mode; g.prof = prof; g.lowp = (int)B.lowp;
+  *out = &g;
   return MEB_OK;
 }
+
+// The input check, the FP32 shadow (origin c_0), the mean centre c0 and
+// r0 = max_i ||c0 - c_i|| + r_i (certified feasibility pass at c0).
+static int setup_instance(meb_ctx* ctx, Buffers& B, const double* C, const double* R, int64_t m,
+                          int d, double* r0) {
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
+  CK(launch_shadow(C, R, m, d, B, B.vec.o, B.vec.c0, ctx->d_flags, s));
+  CK(launch_feas_cert(C, R, m, d, B.vec.c0, 0.0, INFINITY, 2, 1, B, ctx->d_scal, ctx->d_i64,
+                      ctx->d_i64 + 1, s));
+  CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int bad;
+  memcpy(&bad, ctx->h_scal + 1, sizeof(int));
+  if (bad) return fail(ctx, MEB_EINVAL, "non-finite centre or radius, or negative radius");
+  *r0 = ctx->h_scal[0];
+  return MEB_OK;
+}
+
+// The controller's initial state on buffer set B: multipliers cleared, the
+// FP16 shadow at scale sc, x = (r0, c0)/sc.
+static int init_state(meb_ctx* ctx, Buffers& B, int64_t m, int d, const meb_params& P, double sc,
+                      double r0) {
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(B.slot, 0xff, sizeof(int) * (size_t)m, s));
+  CK(prepare_pass(B, d));
+  CK(prepare_newton(d));
+  if (B.use_x16) CK(launch_shadow16(B, m, d, 1.0 / sc, s));
+  state_defaults(*ctx->h_st, m, d, P, sc, (d <= P.dense_max_d && d + 1 <= kMaxDenseN) ? 1 : 0);
+  ctx->h_st->sh_s = sc;
+  ctx->h_st->sh_inv_s = 1.0 / sc;
+  ctx->h_st->rt_abs = r0;   // initial radius; k_state_init scales it
+  CK(cudaMemcpyAsync(B.st, ctx->h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  CK(launch_state_init(B, d, s));
+  return MEB_OK;
+}
+
+// The controller ticks on buffer set B until the controller stops (status in
+// ctx->h_st afterwards): graph batches, a while-node graph, or host launches
+// (the CG path and MEB_OPT_TICK_LOOP = 1).
+static int run_ticks(meb_ctx* ctx, Buffers& B, const double* C, const double* R, int64_t m,
+                     int d, const meb_params& P) {
+  cudaStream_t s = ctx->stream;
+  const bool dense = (d <= P.dense_max_d && d + 1 <= kMaxDenseN);
+  ctx->prof_screens = 0;
+  // per ball: the shadow row (FP16: 16 bytes per 8 coordinates; FP32: 16
+  // bytes per 4 coordinates), its error bound, the FP32 radius and the slot
+  const int64_t d4 = (d + 3) / 4;
+  const int64_t pass_bytes = B.fp64_all ? m * 8   // the slot read and the list written
+                                         : m * (B.use_x16 ? 16 * ((d4 + 1) / 2) + 12 : 16 * d4 + 12);
+  const int64_t max_ticks = tick_cap(P);
+  int rc;
+  if (dense && ctx->loop_mode != 1 && !(ctx->profiling && ctx->loop_mode == 2)) {
+    // device-resident ticks: graph launches, one status read per kUnrollTicks ticks
+    meb_ctx::TickGraph* g = nullptr;
+    rc = solve_graph(ctx, B, C, R, m, d, &g);
+    if (rc) return rc;
+    const int64_t before = B.launches;
+    if (ctx->loop_mode == 2) {
+      ctx->h_st->max_ticks = max_ticks < 20000 ? max_ticks : 20000;
+      CK(cudaMemcpyAsync(&B.st->max_ticks, &ctx->h_st->max_ticks, sizeof(int64_t),
+                         cudaMemcpyHostToDevice, s));
+      CK(cudaGraphLaunch(g->gexec, s));
+      rc = read_state(ctx, B);
+      if (rc) return rc;
+      B.launches = before + ctx->h_st->ticks * (tick_launches(d) + 1);
+      if (ctx->h_st->status == kStatusTickCap)
+        return fail(ctx, MEB_ECUDA, "controller did not terminate");
+    } else {
+      int64_t ticks = 0;
+      for (;;) {
+        if (ctx->profiling)
+          CK(cudaMemsetAsync(B.st->screen_log, 0, sizeof(B.st->screen_log), s));
+        CK(cudaGraphLaunch(g->gexec, s));
+        ticks += kUnrollTicks;
+        rc = read_state(ctx, B);
+        if (rc) return rc;
+        if (ctx->profiling) {
+          for (int t = 0; t < kUnrollTicks; t++) {
+            if (!ctx->h_st->screen_log[t]) continue;
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ctx->gev[2 * t], ctx->gev[2 * t + 1]));
+            ctx->stats.pass_ms += ms;
+            ctx->stats.pass_launches += 1;
+            ctx->stats.pass_balls += m;
+            ctx->stats.pass_bytes += pass_bytes;
+          }
+        }
+        if (ctx->h_st->status != 0) break;
+        if (ticks > max_ticks) return fail(ctx, MEB_ECUDA, "controller did not terminate");
+      }
+      B.launches = before + ticks * tick_launches(d);
+    }
+  } else {
+    int64_t ticks = 0;
+    for (;;) {
+      CK(launch_pass(C, R, B, m, d, s, ctx->profiling ? ctx->ev[0] : nullptr,
+                     ctx->profiling ? ctx->ev[1] : nullptr));
+      CK(launch_tick_control(B, m, d, s));
+      rc = read_state(ctx, B);
+      if (rc) return rc;
+      if (ctx->profiling && ctx->h_st->screens > ctx->prof_screens) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+        ctx->stats.pass_ms += ms;
+        ctx->stats.pass_launches += 1;
+        ctx->stats.pass_balls += m;
+        ctx->stats.pass_bytes += pass_bytes;
+        ctx->stats.pass_fp64_rows += (int64_t)ctx->h_st->last[P_N64];
+      }
+      ctx->prof_screens = ctx->h_st->screens;
+      if (ctx->h_st->status != 0) break;
+      if (ctx->h_st->action == ACT_NEWTON) {
+        if (dense) {
+          CK(launch_newton_dense(B, d, s));
+        } else {
+          CK(launch_cg_setup(B, d, s));
+          for (int round = 0; round <= P.max_cg / 4 + 1; round++) {
+            for (int k = 0; k < 4; k++) CK(launch_cg_iter(B, d, s));
+            rc = read_state(ctx, B);
+            if (rc) return rc;
+            if (ctx->h_st->cg_done || ctx->h_st->status != 0 || ctx->h_st->action != ACT_NEWTON) break;
+          }
+          CK(launch_cg_finish(B, d, s));
+        }
+      }
+      CK(launch_mult_update(C, B, m, d, s));
+      if (++ticks > max_ticks) return fail(ctx, MEB_ECUDA, "controller did not terminate");
+    }
+  }
+  if (ctx->h_st->status == kStatusWaitTimeout)
+    return fail(ctx, MEB_ETIMEOUT, "a device wait timed out (a bulk copy did not complete)");
+  return MEB_OK;
+}
+
+// The final point, the radius lift (max-type value at c over all m balls,
+// Sec. 4.2) and the active set, on the full instance's buffers B.  Fills
+// info's radius and active fields; the active list stays in B.viol.
+static int finish_solve(meb_ctx* ctx, Buffers& Bx, Buffers& B, const double* C, const double* R,
+                        int64_t m, int d, const meb_params& P, double* dcout, double* r_alm_out,
+                        double* r_out_out, int64_t* n_active_out) {
+  cudaStream_t s = ctx->stream;
+  double* d_ralm = ctx->d_scal + 1;
+  CK(launch_final_point(Bx, d, dcout, d_ralm, s));
+  CK(launch_feas_cert(C, R, m, d, dcout, 0.0, INFINITY, 2, 1, B, ctx->d_scal + 2, ctx->d_i64 + 2,
+                      ctx->d_i64 + 3, s));
+  CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double r_alm = ctx->h_scal[1];
+  const double r_out = ctx->h_scal[2];
+  CK(launch_feas_cert(C, R, m, d, dcout, r_out, P.active_theta * r_out, 1, 0, B, nullptr, nullptr,
+                      ctx->d_i64 + 5, s, /*reuse_bounds=*/true));
+  CK(cudaMemcpyAsync(ctx->h_scal + 8, ctx->d_i64 + 5, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  memcpy(n_active_out, ctx->h_scal + 8, sizeof(int64_t));
+  *r_alm_out = r_alm;
+  *r_out_out = r_out;
+  return MEB_OK;
+}
+
+static void fill_info(meb_info* info, const DevState& S, double sc, double r_alm, double r_out,
+                      int64_t n_active) {
+  if (!info) return;
+  info->r = r_out;
+  info->r_alm = r_alm;
+  info->kkt[0] = S.kkt[0];
+  info->kkt[1] = S.kkt[1];
+  info->kkt[2] = S.kkt[2] * sc;
+  info->kkt[3] = S.kkt[3];
+  info->kkt[4] = S.kkt[4] * sc;
+  info->kkt_max = S.kkt_max;
+  info->delta_max = r_out - r_alm;
+  info->scale = sc;
+  info->n_active = n_active;
+  info->fp64_rows = S.n64_total;
+  info->outer_iters = S.outer;
+  info->ssn_iters = S.tot_ssn;
+  info->cg_iters = S.tot_cg;
+  info->passes = S.tot_passes;
+  info->backtracks = S.tot_bt;
+  info->status = S.status == 1 ? 0 : 1;
+  info->newton_inverses = S.gj_inverses;
+  info->newton_fp64 = S.fp64_solves;
+}
+
+static int solve_mixed(meb_ctx* ctx, const double* C, const double* R, int64_t m, int d,
+                       const meb_params& P, double sc, double r0, double* dcout, meb_info* info,
+                       int64_t* n_active, DevState* Sout);
 
 extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radii, int64_t m,
                          int32_t d, double tol, const meb_params* params, unsigned flags,
@@ -564,22 +785,14 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   B.use_x16 = ctx->screen_mode == MEB_SCREEN_FP16 || ctx->screen_mode == MEB_SCREEN_FP16_BULK;
   B.bulk = ctx->screen_mode == MEB_SCREEN_FP16_BULK;
   B.fp64_all = ctx->screen_mode == MEB_SCREEN_FP64;
+  B.lowp = false;
   B.wait_cycles = ctx->wait_cycles;
-  CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
   if (info) memset(info, 0, sizeof(*info));
 
-  // FP32 shadow (origin c_0) and the mean centre c0; r0 = max_i ||c0 - c_i|| + r_i
-  // (the shadow also checks the input; the plain FP64 mode reads it no further)
-  CK(launch_shadow(C, R, m, d, B, B.vec.o, B.vec.c0, ctx->d_flags, s));
-  CK(launch_feas_cert(C, R, m, d, B.vec.c0, 0.0, INFINITY, 2, 1, B, ctx->d_scal, ctx->d_i64,
-                      ctx->d_i64 + 1, s));
-  CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  int bad;
-  memcpy(&bad, ctx->h_scal + 1, sizeof(int));
-  if (bad) return fail(ctx, MEB_EINVAL, "non-finite centre or radius, or negative radius");
-  const double r0 = ctx->h_scal[0];
+  // the input check, the FP32 shadow and r0 at the mean centre
+  double r0 = 0.0;
+  rc = setup_instance(ctx, B, C, R, m, d, &r0);
+  if (rc) return rc;
   void* dcout = nullptr;
   if (flags & MEB_PTR_DEVICE) dcout = c_out;
   else { rc = pool(ctx, POOL_COUT, sizeof(double) * (size_t)d, &dcout); if (rc) return rc; }
@@ -599,6 +812,7 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
     }
     if (info) {
       info->r = r; info->r_alm = r; info->scale = 1.0; info->n_active = na; info->status = 0;
+      info->n_reduced = m;
     }
     ctx->mult_kind = (m == 1) ? 2 : 3;
     ctx->mult_n = m;
@@ -611,155 +825,36 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   frexp(r0, &ex);
   double sc = ldexp(1.0, ex);
   if (sc / 2.0 >= r0) sc /= 2.0;
-  CK(cudaMemsetAsync(B.slot, 0xff, sizeof(int) * (size_t)m, s));
-  CK(prepare_pass(B, d));
-  CK(prepare_newton(d));
-  if (B.use_x16) CK(launch_shadow16(B, m, d, 1.0 / sc, s));
-  state_defaults(*ctx->h_st, m, d, P, sc, (d <= P.dense_max_d && d + 1 <= kMaxDenseN) ? 1 : 0);
-  ctx->h_st->sh_s = sc;
-  ctx->h_st->sh_inv_s = 1.0 / sc;
-  ctx->h_st->rt_abs = r0;   // initial radius; k_state_init scales it
-  CK(cudaMemcpyAsync(B.st, ctx->h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
-  CK(launch_state_init(B, d, s));
-  const bool dense = ctx->h_st->dense;
-  ctx->prof_screens = 0;
-  // per ball: the shadow row (FP16: 16 bytes per 8 coordinates; FP32: 16
-  // bytes per 4 coordinates), its error bound, the FP32 radius and the slot
-  const int64_t d4 = (d + 3) / 4;
-  const int64_t pass_bytes = B.fp64_all ? m * 8   // the slot read and the list written
-                                         : m * (B.use_x16 ? 16 * ((d4 + 1) / 2) + 12 : 16 * d4 + 12);
-
-  const int64_t max_ticks = tick_cap(P);
-  if (dense && ctx->loop_mode != 1 && !(ctx->profiling && ctx->loop_mode == 2)) {
-    // device-resident ticks: graph launches, one status read per kUnrollTicks ticks
-    rc = solve_graph(ctx, C, R, m, d);
+  int64_t n_active = 0;
+  DevState S;
+  if (P.mixed) {
+    // Sec. 4.2: low-precision run, screening, FP64 on the reduced set, re-adds
+    rc = solve_mixed(ctx, C, R, m, d, P, sc, r0, (double*)dcout, info, &n_active, &S);
     if (rc) return rc;
-    const int64_t before = B.launches;
-    if (ctx->loop_mode == 2) {
-      ctx->h_st->max_ticks = max_ticks < 20000 ? max_ticks : 20000;
-      CK(cudaMemcpyAsync(&B.st->max_ticks, &ctx->h_st->max_ticks, sizeof(int64_t),
-                         cudaMemcpyHostToDevice, s));
-      CK(cudaGraphLaunch(ctx->gexec, s));
-      rc = read_state(ctx);
-      if (rc) return rc;
-      B.launches = before + ctx->h_st->ticks * (tick_launches(d) + 1);
-      if (ctx->h_st->status == kStatusTickCap)
-        return fail(ctx, MEB_ECUDA, "controller did not terminate");
-    } else {
-      int64_t ticks = 0;
-      for (;;) {
-        if (ctx->profiling)
-          CK(cudaMemsetAsync(B.st->screen_log, 0, sizeof(B.st->screen_log), s));
-        CK(cudaGraphLaunch(ctx->gexec, s));
-        ticks += kUnrollTicks;
-        rc = read_state(ctx);
-        if (rc) return rc;
-        if (ctx->profiling) {
-          for (int t = 0; t < kUnrollTicks; t++) {
-            if (!ctx->h_st->screen_log[t]) continue;
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, ctx->gev[2 * t], ctx->gev[2 * t + 1]));
-            ctx->stats.pass_ms += ms;
-            ctx->stats.pass_launches += 1;
-            ctx->stats.pass_balls += m;
-            ctx->stats.pass_bytes += pass_bytes;
-          }
-        }
-        if (ctx->h_st->status != 0) break;
-        if (ticks > max_ticks) return fail(ctx, MEB_ECUDA, "controller did not terminate");
-      }
-      B.launches = before + ticks * tick_launches(d);
-    }
   } else {
-    int64_t ticks = 0;
-    for (;;) {
-      CK(launch_pass(C, R, B, m, d, s, ctx->profiling ? ctx->ev[0] : nullptr,
-                     ctx->profiling ? ctx->ev[1] : nullptr));
-      CK(launch_tick_control(B, m, d, s));
-      rc = read_state(ctx);
-      if (rc) return rc;
-      if (ctx->profiling && ctx->h_st->screens > ctx->prof_screens) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
-        ctx->stats.pass_ms += ms;
-        ctx->stats.pass_launches += 1;
-        ctx->stats.pass_balls += m;
-        ctx->stats.pass_bytes += pass_bytes;
-        ctx->stats.pass_fp64_rows += (int64_t)ctx->h_st->last[P_N64];
-      }
-      ctx->prof_screens = ctx->h_st->screens;
-      if (ctx->h_st->status != 0) break;
-      if (ctx->h_st->action == ACT_NEWTON) {
-        if (dense) {
-          CK(launch_newton_dense(B, d, s));
-        } else {
-          CK(launch_cg_setup(B, d, s));
-          for (int round = 0; round <= P.max_cg / 4 + 1; round++) {
-            for (int k = 0; k < 4; k++) CK(launch_cg_iter(B, d, s));
-            rc = read_state(ctx);
-            if (rc) return rc;
-            if (ctx->h_st->cg_done || ctx->h_st->status != 0 || ctx->h_st->action != ACT_NEWTON) break;
-          }
-          CK(launch_cg_finish(B, d, s));
-        }
-      }
-      CK(launch_mult_update(C, B, m, d, s));
-      if (++ticks > max_ticks) return fail(ctx, MEB_ECUDA, "controller did not terminate");
-    }
+    rc = init_state(ctx, B, m, d, P, sc, r0);
+    if (rc) return rc;
+    rc = run_ticks(ctx, B, C, R, m, d, P);
+    if (rc) return rc;
+    S = *ctx->h_st;
+    ctx->mult_kind = 1;
+    ctx->mult_n = S.nS;
+    ctx->mult_m = m;
+    ctx->mult_d = d;
+    double r_alm, r_out;
+    rc = finish_solve(ctx, B, B, C, R, m, d, P, (double*)dcout, &r_alm, &r_out, &n_active);
+    if (rc) return rc;
+    fill_info(info, S, sc, r_alm, r_out, n_active);
+    if (info) info->n_reduced = m;
   }
-  const DevState S = *ctx->h_st;
-  if (S.status == kStatusWaitTimeout)
-    return fail(ctx, MEB_ETIMEOUT, "a device wait timed out (a bulk copy did not complete)");
-  ctx->mult_kind = 1;
-  ctx->mult_n = S.nS;
-  ctx->mult_m = m;
-  ctx->mult_d = d;
-
-  // final point, radius lift (max-type value at c) and active set
-  double* d_ralm = ctx->d_scal + 1;
-  CK(launch_final_point(B, d, (double*)dcout, d_ralm, s));
-  CK(launch_feas_cert(C, R, m, d, (const double*)dcout, 0.0, INFINITY, 2, 1, B, ctx->d_scal + 2,
-                      ctx->d_i64 + 2, ctx->d_i64 + 3, s));
-  CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  const double r_alm = ctx->h_scal[1];
-  const double r_out = ctx->h_scal[2];
-  CK(launch_feas_cert(C, R, m, d, (const double*)dcout, r_out, P.active_theta * r_out, 1, 0, B,
-                      nullptr, nullptr, ctx->d_i64 + 5, s, /*reuse_bounds=*/true));
-  CK(cudaMemcpyAsync(ctx->h_scal + 8, ctx->d_i64 + 5, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   if (!(flags & MEB_PTR_DEVICE))
     CK(cudaMemcpyAsync(c_out, dcout, sizeof(double) * d, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  int64_t n_active;
-  memcpy(&n_active, ctx->h_scal + 8, sizeof(int64_t));
   const int64_t ncp = n_active < active_cap ? n_active : active_cap;
   if (ncp > 0) {
     rc = copy_out(ctx, active_idx, B.viol, sizeof(int64_t) * (size_t)ncp, flags);
     if (rc) return rc;
-    CK(cudaStreamSynchronize(s));
   }
-  if (info) {
-    info->r = r_out;
-    info->r_alm = r_alm;
-    info->kkt[0] = S.kkt[0];
-    info->kkt[1] = S.kkt[1];
-    info->kkt[2] = S.kkt[2] * sc;
-    info->kkt[3] = S.kkt[3];
-    info->kkt[4] = S.kkt[4] * sc;
-    info->kkt_max = S.kkt_max;
-    info->delta_max = r_out - r_alm;
-    info->scale = sc;
-    info->n_active = n_active;
-    info->fp64_rows = S.n64_total;
-    info->outer_iters = S.outer;
-    info->ssn_iters = S.tot_ssn;
-    info->cg_iters = S.tot_cg;
-    info->passes = S.tot_passes;
-    info->backtracks = S.tot_bt;
-    info->status = S.status == 1 ? 0 : 1;
-    info->newton_inverses = S.gj_inverses;
-    info->newton_fp64 = S.fp64_solves;
-  }
+  CK(cudaStreamSynchronize(s));
   return S.status == 1 ? MEB_OK : fail(ctx, MEB_ENOTCONV, "iteration cap reached");
 }
 
@@ -848,7 +943,7 @@ extern "C" int meb_eval_alm(meb_ctx* ctx, const double* centers, const double* r
   if (Hq && !(flags & MEB_PTR_DEVICE) && (rc = copy_out(ctx, Hq, dHq, n1b, flags))) return rc;
   if (H && !(flags & MEB_PTR_DEVICE) && (rc = copy_out(ctx, H, dH, n1b * (d + 1), flags))) return rc;
   CK(cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
-  rc = read_state(ctx);
+  rc = read_state(ctx, ctx->B);
   if (rc) return rc;
   int bad;
   memcpy(&bad, ctx->h_scal + 1, sizeof(int));
@@ -928,7 +1023,8 @@ extern "C" int meb_get_multipliers(meb_ctx* ctx, unsigned flags, int64_t* idx, d
   const int64_t k = n < cap ? n : cap;
   if (k == 0) return MEB_OK;
   const bool dev = (flags & MEB_PTR_DEVICE) != 0;
-  if (ctx->mult_kind == 1) {
+  if (ctx->mult_kind == 1 || ctx->mult_kind == 4) {
+    Buffers& Bs = ctx->mult_kind == 4 ? ctx->Bred : ctx->B;
     int64_t* didx;
     double *du, *dv;
     int rc;
@@ -938,7 +1034,8 @@ extern "C" int meb_get_multipliers(meb_ctx* ctx, unsigned flags, int64_t* idx, d
       if ((rc = pool(ctx, POOL_UP, sizeof(double) * (size_t)k, (void**)&du))) return rc;
       if ((rc = pool(ctx, POOL_VP, sizeof(double) * (size_t)k * d, (void**)&dv))) return rc;
     }
-    CK(launch_mult_out(ctx->B, d, didx, du, dv, k, s));
+    CK(launch_mult_out(Bs, d, didx, du, dv, k, s));
+    if (ctx->mult_kind == 4) CK(launch_map_idx(didx, k, ctx->mult_map, s));
     if (!dev) {
       CK(cudaMemcpyAsync(idx, didx, sizeof(int64_t) * (size_t)k, cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(u, du, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost, s));
@@ -1253,5 +1350,193 @@ extern "C" int meb_footprint(int64_t m, int32_t d, int32_t path, int64_t* bytes)
   if (path == 1 && d > kBatchMaxD) return MEB_EINVAL;
   *bytes = path == 0 ? (int64_t)solve_layout(nullptr, nullptr, m, d)
                      : (int64_t)batch_slot_layout(nullptr, nullptr, m, d, batch_support_cap(m, d));
+  return MEB_OK;
+}
+
+// ===========================================================================
+// The mixed-precision reduction pipeline of Sec. 4.2.
+
+// Buffers of the reduced instance (n balls): re-laid out in place when the
+// arena is large enough, else reallocated.
+static int ensure_red(meb_ctx* ctx, int64_t n, int d) {
+  const size_t bytes = solve_layout(nullptr, nullptr, n, d);
+  if (!ctx->red_arena || ctx->red_bytes < bytes) {
+    dev_free(ctx, ctx->red_arena);
+    ctx->red_arena = nullptr;
+    ctx->red_bytes = 0;
+    drop_graphs(ctx);
+    CK(dev_alloc(ctx, &ctx->red_arena, bytes));
+    ctx->red_bytes = bytes;
+  }
+  solve_layout(&ctx->Bred, (char*)ctx->red_arena, n, d);
+  const int n1 = d + 1, d4 = (d + 3) / 4;
+  const size_t nv = 20 * (size_t)((n1 + 8 + 1) / 2) * 2 + (size_t)(d4 * 4 + 8);
+  CK(cudaMemsetAsync(ctx->Bred.vec_store, 0, sizeof(double) * nv, ctx->stream));
+  return MEB_OK;
+}
+
+// Sorted union of two ascending index lists.
+static std::vector<int64_t> merge_sorted(const std::vector<int64_t>& a, const std::vector<int64_t>& b) {
+  std::vector<int64_t> out;
+  out.reserve(a.size() + b.size());
+  std::set_union(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(out));
+  return out;
+}
+
+// The warm start's source: the point x (scaled), the penalty, and the
+// multipliers of the last accepted point of buffer set Bs (map: its ball
+// indices in the full instance, or null when they already are), into the
+// warm pools.  Returns their count in *nw.
+static int save_warm(meb_ctx* ctx, Buffers& Bs, int d, const DevState& S, const int64_t* map,
+                     int64_t* nw, std::vector<int64_t>* host_idx) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = S.nS;
+  int64_t* widx;
+  double *wu, *wv, *wx;
+  int rc;
+  if ((rc = pool(ctx, POOL_WIDX, sizeof(int64_t) * (size_t)(n + 1), (void**)&widx))) return rc;
+  if ((rc = pool(ctx, POOL_WU, sizeof(double) * (size_t)(n + 1), (void**)&wu))) return rc;
+  if ((rc = pool(ctx, POOL_WV, sizeof(double) * (size_t)(n + 1) * d, (void**)&wv))) return rc;
+  if ((rc = pool(ctx, POOL_WX, sizeof(double) * (size_t)(d + 1), (void**)&wx))) return rc;
+  if (n > 0) {
+    CK(launch_mult_out(Bs, d, widx, wu, wv, n, s));
+    if (map) CK(launch_map_idx(widx, n, map, s));
+  }
+  CK(cudaMemcpyAsync(wx, Bs.vec.x, sizeof(double) * (size_t)(d + 1), cudaMemcpyDeviceToDevice, s));
+  host_idx->resize(n);
+  if (n > 0)
+    CK(cudaMemcpyAsync(host_idx->data(), widx, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *nw = n;
+  return MEB_OK;
+}
+
+static int solve_mixed(meb_ctx* ctx, const double* C, const double* R, int64_t m, int d,
+                       const meb_params& P, double sc, double r0, double* dcout, meb_info* info,
+                       int64_t* n_active, DevState* Sout) {
+  cudaStream_t s = ctx->stream;
+  Buffers& B = ctx->B;
+  int rc;
+  // 1. the low-precision ripALM on all balls, to tol_lp
+  meb_params P1 = P;
+  P1.tol = P.tol_lp;
+  B.lowp = true;
+  rc = init_state(ctx, B, m, d, P1, sc, r0);
+  if (rc == MEB_OK) rc = run_ticks(ctx, B, C, R, m, d, P1);
+  B.lowp = false;
+  if (rc) return rc;
+  const DevState S1 = *ctx->h_st;
+  // 2. screening at the low-precision point: I_red = {slack <= tol_red r_hat}
+  //    (certified bounds, FP64 where they do not decide) plus every ball with
+  //    a multiplier
+  CK(launch_final_point(B, d, dcout, ctx->d_scal + 1, s));
+  CK(cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double r_hat = ctx->h_scal[1];
+  const double fac = P.tol_red > 0 ? P.tol_red : std::max(10.0 * S1.kkt_max, 1e-3);
+  CK(launch_feas_cert(C, R, m, d, dcout, r_hat, fac * r_hat, 1, 0, B, nullptr, nullptr,
+                      ctx->d_i64 + 6, s));
+  int64_t n_scr = 0;
+  CK(cudaMemcpyAsync(&n_scr, ctx->d_i64 + 6, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<int64_t> scr(n_scr);
+  if (n_scr > 0)
+    CK(cudaMemcpyAsync(scr.data(), B.viol, sizeof(int64_t) * (size_t)n_scr, cudaMemcpyDeviceToHost, s));
+  int64_t nw = 0;
+  std::vector<int64_t> wsup;
+  rc = save_warm(ctx, B, d, S1, nullptr, &nw, &wsup);
+  if (rc) return rc;
+  double sigma = S1.sigma;
+  std::vector<int64_t> ired = merge_sorted(scr, wsup);
+  // 3.-5. the FP64 ripALM on I_red, warm-started; the full feasibility pass;
+  //        violated balls join I_red and the reduced solve runs again
+  const double eps_feas = 2.0 * P.tol * sc;
+  DevState S2{};
+  int rounds = 0;
+  int passes = S1.tot_passes, outer = S1.outer, ssn = S1.tot_ssn, cg = S1.tot_cg, bt = S1.tot_bt;
+  int64_t fp64_rows = S1.n64_total;
+  int64_t* dired = nullptr;
+  for (;;) {
+    const int64_t nred = (int64_t)ired.size();
+    if ((rc = pool(ctx, POOL_RED_IDX, sizeof(int64_t) * (size_t)nred, (void**)&dired))) return rc;
+    double *Cr, *Rr;
+    if ((rc = pool(ctx, POOL_RED_C, sizeof(double) * (size_t)nred * d, (void**)&Cr))) return rc;
+    if ((rc = pool(ctx, POOL_RED_R, sizeof(double) * (size_t)nred, (void**)&Rr))) return rc;
+    CK(cudaMemcpyAsync(dired, ired.data(), sizeof(int64_t) * (size_t)nred, cudaMemcpyHostToDevice, s));
+    CK(launch_gather_rows(C, R, dired, nred, d, Cr, Rr, s));
+    rc = ensure_red(ctx, nred, d);
+    if (rc) return rc;
+    Buffers& Br = ctx->Bred;
+    Br.C_in = Cr;
+    Br.use_x16 = B.use_x16;
+    Br.bulk = B.bulk;
+    Br.fp64_all = B.fp64_all;
+    Br.lowp = false;
+    Br.wait_cycles = B.wait_cycles;
+    CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
+    CK(launch_shadow(Cr, Rr, nred, d, Br, Br.vec.o, Br.vec.c0, ctx->d_flags, s));
+    rc = init_state(ctx, Br, nred, d, P, sc, r0);
+    if (rc) return rc;
+    int64_t* widx;
+    double *wu, *wv, *wx;
+    pool(ctx, POOL_WIDX, 0, (void**)&widx);
+    pool(ctx, POOL_WU, 0, (void**)&wu);
+    pool(ctx, POOL_WV, 0, (void**)&wv);
+    pool(ctx, POOL_WX, 0, (void**)&wx);
+    CK(launch_warm_start(Br, d, wx, sigma, widx, wu, wv, nw, dired, nred, s));
+    rc = run_ticks(ctx, Br, Cr, Rr, nred, d, P);
+    if (rc) return rc;
+    S2 = *ctx->h_st;
+    passes += S2.tot_passes;
+    outer += S2.outer;
+    ssn += S2.tot_ssn;
+    cg += S2.tot_cg;
+    bt += S2.tot_bt;
+    fp64_rows += S2.n64_total;
+    // the reduced solution against every ball
+    CK(launch_final_point(Br, d, dcout, ctx->d_scal + 1, s));
+    CK(cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double r_bar = ctx->h_scal[1];
+    CK(launch_feas_cert(C, R, m, d, dcout, r_bar, eps_feas, 0, 1, B, ctx->d_scal + 2, ctx->d_i64,
+                        ctx->d_i64 + 1, s));
+    int64_t nv = 0;
+    CK(cudaMemcpyAsync(&nv, ctx->d_i64 + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int64_t> viol(nv), add;
+    if (nv > 0) {
+      CK(cudaMemcpyAsync(viol.data(), B.viol, sizeof(int64_t) * (size_t)nv, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      std::set_difference(viol.begin(), viol.end(), ired.begin(), ired.end(), std::back_inserter(add));
+    }
+    if (add.empty() || rounds >= P.max_readd || S2.status != 1) break;
+    rc = save_warm(ctx, Br, d, S2, dired, &nw, &wsup);
+    if (rc) return rc;
+    sigma = S2.sigma;
+    ired = merge_sorted(ired, add);
+    rounds++;
+  }
+  // the radius lift and the active set over all balls, at the reduced solution
+  double r_alm, r_out;
+  rc = finish_solve(ctx, ctx->Bred, B, C, R, m, d, P, dcout, &r_alm, &r_out, n_active);
+  if (rc) return rc;
+  ctx->mult_kind = 4;
+  ctx->mult_map = dired;
+  ctx->mult_n = S2.nS;
+  ctx->mult_m = m;
+  ctx->mult_d = d;
+  fill_info(info, S2, sc, r_alm, r_out, *n_active);
+  if (info) {
+    info->passes = passes;
+    info->outer_iters = outer;
+    info->ssn_iters = ssn;
+    info->cg_iters = cg;
+    info->backtracks = bt;
+    info->fp64_rows = fp64_rows;
+    info->n_reduced = (int64_t)ired.size();
+    info->readd_rounds = rounds;
+    info->lowp_passes = S1.tot_passes;
+  }
+  *Sout = S2;
   return MEB_OK;
 }

@@ -112,6 +112,11 @@ __device__ double block_max(double v, double* sh) {
   return t;
 }
 
+// Element j of ball i of the FP32 shadow (layout [ceil(d/4)][m_pad] float4).
+__device__ __forceinline__ float x32_at(const float4* X32, int64_t m_pad, int64_t i, int j) {
+  return reinterpret_cast<const float*>(X32)[(((int64_t)(j >> 2)) * m_pad + i) * 4 + (j & 3)];
+}
+
 // Distance to Q of a point (a, b) with ||b|| = n (closed form of ||z - Pi(z)||).
 __device__ __forceinline__ double soc_dist_an(double a, double n) {
   if (n <= a) return 0.0;

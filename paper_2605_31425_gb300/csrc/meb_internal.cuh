@@ -143,6 +143,8 @@ struct Buffers {
   bool use_x16;         // host side: the screens read X16
   bool bulk;            // host side: FP16 screens through the bulk-copy pipeline
   bool fp64_all;        // host side: no shadow is read; every ball goes through the FP64 rows
+  bool lowp;            // host side: rows, support rows and multiplier rows in FP32 from the
+                        // FP32 shadow (the low-precision run of the mixed-precision pipeline)
   long long wait_cycles;   // bound of the bulk-copy screen's waits (SM clock cycles; 0: one test)
   float* R32;           // [m_pad]
   // multipliers (double buffered)
@@ -344,6 +346,12 @@ cudaError_t launch_eval_prepare(Buffers& B, const double* x, const double* xbar,
 cudaError_t launch_final_point(Buffers& B, int d, double* c_out, double* r_alm, cudaStream_t s);
 cudaError_t launch_mult_out(Buffers& B, int d, int64_t* idx, double* u, double* v, int64_t cap,
                             cudaStream_t s);
+cudaError_t launch_gather_rows(const double* C, const double* R, const int64_t* idx, int64_t n,
+                               int d, double* Cr, double* Rr, cudaStream_t s);
+cudaError_t launch_warm_start(Buffers& B, int d, const double* wx, double sigma,
+                              const int64_t* widx, const double* wu, const double* wv, int64_t nw,
+                              const int64_t* ired, int64_t nred, cudaStream_t s);
+cudaError_t launch_map_idx(int64_t* idx, int64_t n, const int64_t* map, cudaStream_t s);
 cudaError_t launch_loop_cond(Buffers& B, cudaGraphConditionalHandle h, cudaStream_t s);
 
 }  // namespace meb

@@ -74,11 +74,12 @@ __global__ void __launch_bounds__(kPassThreads, 4) k_screen(PassArgs A, Buffers 
   if (last_block_ticket(&st->ctr_screen)) early_body(B, A.d, gridDim.x);
 }
 
+template <bool LOWP>
 __global__ void __launch_bounds__(kPassThreads) k_rows64(PassArgs A, Buffers B) {
   pdl_wait_and_release();
   DevState* st = A.st;
   if (!rows_gate(st)) return;
-  rows_block(A, blockIdx.x);
+  rows_block<LOWP>(A, blockIdx.x);
   if (last_block_ticket(&st->ctr_rows)) control_a_body(B, A.d, gridDim.x);
 }
 
@@ -349,29 +350,35 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
   if (ev1) cudaEventRecordWithFlags(ev1, s, evf);
   const size_t sh2 = 8 * (size_t)d;
   if (sh2 > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_rows64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh2);
+    e = cudaFuncSetAttribute(k_rows64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh2);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_rows64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh2);
     if (e != cudaSuccess) return e;
   }
-  e = launch_pdl(k_rows64, dim3(nb), dim3(kPassThreads), sh2, s, A, B);
+  e = B.lowp ? launch_pdl(k_rows64<true>, dim3(nb), dim3(kPassThreads), sh2, s, A, B)
+             : launch_pdl(k_rows64<false>, dim3(nb), dim3(kPassThreads), sh2, s, A, B);
   if (e != cudaSuccess) return e;
   B.launches += 2;
   return cudaGetLastError();
 }
 
+template <bool LOWP>
 __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buffers B, int d,
                                               int npb, int64_t seg) {
   pdl_wait_and_release();
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_GRAD) return;
-  svec_block(C, B, d, npb, seg, blockIdx.x, kSvecBlocks);
+  svec_block<LOWP>(C, B, d, npb, seg, blockIdx.x, kSvecBlocks);
   if (last_block_ticket(&st->ctr_svec)) control_b_body(B, d);
 }
 
 cudaError_t launch_support_rows(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s) {
   int tpb;
   const int nb = pass_blocks(m, d, screen_variant(B, d), &tpb);
-  cudaError_t e = launch_pdl(k_svec, dim3(kSvecBlocks), dim3(256), 0, s, C, B, d, nb,
-                             (int64_t)tpb * kPassThreads);
+  cudaError_t e = B.lowp ? launch_pdl(k_svec<true>, dim3(kSvecBlocks), dim3(256), 0, s, C, B, d,
+                                      nb, (int64_t)tpb * kPassThreads)
+                        : launch_pdl(k_svec<false>, dim3(kSvecBlocks), dim3(256), 0, s, C, B, d,
+                                      nb, (int64_t)tpb * kPassThreads);
   if (e != cudaSuccess) return e;
   B.launches += 1;
   return cudaGetLastError();

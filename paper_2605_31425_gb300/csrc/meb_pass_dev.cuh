@@ -8,6 +8,8 @@
 #pragma once
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "meb_control.cuh"
 #include "meb_tma.cuh"
 
@@ -403,7 +405,20 @@ __device__ __forceinline__ bool screen_gate(const DevState* st) {
 }
 
 // The FP64 rows of pass block `bid`: its list of uncertain balls.
+// LOWP: the low-precision run of the mixed-precision pipeline (Sec. 4.2):
+// the rows come from the FP32 shadow (x32 = c_i - o, radii r32, the query
+// y32 = trunc32(c - o), fl32(r)) and every per-ball operation and per-lane sum
+// is FP32; the block records stay FP64 (their sums are the controller's).
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(MEB_FULLMASK, v, o);
+  return v;
+}
+
+template <bool LOWP = false>
 __device__ __forceinline__ void rows_block(const PassArgs& A, int bid) {
+  using T = typename std::conditional<LOWP, float, double>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const DevState* st = A.st;
   const int n_b = A.unc_cnt[bid];
@@ -415,34 +430,39 @@ __device__ __forceinline__ void rows_block(const PassArgs& A, int bid) {
     return;
   }
   const int d = A.d;
-  double* s_ct = reinterpret_cast<double*>(smem_raw);   // d
+  double* s_ct = reinterpret_cast<double*>(smem_raw);   // d (FP64 rows)
+  float* s_yf = reinterpret_cast<float*>(smem_raw);     // d (LOWP: y32)
   __shared__ unsigned char s_cf[kPassThreads];
   __shared__ unsigned char s_cc[kPassThreads];
   __shared__ double s_ca[kPassThreads], s_cn[kPassThreads], s_cu[kPassThreads];
   __shared__ int s_wc[kPassWarps];
   __shared__ double s_wp[kPassWarps][P_NREC];
   __shared__ int s_wn[kPassWarps][P_NCNT];
-  for (int j = threadIdx.x; j < d; j += kPassThreads) s_ct[j] = A.ct[j];
+  for (int j = threadIdx.x; j < d; j += kPassThreads) {
+    if (LOWP) s_yf[j] = A.y32[j];
+    else s_ct[j] = A.ct[j];
+  }
   const int cur = st->sup_cur;
   const int nsup = st->nsup;
   const int* sidx = cur ? A.sup_idx1 : A.sup_idx0;
   const double* su = cur ? A.sup_u1 : A.sup_u0;
   const double* sv = cur ? A.sup_v1 : A.sup_v0;
-  const double inv_s = st->inv_s, sigma = st->sigma, inv_sigma = st->inv_sigma;
-  const double rt = st->rt_abs;
+  const T inv_s = (T)st->inv_s, sigma = (T)st->sigma, inv_sigma = (T)st->inv_sigma;
+  const T rt = LOWP ? (T)st->rq32 : (T)st->rt_abs;
+  const float* R32 = A.R32;
   __syncthreads();
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t base = (int64_t)bid * A.tiles_per_block * kPassThreads;
-  double acc[P_NREC];
+  T acc[P_NREC];
 #pragma unroll
-  for (int k = 0; k < P_NREC; k++) acc[k] = 0.0;
+  for (int k = 0; k < P_NREC; k++) acc[k] = (T)0;
   int cnt[P_NCNT] = {0, 0, 0};
   int ccount = 0;
   for (int c0 = 0; c0 < n_b; c0 += kPassThreads) {
     const int tot = min(kPassThreads, n_b - c0);
     // warp w takes the 32 chunk entries 32w .. 32w+31; lane q ends with entry q's sums
     const int e0 = 32 * w;
-    double mnn = 0.0, mpp = 0.0, mdv = 0.0, mvv = 0.0;
+    T mnn = 0, mpp = 0, mdv = 0, mvv = 0;
     const int my = e0 + lane;
     const bool valid = my < tot;
     const int64_t myii = valid ? (int64_t)A.unc_idx[base + c0 + my] : 0;
@@ -455,25 +475,27 @@ __device__ __forceinline__ void rows_block(const PassArgs& A, int bid) {
       const int64_t ii = __shfl_sync(MEB_FULLMASK, myii, q);
       const int sl = __shfl_sync(MEB_FULLMASK, mysl, q);
       const double* crow = A.C + ii * (int64_t)d;
-      double nn = 0.0, pp = 0.0, dv = 0.0, vv = 0.0;
+      T nn = 0, pp = 0, dv = 0, vv = 0;
       if (sl >= 0) {
         const double* vrow = sv + (int64_t)sl * d;
         for (int j = lane; j < d; j += 32) {
-          const double dl = (crow[j] - s_ct[j]) * inv_s;
-          const double v = vrow[j];
-          const double b = fma(v, inv_sigma, dl);
+          const T dl = LOWP ? (T)((x32_at(A.X32, A.m_pad, ii, j) - s_yf[j]) * (float)inv_s)
+                            : (T)((crow[j] - s_ct[j]) * (double)inv_s);
+          const T v = (T)vrow[j];
+          const T b = fma(v, inv_sigma, dl);
           nn = fma(b, b, nn);
           pp = fma(dl, dl, pp);
           dv = fma(dl, v, dv);
           vv = fma(v, v, vv);
         }
-        nn = warp_sum(nn); pp = warp_sum(pp); dv = warp_sum(dv); vv = warp_sum(vv);
+        nn = warp_sum_t(nn); pp = warp_sum_t(pp); dv = warp_sum_t(dv); vv = warp_sum_t(vv);
       } else {
         for (int j = lane; j < d; j += 32) {
-          const double dl = (crow[j] - s_ct[j]) * inv_s;
+          const T dl = LOWP ? (T)((x32_at(A.X32, A.m_pad, ii, j) - s_yf[j]) * (float)inv_s)
+                            : (T)((crow[j] - s_ct[j]) * (double)inv_s);
           nn = fma(dl, dl, nn);
         }
-        nn = warp_sum(nn);
+        nn = warp_sum_t(nn);
         pp = nn;
       }
       if (lane == q) { mnn = nn; mpp = pp; mdv = dv; mvv = vv; }
@@ -481,28 +503,29 @@ __device__ __forceinline__ void rows_block(const PassArgs& A, int bid) {
     if (valid) {
       const int sl = mysl;
       const int64_t ii = myii;
-      const double nn = mnn, pp = mpp, dv = mdv, vv = mvv;
-      const double uo = (sl >= 0) ? su[sl] : 0.0;
-      const double a = fma(uo, inv_sigma, (A.R[ii] - rt) * inv_s);
-      const double n = sqrt(nn);
+      const T nn = mnn, pp = mpp, dv = mdv, vv = mvv;
+      const T uo = (sl >= 0) ? (T)su[sl] : (T)0;
+      const T ri = LOWP ? (T)R32[ii] : (T)A.R[ii];
+      const T a = fma(uo, inv_sigma, (ri - rt) * inv_s);
+      const T n = sqrt(nn);
       int cs;
-      double pa, f, pi2;
-      if (n <= a) { cs = CASE_I; pa = a; f = 1.0; pi2 = a * a + nn; }
-      else if (n <= -a) { cs = CASE_Z; pa = 0.0; f = 0.0; pi2 = 0.0; }
-      else { cs = CASE_M; pa = 0.5 * (a + n); f = pa / n; pi2 = 2.0 * pa * pa; }
-      const double up = sigma * pa;
+      T pa, f, pi2;
+      if (n <= a) { cs = CASE_I; pa = a; f = 1; pi2 = a * a + nn; }
+      else if (n <= -a) { cs = CASE_Z; pa = 0; f = 0; pi2 = 0; }
+      else { cs = CASE_M; pa = (T)0.5 * (a + n); f = pa / n; pi2 = (T)2 * pa * pa; }
+      const T up = sigma * pa;
       // b.v = dl.v + ||v||^2/sigma;  ||v^+ - v||^2 = sigma^2 f^2 nn - 2 sigma f (b.v) + vv
-      const double bv = dv + vv * inv_sigma;
-      const double sf = sigma * f;
-      double dvv = sf * sf * nn - 2.0 * sf * bv + vv;
-      if (dvv < 0.0) dvv = 0.0;
+      const T bv = dv + vv * inv_sigma;
+      const T sf = sigma * f;
+      T dvv = sf * sf * nn - (T)2 * sf * bv + vv;
+      if (dvv < (T)0) dvv = 0;
       acc[P_PI2] += pi2;
       acc[P_SU] += up;
       acc[P_DUV2] += (up - uo) * (up - uo) + dvv;
       acc[P_UV2] += uo * uo + vv;
-      const double ap = (rt - A.R[ii]) * inv_s;   // (r - r_i)/s
-      acc[P_KP] = fmax(acc[P_KP], soc_dist_an(ap, sqrt(pp)));
-      acc[P_KD] = fmax(acc[P_KD], soc_dist_an(up, sf * n));
+      const T ap = (rt - ri) * inv_s;   // (r - r_i)/s
+      acc[P_KP] = fmax(acc[P_KP], (T)soc_dist_an((double)ap, sqrt((double)pp)));
+      acc[P_KD] = fmax(acc[P_KD], (T)soc_dist_an((double)up, (double)(sf * n)));
       // (r - r_i) u^+ + (c - c_i).v^+ = ap u^+ - sigma f (dl.b), dl.b = pp + dv/sigma
       acc[P_KC] = fmax(acc[P_KC], fabs(ap * up - sf * (pp + dv * inv_sigma)));
       if (cs != CASE_Z) acc[P_ZMAG] += fabs(a) + n;
@@ -541,12 +564,13 @@ __device__ __forceinline__ void rows_block(const PassArgs& A, int bid) {
   // block partial: per-lane accumulators -> warp (fixed trees) -> warps in
   // order.  Warps that took no entry hold zeros and skip the exchanges.
   if (32 * w < n_b) {
-    const double v8[8] = {acc[0], acc[1], acc[2], acc[3], acc[4], 0.0, 0.0, 0.0};
+    const double v8[8] = {(double)acc[0], (double)acc[1], (double)acc[2], (double)acc[3],
+                          (double)acc[4], 0.0, 0.0, 0.0};
     const double sv = warp_sum8_transposed(v8);
     if ((lane & 3) == 0 && (lane >> 2) < P_NSUM) s_wp[w][lane >> 2] = sv;
 #pragma unroll
     for (int k = P_NSUM; k < P_NREC; k++) {
-      const double mx = warp_max_nonneg(acc[k]);
+      const double mx = warp_max_nonneg((double)acc[k]);
       if (lane == 0) s_wp[w][k] = mx;
     }
 #pragma unroll
@@ -636,6 +660,7 @@ __host__ __device__ __forceinline__ int svec_rows_per_block(int nS, int nsvb) {
 }
 
 // Support-row block `bid` of at most nsvb (blocks past the rows return).
+template <bool LOWP = false>
 __device__ __forceinline__ void svec_block(const double* __restrict__ C, const Buffers& B, int d,
                                            int npb, int64_t seg, int bid, int nsvb) {
   DevState* st = B.st;
@@ -721,7 +746,9 @@ __device__ __forceinline__ void svec_block(const double* __restrict__ C, const B
         for (int r = grp; r < nr; r += G) {
           const int64_t idx = s_idx[r];
           const int sl = s_sl[r];
-          double b = (C[idx * d + j] - ct[j]) * inv_s;
+          double b = LOWP ? (double)((x32_at(B.X32, st->m_pad, idx, j) - B.vec.y32[j]) *
+                                     (float)inv_s)
+                          : (C[idx * d + j] - ct[j]) * inv_s;
           if (sl >= 0) b = fma(sv[(int64_t)sl * d + j], inv_sigma, b);
           av = fma(s_sf[r], b, av);
           const int64_t k = r0 + r;

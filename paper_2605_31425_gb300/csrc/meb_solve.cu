@@ -142,19 +142,21 @@ cudaError_t launch_cg_finish(Buffers& B, int d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <bool LOWP>
 __global__ void __launch_bounds__(256) k_mult_rows(const double* __restrict__ C, Buffers B,
                                                    int d) {
   pdl_wait_and_release();
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_OUTER) return;
-  mult_rows_block(C, B, d, blockIdx.x, gridDim.x);
+  mult_rows_block<LOWP>(C, B, d, blockIdx.x, gridDim.x);
   // the last block switches to the new multiplier buffers
   if (last_block_ticket(&st->ctr_slots) && threadIdx.x == 0) mult_flip(st);
 }
 
 cudaError_t launch_mult_update(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s) {
   (void)m;
-  cudaError_t e = launch_pdl(k_mult_rows, dim3(304), dim3(256), 0, s, C, B, d);
+  cudaError_t e = B.lowp ? launch_pdl(k_mult_rows<true>, dim3(304), dim3(256), 0, s, C, B, d)
+                        : launch_pdl(k_mult_rows<false>, dim3(304), dim3(256), 0, s, C, B, d);
   if (e != cudaSuccess) return e;
   B.launches += 1;
   return cudaGetLastError();
@@ -276,6 +278,89 @@ cudaError_t launch_mult_out(Buffers& B, int d, int64_t* idx, double* u, double* 
                             cudaStream_t s) {
   k_mult_out<<<152, 256, 0, s>>>(B, d, idx, u, v, cap);
   B.launches += 1;
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// The mixed-precision pipeline (Sec. 4.2): the reduced instance and its warm
+// start.
+
+// Rows idx[k] of (C, R), k < n, into (Cr, Rr): warp per row.
+__global__ void k_gather_rows(const double* __restrict__ C, const double* __restrict__ R,
+                              const int64_t* __restrict__ idx, int64_t n, int d,
+                              double* __restrict__ Cr, double* __restrict__ Rr) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n;
+       k += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t i = idx[k];
+    for (int j = lane; j < d; j += 32) Cr[k * d + j] = C[i * d + j];
+    if (lane == 0) Rr[k] = R[i];
+  }
+}
+
+cudaError_t launch_gather_rows(const double* C, const double* R, const int64_t* idx, int64_t n,
+                               int d, double* Cr, double* Rr, cudaStream_t s) {
+  k_gather_rows<<<304, 256, 0, s>>>(C, R, idx, n, d, Cr, Rr);
+  return cudaGetLastError();
+}
+
+// Warm start of the reduced solve (the state was initialised by
+// k_state_init): x = xk = (alpha, beta) = the previous point (scaled), the
+// previous penalty, and the previous multipliers (full-instance indices widx,
+// all present in the sorted list ired of the reduced instance's balls) as the
+// current multipliers, then the first trial's query shadow.  One block.
+__global__ void k_warm_start(Buffers B, int d, const double* __restrict__ wx, double sigma,
+                             const int64_t* __restrict__ widx, const double* __restrict__ wu,
+                             const double* __restrict__ wv, int64_t nw,
+                             const int64_t* __restrict__ ired, int64_t nred) {
+  __shared__ double sh[32];
+  DevState* st = B.st;
+  const DevVecs& V = B.vec;
+  for (int k = threadIdx.x; k <= d; k += blockDim.x) {
+    V.x[k] = wx[k]; V.xt[k] = wx[k]; V.xk[k] = wx[k]; V.ab[k] = wx[k];
+  }
+  for (int64_t k = threadIdx.x; k < nw; k += blockDim.x) {
+    const int64_t i = widx[k];
+    int64_t lo = 0, hi = nred;   // the position of i in ired
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (ired[mid] < i) lo = mid + 1; else hi = mid;
+    }
+    B.sup_idx[0][k] = (int)lo;
+    B.sup_u[0][k] = wu[k];
+    B.slot[lo] = (int)k;
+  }
+  for (int64_t e = threadIdx.x; e < nw * d; e += blockDim.x) B.sup_v[0][e] = wv[e];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->sigma = sigma;
+    st->inv_sigma = 1.0 / sigma;
+    st->tos = st->tau / sigma;
+    st->sup_cur = 0;
+    st->nsup = (int)nw;
+  }
+  __syncthreads();
+  set_trial(st, V, d, sh);
+}
+
+cudaError_t launch_warm_start(Buffers& B, int d, const double* wx, double sigma,
+                              const int64_t* widx, const double* wu, const double* wv, int64_t nw,
+                              const int64_t* ired, int64_t nred, cudaStream_t s) {
+  k_warm_start<<<1, 256, 0, s>>>(B, d, wx, sigma, widx, wu, wv, nw, ired, nred);
+  B.launches += 1;
+  return cudaGetLastError();
+}
+
+// idx[k] = map[idx[k]] (reduced-instance indices to full-instance indices).
+__global__ void k_map_idx(int64_t* __restrict__ idx, int64_t n, const int64_t* __restrict__ map) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    idx[k] = map[idx[k]];
+}
+
+cudaError_t launch_map_idx(int64_t* idx, int64_t n, const int64_t* map, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_map_idx<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, s>>>(idx, n, map);
   return cudaGetLastError();
 }
 

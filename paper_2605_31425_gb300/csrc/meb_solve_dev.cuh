@@ -748,6 +748,7 @@ __device__ __forceinline__ void cg_finish_body(const Buffers& B, int d) {
 // Multiplier update (Algorithm 1): (u, v)^{k+1} = sigma_k Pi(z_k) on the
 // support of the accepted point, written to the other buffer, with the
 // ball->slot map; the last block flips the buffer parity.
+template <bool LOWP = false>
 __device__ __forceinline__ void mult_rows_block(const double* __restrict__ C, const Buffers& B,
                                                 int d, int bid, int nb) {
   const DevState* st = B.st;
@@ -768,7 +769,9 @@ __device__ __forceinline__ void mult_rows_block(const double* __restrict__ C, co
     const double a = B.S_a[k], n = B.S_n[k];
     const double f = (B.S_case[k] == CASE_I) ? 1.0 : 0.5 * (a + n) / n;
     for (int j = lane; j < d; j += 32) {
-      double b = (C[(int64_t)idx * d + j] - ct[j]) * inv_s;
+      double b = LOWP ? (double)((x32_at(B.X32, st->m_pad, idx, j) - B.vec.y32[j]) *
+                                 (float)inv_s)
+                      : (C[(int64_t)idx * d + j] - ct[j]) * inv_s;
       if (sl >= 0) b = fma(sv[(int64_t)sl * d + j], inv_sigma, b);
       nv[(int64_t)k * d + j] = sigma * f * b;
     }

@@ -42,10 +42,31 @@ def paper_sweep():
                   f, indent=1)
 
 
+def ragged_sample(n=64, seed=1004):
+    """tests/golden/ragged_sample.json: the oracle's radius (tol 1e-12) of the
+    first n instances of the ragged batch."""
+    out = []
+    for k in range(n):
+        C, R = workloads.ragged_instance(k, seed)
+        t = time.time()
+        res = oracle.solve(C, R, tol=1e-12)
+        out.append(dict(k=k, m=int(C.shape[0]), d=int(C.shape[1]),
+                        input_sha256=workloads.digest(C, R), r=res["r"], status=res["status"],
+                        oracle_seconds=time.time() - t))
+        print(k, C.shape, res["r"], res["status"], flush=True)
+    with open(os.path.join(HERE, "ragged_sample.json"), "w") as f:
+        json.dump(dict(tol=1e-12, seed=seed, note="written by tests/golden/make_golden.py from "
+                       "oracle.solve; inputs from workloads.ragged_instance(k, seed)",
+                       instances=out), f, indent=1)
+
+
 def main(names):
     for name in names:
         if name == "paper_sweep":
             paper_sweep()
+            continue
+        if name == "ragged_sample":
+            ragged_sample()
             continue
         C, R = workloads.workload(name)
         t = time.time()
