@@ -329,16 +329,22 @@ def paper_sweep(meb, torch, local, stream):
         dC, dR = torch.from_numpy(C).cuda(), torch.from_numpy(R).cuda()
         row = {"m": m, "d": d}
         for tag, prm in (("plain", None), ("mixed", mp)):
-            meb.solve(dC, dR, params=prm, ctx=ctx, allow_notconv=True)
-            ts = []
-            for _ in range(3):
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                res = meb.solve(dC, dR, params=prm, ctx=ctx, allow_notconv=True)
-                torch.cuda.synchronize()
-                ts.append(time.perf_counter() - t0)
+            try:
+                meb.solve(dC, dR, params=prm, ctx=ctx, allow_notconv=True)
+                ts = []
+                for _ in range(3):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    res = meb.solve(dC, dR, params=prm, ctx=ctx, allow_notconv=True)
+                    torch.cuda.synchronize()
+                    ts.append(time.perf_counter() - t0)
+            except meb.MebError as e:   # reported, not hidden
+                row[tag + "_error"] = str(e)
+                ctx = meb.Context(local, stream.cuda_stream)
+                continue
             row[tag + "_ms"] = 1e3 * statistics.median(ts)
             row[tag + "_relerr"] = abs(res["r"] - g["r"]) / g["r"]
+            row[tag + "_status"] = res["status"]
             if tag == "mixed":
                 row["kept"] = res["n_reduced"]
                 row["readd_rounds"] = res["readd_rounds"]
@@ -347,8 +353,9 @@ def paper_sweep(meb, torch, local, stream):
         rows.append(row)
         del dC, dR
     return {"instances": rows,
-            "max_relerr_plain": max(r["plain_relerr"] for r in rows),
-            "max_relerr_mixed": max(r["mixed_relerr"] for r in rows)}
+            "max_relerr_plain": max((r["plain_relerr"] for r in rows if "plain_relerr" in r), default=None),
+            "max_relerr_mixed": max((r["mixed_relerr"] for r in rows if "mixed_relerr" in r), default=None),
+            "errors": sum(1 for r in rows for k in r if k.endswith("_error"))}
 
 
 def serving(meb, workloads, seconds, rate=2000.0, n_pool=256):
@@ -399,6 +406,8 @@ def main():
                     help="headline only (no FP64 arm, no other workloads)")
     ap.add_argument("--batch-instances", type=int, default=1024)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--only", choices=["ragged", "sphere", "serving"], default=None,
+                    help="run one extra line alone and print it (for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -423,6 +432,15 @@ def main():
 
     import paper_2605_31425_gb300 as meb
     stream = torch.cuda.current_stream()
+    if args.only:
+        if args.only == "ragged":
+            out = ragged_batch(meb, torch, local, stream, workloads, args.batch_instances)
+        elif args.only == "serving":
+            out = serving(meb, workloads, args.serve_seconds)
+        else:
+            out = extra_workloads(meb, torch, local, stream, workloads)["sphere_m2e5_d2000"]
+        print(json.dumps({"only": args.only, **out}), flush=True)
+        return
     ctx = meb.Context(local, stream.cuda_stream)
     dC = torch.from_numpy(C).cuda()
     dR = torch.from_numpy(R).cuda()

@@ -270,8 +270,10 @@ int meb_tune_batch(meb_ctx *ctx, int32_t n, const meb_batch_item *items, int32_t
  * with them; requests with m*d >= large_balls take meb_solve's multi-block
  * path on their own workers.  Each request is solved by exactly the steps it
  * would take alone: its results do not depend on the mix.
- * Zero fields of cfg take the defaults: 4 small workers, 1 large worker,
- * large_balls 2^24, groups of at most 152 requests. */
+ * Zero fields of cfg take the defaults: 16 small workers, 1 large worker,
+ * large_balls 2^24, groups of at most 32 requests.  The server keeps memory
+ * its workers free in this process's stream-ordered pool of the device (up to
+ * budget_bytes) for the next requests. */
 typedef struct {
     int64_t budget_bytes;     /* device memory for admitted requests (required, > 0) */
     int64_t large_balls;      /* m*d at or above which a request is "large"          */

@@ -13,6 +13,8 @@
 
 #include <algorithm>
 #include <iterator>
+#include <map>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -110,7 +112,8 @@ static int fail(meb_ctx* ctx, int code, const char* fmt, ...) {
     cudaError_t e_ = (call);                                                          \
     if (e_ != cudaSuccess)                                                            \
       return fail(ctx, e_ == cudaErrorMemoryAllocation ? MEB_ENOMEM : MEB_ECUDA,      \
-                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+                  "%s: %s (%s:%d) [%s]", #call, cudaGetErrorString(e_), __FILE__, __LINE__, \
+                  launch_failure_note());                                             \
   } while (0)
 
 // Device allocations of the context's scratch.  With MEB_OPT_RELEASE_SCRATCH
@@ -209,6 +212,7 @@ static size_t solve_layout(Buffers* Bp, char* base, int64_t m, int d) {
   take(&B.S_u, m);
   take(&B.S_t, m);
   take(&B.W, md);
+  if (d + 1 > kMaxDenseN) take(&B.W32, md);   // the matrix-free path for sure: FP32 rows
   take(&B.svec_part, (size_t)kSvecBlocks * (3 * d + 1));
   take(&B.hpart, hp);
   take(&B.H, dn);
@@ -285,7 +289,10 @@ static void release_scratch(meb_ctx* ctx) {
 // outermost call frees the context's device scratch when it returns.
 struct CallScope {
   meb_ctx* c;
-  explicit CallScope(meb_ctx* ctx) : c(ctx) { c->depth++; }
+  explicit CallScope(meb_ctx* ctx) : c(ctx) {
+    // an earlier failed launch of this thread must not surface here
+    if (c->depth++ == 0) (void)cudaGetLastError();
+  }
   ~CallScope() {
     if (--c->depth == 0 && c->release) {
       cudaStreamSynchronize(c->stream);
@@ -328,6 +335,38 @@ static int copy_out(meb_ctx* ctx, void* dst, const void* dsrc, size_t bytes, uns
                      ctx->stream));
   return MEB_OK;
 }
+
+namespace meb {
+
+// The dynamic shared-memory limit of a kernel is process-wide (per device):
+// several host threads launching the same kernel with different sizes must
+// never lower it under one another, so it is only ever raised, under a lock.
+// (A kernel with static shared memory needs the opt-in for any dynamic size
+// that takes the total past 48 KB, so it is set for every size asked.)
+cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> cur;
+  if (bytes == 0) return cudaSuccess;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& c = cur[std::make_pair(dev, fn)];
+  if (bytes <= c) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) c = bytes;
+  return e;
+}
+
+// The kernel launch that failed last on this host thread (for the message).
+static thread_local char g_launch_note[160] = {0};
+void note_launch_failure(const char* what, unsigned grid, size_t smem, cudaError_t e) {
+  snprintf(g_launch_note, sizeof(g_launch_note), "%s grid %u smem %zu: %s", what, grid, smem,
+           cudaGetErrorString(e));
+}
+const char* launch_failure_note() { return g_launch_note; }
+
+}  // namespace meb
 
 extern "C" {
 
@@ -1418,8 +1457,13 @@ static int solve_mixed(meb_ctx* ctx, const double* C, const double* R, int64_t m
   Buffers& B = ctx->B;
   int rc;
   // 1. the low-precision ripALM on all balls, to tol_lp
+  // (its FP32 rows resolve u = sigma Pi(z) to about sigma 2^-24: the penalty
+  // stays at most 1e4, so that floor stays below tol_lp; it is a warm start,
+  // so at most 50 outer steps)
   meb_params P1 = P;
   P1.tol = P.tol_lp;
+  P1.sigma_max = std::min(P.sigma_max, std::max(P.sigma0, 1e4));
+  P1.max_outer = std::min(P.max_outer, 50);
   B.lowp = true;
   rc = init_state(ctx, B, m, d, P1, sc, r0);
   if (rc == MEB_OK) rc = run_ticks(ctx, B, C, R, m, d, P1);

@@ -235,9 +235,11 @@ __device__ void batch_solve_one(const BatchArgs& G, int j, const Buffers& B,
         cg_setup_body(B, d);
         __syncthreads();
         while (cg_gate(st)) {
-          hvp_dot_block(B, d, B.vec.cg_p, B.wq, 0, 1);
+          if (B.W32) hvp_dot_block<true>(B, d, B.vec.cg_p, B.wq, 0, 1);
+          else hvp_dot_block<false>(B, d, B.vec.cg_p, B.wq, 0, 1);
           __syncthreads();
-          hvp_acc_block(B, d, B.vec.cg_p, B.wq, B.hpart, 0, 1);
+          if (B.W32) hvp_acc_block<true>(B, d, B.vec.cg_p, B.wq, B.hpart, 0, 1, -1);
+          else hvp_acc_block<false>(B, d, B.vec.cg_p, B.wq, B.hpart, 0, 1);
           __syncthreads();
           cg_update_body(B, d, 1);
           __syncthreads();
@@ -378,6 +380,7 @@ size_t batch_slot_layout(Buffers* Bp, char* base, int64_t m_cap, int d_cap, int6
   take(&B.S_u, sup_cap);
   take(&B.S_t, sup_cap);
   take(&B.W, (size_t)sup_cap * d_cap);
+  if (n1 > kGjRegN) take(&B.W32, (size_t)sup_cap * d_cap);   // CG instances: FP32 rows
   take(&B.svec_part, (size_t)kBatchMaxSvec * (3 * d_cap + 1));
   const size_t hp = (size_t)ntri * kSyrkTile * kSyrkTile;
   take(&B.hpart, hp > (size_t)n1 ? hp : (size_t)n1);
@@ -429,8 +432,7 @@ size_t batch_smem(int d_cap) {
 }
 
 cudaError_t launch_batch(const BatchArgs& G, int nblocks, size_t smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)k_batch, smem);
   if (e != cudaSuccess) return e;
   k_batch<<<nblocks, 256, smem, s>>>(G);
   return cudaGetLastError();

@@ -112,6 +112,13 @@ __device__ double block_max(double v, double* sh) {
   return t;
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(MEB_FULLMASK, v, o);
+  return v;
+}
+
 // Element j of ball i of the FP32 shadow (layout [ceil(d/4)][m_pad] float4).
 __device__ __forceinline__ float x32_at(const float4* X32, int64_t m_pad, int64_t i, int j) {
   return reinterpret_cast<const float*>(X32)[(((int64_t)(j >> 2)) * m_pad + i) * 4 + (j & 3)];

@@ -168,6 +168,7 @@ struct Buffers {
   // support list of the last pass (ball order)
   int* S_idx; unsigned char* S_case; double* S_a; double* S_n; double* S_u; double* S_t;
   double* W;            // [m*d] w rows (case M) / b rows (case I)
+  float* W32;           // [m*d] the same in FP32 for the CG products (matrix-free path), or null
   double* svec_part;    // [kSvecBlocks][2d+1]
   double* hpart;        // SYRK partials
   int64_t hpart_cap;
@@ -230,6 +231,12 @@ __host__ __device__ inline void state_defaults(DevState& S, int64_t m, int d, co
   S.action = ACT_NONE;
   S.status = 0;
 }
+
+// Raise (never lower) a kernel's dynamic shared-memory limit; thread-safe.
+cudaError_t raise_smem_limit(const void* fn, size_t bytes);
+// Record / read the last failed launch of this host thread.
+void note_launch_failure(const char* what, unsigned grid, size_t smem, cudaError_t e);
+const char* launch_failure_note();
 
 // ---- the batched solver (meb_batch.cu) ----
 constexpr int kBatchMaxSvec = 16;   // support-row blocks of one batched solve, at most

@@ -205,6 +205,25 @@ static int scratch_for_current_device(void** out) {
   return MEB_OK;
 }
 
+// The kernels' dynamic shared-memory limits are process-wide: raise them
+// (never lower them) under a lock, per device, without allocating.
+static size_t g_smem_limit[kMaxDevices] = {};
+static std::mutex g_smem_mu;
+
+static int raise_smem_limits(size_t bytes) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MEB_ECUDA;
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  if (bytes <= g_smem_limit[dev]) return MEB_OK;
+  if (cudaFuncSetAttribute(k_nf_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_nf_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+          cudaSuccess)
+    return MEB_ECUDA;
+  g_smem_limit[dev] = bytes;
+  return MEB_OK;
+}
+
 }  // namespace
 
 extern "C" int meb_feas_check_noalloc(const double* centers, const double* radii, int64_t m,
@@ -221,13 +240,7 @@ extern "C" int meb_feas_check_noalloc(const double* centers, const double* radii
   Scratch* S = static_cast<Scratch*>(sp);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const size_t sh = sizeof(double) * (size_t)d;
-  if (sh > 48 * 1024) {
-    if (cudaFuncSetAttribute(k_nf_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_nf_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh) !=
-            cudaSuccess)
-      return MEB_ECUDA;
-  }
+  if (raise_smem_limits(sh) != MEB_OK) return MEB_ECUDA;
   k_nf_count<<<kBlocks, kNT, sh, s>>>(centers, radii, m, d, c, r, eps, S);
   k_nf_reduce<<<1, 32, 0, s>>>(S);
   if (viol_cap > 0) k_nf_list<<<kBlocks, kNT, sh, s>>>(centers, radii, m, d, c, r, eps, S, viol_idx, viol_cap);

@@ -286,7 +286,7 @@ cudaError_t prepare_pass(const Buffers& B, int d) {
   pass_blocks(1, d, variant, &tpb);
   if (variant == 2) {
     const size_t shb = bulk_smem(d, bulk_stages(d));
-    return cudaFuncSetAttribute(k_screen_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
+    return raise_smem_limit((const void*)k_screen_bulk, shb);
   }
   return cudaSuccess;
 }
@@ -324,10 +324,10 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
   A.cand_a = B.cand_a; A.cand_n = B.cand_n; A.cand_u = B.cand_u;
   const size_t sh1 = 16 * (size_t)(2 * ((d4 + 1) / 2));   // -y padded to whole FP16 rows
   cudaError_t e;
-  if (sh1 > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_screen<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh1);
+  {
+    e = raise_smem_limit((const void*)k_screen<false>, sh1);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_screen<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh1);
+    e = raise_smem_limit((const void*)k_screen<true>, sh1);
     if (e != cudaSuccess) return e;
   }
   // cudaEventRecordExternal: inside a stream capture the records become event
@@ -346,18 +346,24 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
   } else {
     e = launch_pdl(k_screen<false>, dim3(nb), dim3(kPassThreads), sh1, s, A, B);
   }
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) {
+    note_launch_failure("screen", (unsigned)nb, sh1, e);
+    return e;
+  }
   if (ev1) cudaEventRecordWithFlags(ev1, s, evf);
   const size_t sh2 = 8 * (size_t)d;
-  if (sh2 > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_rows64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh2);
+  {
+    e = raise_smem_limit((const void*)k_rows64<false>, sh2);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_rows64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh2);
+    e = raise_smem_limit((const void*)k_rows64<true>, sh2);
     if (e != cudaSuccess) return e;
   }
   e = B.lowp ? launch_pdl(k_rows64<true>, dim3(nb), dim3(kPassThreads), sh2, s, A, B)
              : launch_pdl(k_rows64<false>, dim3(nb), dim3(kPassThreads), sh2, s, A, B);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) {
+    note_launch_failure(B.lowp ? "rows (FP32)" : "rows", (unsigned)nb, sh2, e);
+    return e;
+  }
   B.launches += 2;
   return cudaGetLastError();
 }
@@ -452,8 +458,8 @@ cudaError_t launch_feas_cert(const double* C, const double* R, int64_t m, int d,
   }
   if (!reuse_bounds && !A.all64) {
     const size_t sha = 16 * (size_t)A.d4;
-    if (sha > 48 * 1024) {
-      e = cudaFuncSetAttribute(k_feas_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sha);
+    {
+      e = raise_smem_limit((const void*)k_feas_a, sha);
       if (e != cudaSuccess) return e;
     }
     k_feas_a<<<nb, kFeasNT, sha, s>>>(A);
@@ -464,8 +470,8 @@ cudaError_t launch_feas_cert(const double* C, const double* R, int64_t m, int d,
     launched += 1;
   }
   const size_t shb = 8 * (size_t)d;
-  if (shb > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_feas_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
+  {
+    e = raise_smem_limit((const void*)k_feas_b, shb);
     if (e != cudaSuccess) return e;
   }
   k_feas_b<<<nb, kFeasNT, shb, s>>>(A);

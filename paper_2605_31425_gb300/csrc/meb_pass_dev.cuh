@@ -409,13 +409,6 @@ __device__ __forceinline__ bool screen_gate(const DevState* st) {
 // the rows come from the FP32 shadow (x32 = c_i - o, radii r32, the query
 // y32 = trunc32(c - o), fl32(r)) and every per-ball operation and per-lane sum
 // is FP32; the block records stay FP64 (their sums are the controller's).
-template <typename T>
-__device__ __forceinline__ T warp_sum_t(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(MEB_FULLMASK, v, o);
-  return v;
-}
-
 template <bool LOWP = false>
 __device__ __forceinline__ void rows_block(const PassArgs& A, int bid) {
   using T = typename std::conditional<LOWP, float, double>::type;
@@ -757,8 +750,10 @@ __device__ __forceinline__ void svec_block(const double* __restrict__ C, const B
             aw += wv;
             atw = fma(s_t[r] * wv, wv, atw);
             B.W[k * d + j] = wv;
+            if (B.W32) B.W32[k * d + j] = (float)wv;
           } else {
             B.W[k * d + j] = b;
+            if (B.W32) B.W32[k * d + j] = (float)b;
           }
         }
       }

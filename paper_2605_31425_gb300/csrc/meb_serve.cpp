@@ -209,15 +209,23 @@ extern "C" int meb_server_create(meb_server** out, int device, const meb_server_
   if (!sv) return MEB_ENOMEM;
   sv->device = device;
   sv->cfg = *cfg;
-  if (sv->cfg.small_workers <= 0) sv->cfg.small_workers = 4;
+  if (sv->cfg.small_workers <= 0) sv->cfg.small_workers = 16;
   if (sv->cfg.large_workers <= 0) sv->cfg.large_workers = 1;
   if (sv->cfg.large_balls <= 0) sv->cfg.large_balls = (int64_t)1 << 24;
-  if (sv->cfg.max_group <= 0) sv->cfg.max_group = 152;
+  if (sv->cfg.max_group <= 0) sv->cfg.max_group = 32;
   if (params) sv->P = *params;
   else meb_params_default(&sv->P);
   if (cudaSetDevice(device) != cudaSuccess) {
     delete sv;
     return MEB_ECUDA;
+  }
+  // the workers allocate and free stream-ordered from the device's default
+  // pool: keep freed memory in this process's pool (up to the budget) rather
+  // than returning it to the driver at every synchronisation
+  cudaMemPool_t mp;
+  if (cudaDeviceGetDefaultMemPool(&mp, device) == cudaSuccess) {
+    uint64_t keep = (uint64_t)sv->cfg.budget_bytes;
+    cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
   }
   for (int k = 0; k < sv->cfg.small_workers; k++) sv->workers.emplace_back(small_worker, sv);
   for (int k = 0; k < sv->cfg.large_workers; k++) sv->workers.emplace_back(large_worker, sv);

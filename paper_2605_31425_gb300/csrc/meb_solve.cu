@@ -60,16 +60,10 @@ cudaError_t prepare_newton(int d) {
   if (n > kMaxDenseN) return cudaSuccess;   // matrix-free path
   const size_t shc = sizeof(double) * (size_t)n * (n + 1) / 2;
   cudaError_t e = cudaSuccess;
-  if (n <= kGjRegN) {
-    if (shc > 48 * 1024)
-      e = cudaFuncSetAttribute(k_newton_gj_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shc);
-    return e;
-  }
+  if (n <= kGjRegN) return raise_smem_limit((const void*)k_newton_gj_reg, shc);
   const size_t shg = sizeof(float) * (size_t)n * n;
-  if (shg > 48 * 1024)
-    e = cudaFuncSetAttribute(k_newton_gj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shg);
-  if (e == cudaSuccess && shc > 48 * 1024)
-    e = cudaFuncSetAttribute(k_newton_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shc);
+  e = raise_smem_limit((const void*)k_newton_gj, shg);
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)k_newton_chol, shc);
   return e;
 }
 
@@ -97,14 +91,16 @@ cudaError_t launch_newton_dense(Buffers& B, int d, cudaStream_t s) {
 __global__ void __launch_bounds__(256) k_hvp_dot(Buffers B, int d, const double* __restrict__ q,
                                                   double* __restrict__ wq, int force) {
   if (!force && !cg_gate(B.st)) return;
-  hvp_dot_block(B, d, q, wq, blockIdx.x, gridDim.x);
+  if (B.W32 && !force) hvp_dot_block<true>(B, d, q, wq, blockIdx.x, gridDim.x);
+  else hvp_dot_block<false>(B, d, q, wq, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(256) k_hvp_acc(Buffers B, int d, const double* __restrict__ q,
                                                   const double* __restrict__ wq,
                                                   double* __restrict__ part, int force) {
   if (!force && !cg_gate(B.st)) return;
-  hvp_acc_block(B, d, q, wq, part, blockIdx.x, gridDim.x);
+  if (B.W32 && !force) hvp_acc_block<true>(B, d, q, wq, part, blockIdx.x, gridDim.x, blockIdx.y);
+  else hvp_acc_block<false>(B, d, q, wq, part, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(256) k_cg_setup(Buffers B, int d) {
@@ -130,8 +126,13 @@ cudaError_t launch_cg_setup(Buffers& B, int d, cudaStream_t s) {
 
 cudaError_t launch_cg_iter(Buffers& B, int d, cudaStream_t s) {
   k_hvp_dot<<<kHvpBlocks * 4, 256, 0, s>>>(B, d, B.vec.cg_p, B.wq, 0);
-  k_hvp_acc<<<kHvpBlocks, 256, 0, s>>>(B, d, B.vec.cg_p, B.wq, B.hpart, 0);
-  k_cg_update<<<1, 256, 0, s>>>(B, d, kHvpBlocks);
+  if (B.W32) {   // FP32 products: row groups x column chunks
+    k_hvp_acc<<<dim3(kHvpGroups32, (d + 255) / 256), 256, 0, s>>>(B, d, B.vec.cg_p, B.wq, B.hpart, 0);
+    k_cg_update<<<1, 256, 0, s>>>(B, d, kHvpGroups32);
+  } else {
+    k_hvp_acc<<<kHvpBlocks, 256, 0, s>>>(B, d, B.vec.cg_p, B.wq, B.hpart, 0);
+    k_cg_update<<<1, 256, 0, s>>>(B, d, kHvpBlocks);
+  }
   B.launches += 3;
   return cudaGetLastError();
 }

@@ -592,6 +592,11 @@ __device__ __forceinline__ void newton_gj_reg_body(const Buffers& B, int d) {
 //   P_k q = 1/2 (q0 + w.q1 ; q0 w + (1+t) q1 - t w (w.q1)).
 // k_hvp_dot: wq_k = w_k . q1 (warp per row); k_hvp_acc: -1/2 sum_k t_k wq_k w_k
 // and 1/2 sum_k wq_k; hvp_finish adds the terms in q0 sum w and sum(1+t) q1.
+// Matrix-free Hessian-vector products, FP64 (the evaluation entry) or FP32
+// (F32: the solve's CG, when the support rows also exist in FP32, W32: the
+// product only shapes the Newton direction; the stop test, Armijo and KKT
+// use the FP64 gradient and Psi).
+template <bool F32 = false>
 __device__ __forceinline__ void hvp_dot_block(const Buffers& B, int d, const double* __restrict__ q,
                                               double* __restrict__ wq, int bid, int nb) {
   const DevState* st = B.st;
@@ -600,9 +605,16 @@ __device__ __forceinline__ void hvp_dot_block(const Buffers& B, int d, const dou
   for (int k = (bid * 256 + threadIdx.x) >> 5; k < nS; k += (nb * 256) >> 5) {
     double t = 0.0;
     if (B.S_case[k] == CASE_M) {
-      const double* w = B.W + (int64_t)k * d;
-      for (int j = lane; j < d; j += 32) t = fma(w[j], q[1 + j], t);
-      t = warp_sum(t);
+      if (F32) {
+        const float* w = B.W32 + (int64_t)k * d;
+        float tf = 0.0f;
+        for (int j = lane; j < d; j += 32) tf = fmaf(w[j], (float)q[1 + j], tf);
+        t = (double)warp_sum_t(tf);
+      } else {
+        const double* w = B.W + (int64_t)k * d;
+        for (int j = lane; j < d; j += 32) t = fma(w[j], q[1 + j], t);
+        t = warp_sum(t);
+      }
     }
     if (lane == 0) wq[k] = t;
   }
@@ -612,28 +624,60 @@ __device__ __forceinline__ bool cg_gate(const DevState* st) {
   return st->status == 0 && st->action == ACT_NEWTON && !st->cg_done;
 }
 
+// Row group bid of nb; F32: column chunk `chunk` of 256 only (chunks < 0:
+// every chunk), FP64: every chunk.
+template <bool F32 = false>
 __device__ __forceinline__ void hvp_acc_block(const Buffers& B, int d, const double* __restrict__ q,
                                               const double* __restrict__ wq,
-                                              double* __restrict__ part, int bid, int nb) {
+                                              double* __restrict__ part, int bid, int nb,
+                                              int chunk = -1) {
   const DevState* st = B.st;
   const int nS = st->nS;
   const int rpb = (nS + nb - 1) / nb;
   const int k0 = bid * rpb, k1 = min(nS, k0 + rpb);
   double* out = part + (int64_t)bid * (d + 1);
   double s0 = 0.0;
-  for (int j0 = 0; j0 < d; j0 += 256) {
+  const int jb = (F32 && chunk >= 0) ? 256 * chunk : 0;
+  const int je = (F32 && chunk >= 0) ? min(d, jb + 256) : d;
+  for (int j0 = jb; j0 < je; j0 += 256) {
     const int j = j0 + threadIdx.x;
-    double acc = 0.0;
-    for (int k = k0; k < k1; k++) {
-      if (B.S_case[k] != CASE_M) continue;
-      const double coef = -0.5 * B.S_t[k] * wq[k];   // the q0 w part is 1/2 q0 sum w
-      if (j < d) acc = fma(coef, B.W[(int64_t)k * d + j], acc);
-      if (j0 == 0 && threadIdx.x == 0) s0 += 0.5 * wq[k];
+    if (F32) {
+      // four independent accumulators (more loads in flight), summed in order
+      float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      int k = k0;
+      for (; k + 3 < k1; k += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int kk = k + u;
+          const float coef = (B.S_case[kk] == CASE_M) ? -0.5f * (float)B.S_t[kk] * (float)wq[kk] : 0.0f;
+          if (j < d) a[u] = fmaf(coef, B.W32[(int64_t)kk * d + j], a[u]);
+        }
+      }
+      for (; k < k1; k++) {
+        const float coef = (B.S_case[k] == CASE_M) ? -0.5f * (float)B.S_t[k] * (float)wq[k] : 0.0f;
+        if (j < d) a[0] = fmaf(coef, B.W32[(int64_t)k * d + j], a[0]);
+      }
+      if (j < d) out[1 + j] = (double)((a[0] + a[1]) + (a[2] + a[3]));
+      if (j0 == 0 && threadIdx.x == 0)
+        for (int kk = k0; kk < k1; kk++)
+          if (B.S_case[kk] == CASE_M) s0 += 0.5 * wq[kk];
+    } else {
+      double acc = 0.0;
+      for (int k = k0; k < k1; k++) {
+        if (B.S_case[k] != CASE_M) continue;
+        const double coef = -0.5 * B.S_t[k] * wq[k];   // the q0 w part is 1/2 q0 sum w
+        if (j < d) acc = fma(coef, B.W[(int64_t)k * d + j], acc);
+        if (j0 == 0 && threadIdx.x == 0) s0 += 0.5 * wq[k];
+      }
+      if (j < d) out[1 + j] = acc;
     }
-    if (j < d) out[1 + j] = acc;
   }
-  if (threadIdx.x == 0) out[0] = s0;
+  if (threadIdx.x == 0 && jb == 0) out[0] = s0;
 }
+
+// Row groups of the FP32 products in the multi-block CG (partials per entry
+// summed by the CG update).
+constexpr int kHvpGroups32 = 32;
 
 // y = tau/sigma q + sigma (n_I q + 1/2 [n_M q0 + S0 ; q0 sum w + sum(1+t) q1] + acc)
 __device__ inline void hvp_finish(DevState* st, const DevVecs& V, int d, const double* q,
@@ -682,6 +726,8 @@ __device__ __forceinline__ void cg_setup_body(const Buffers& B, int d) {
     st->cg_bn = sqrt(bn);
     double gn = sqrt(bn);
     st->cg_rtol = gn < 0.01 ? sqrt(gn) : 0.1;
+    // FP32 products resolve a relative residual of about 1e-7, not below
+    if (B.W32 && st->cg_rtol < 1e-6) st->cg_rtol = 1e-6;
     st->cg_it = 0;
     st->cg_done = (bn == 0.0);
   }
