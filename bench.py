@@ -52,6 +52,10 @@ import time
 
 import numpy as np
 
+# the serving workers' streams need hardware queues of their own (read when the
+# process first uses CUDA)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -209,9 +213,11 @@ def timed_solves(meb, torch, ctx, dC, dR, steps, warmup, stream):
     return [a.elapsed_time(b) for a, b in ev], res, radii
 
 
-def extra_workloads(meb, torch, local, stream, workloads):
+def extra_workloads(meb, torch, local, stream, workloads, sphere_only=False):
     """The small latency-bound instance and the large high-dimensional one."""
     out = {}
+    if sphere_only:
+        return sphere_workload(meb, torch, local, stream, workloads, out)
     # m = 1e4, d = 10 (gaussian, seed 1001): stored oracle radius
     C, R = workloads.workload("gaussian_m1e4_d10")
     gold = _golden("gaussian_m1e4_d10")
@@ -229,6 +235,10 @@ def extra_workloads(meb, torch, local, stream, workloads):
         "max_relerr": max(rel) if rel else None, "reference": "stored oracle radius",
         "bound": "latency (working set 0.9 MB, L2-resident)"}
     del dC, dR
+    return sphere_workload(meb, torch, local, stream, workloads, out)
+
+
+def sphere_workload(meb, torch, local, stream, workloads, out):
     # m = 2e5, d = 2000 (sphere, seed 1003): closed form r* = 1
     C, R, _ctr = workloads.sphere(200_000, 2000, 1003)
     ctx = meb.Context(local, stream.cuda_stream)
@@ -358,7 +368,8 @@ def paper_sweep(meb, torch, local, stream):
             "errors": sum(1 for r in rows for k in r if k.endswith("_error"))}
 
 
-def serving(meb, workloads, seconds, rate=2000.0, n_pool=256):
+def serving(meb, workloads, seconds, rate=2000.0, n_pool=256, small_workers=0, max_group=0,
+            large_balls=0):
     """Poisson arrivals at `rate` requests/s for `seconds`, instances drawn from
     a pool of ragged instances (1% large: m = 5e5, d = 128), under an 80 GB
     device-memory budget; every request's latency from submission to result.
@@ -369,7 +380,8 @@ def serving(meb, workloads, seconds, rate=2000.0, n_pool=256):
     big = [tuple(torch.from_numpy(a).pin_memory() for a in workloads.cube(500_000, 128, 1005 + k, 0.05))
            for k in range(2)]
     t_arr, pick = workloads.poisson_arrivals(rate, seconds, n_pool, 1005, 0.01, len(big))
-    sv = meb.Server(budget_bytes=80 * 10 ** 9)
+    sv = meb.Server(budget_bytes=80 * 10 ** 9, small_workers=small_workers, max_group=max_group,
+                    large_balls=large_balls)
     tickets = [None] * len(t_arr)
     t0 = time.perf_counter()
     for k, (ta, p) in enumerate(zip(t_arr, pick)):
@@ -390,7 +402,9 @@ def serving(meb, workloads, seconds, rate=2000.0, n_pool=256):
             "p99_small_ms": float(np.percentile(small_lat, 99)),
             "large_requests": int(np.sum(pick < 0)), "launches": st["launches"],
             "peak_device_gb": st["peak_bytes"] / 1e9, "budget_gb": 80,
-            "pool": f"{n_pool} ragged instances (seed 1005) + 2 large (m=5e5, d=128), pinned host memory"}
+            "pool": f"{n_pool} ragged instances (seed 1005) + 2 large (m=5e5, d=128), pinned host memory",
+            "small_workers": small_workers or "default", "max_group": max_group or "default",
+            "large_balls": large_balls or "default"}
 
 
 def main():
@@ -438,7 +452,8 @@ def main():
         elif args.only == "serving":
             out = serving(meb, workloads, args.serve_seconds)
         else:
-            out = extra_workloads(meb, torch, local, stream, workloads)["sphere_m2e5_d2000"]
+            out = extra_workloads(meb, torch, local, stream, workloads,
+                                  sphere_only=True)["sphere_m2e5_d2000"]
         print(json.dumps({"only": args.only, **out}), flush=True)
         return
     ctx = meb.Context(local, stream.cuda_stream)

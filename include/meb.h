@@ -163,6 +163,11 @@ const char *meb_last_error(const meb_ctx *ctx);
  *                       before it returns (for callers that account device
  *                       memory against a budget); 0 (default) keeps it for the
  *                       next call.
+ *  MEB_OPT_BLOCKING_SYNC  1: the calling thread sleeps while it waits for the
+ *                       context's stream (a blocking-sync event) instead of
+ *                       spinning, for callers that run many contexts from
+ *                       more threads than host cores; 0 (default) spins, the
+ *                       shortest wake-up.
  * Returns MEB_EINVAL for an unknown option or value. */
 #define MEB_OPT_SCREEN 1
 #define MEB_OPT_EVAL_SCREEN 2
@@ -171,6 +176,7 @@ const char *meb_last_error(const meb_ctx *ctx);
 #define MEB_OPT_WAIT_CYCLES 5
 #define MEB_OPT_BATCH_SLOTS 6
 #define MEB_OPT_RELEASE_SCRATCH 7
+#define MEB_OPT_BLOCKING_SYNC 8
 #define MEB_SCREEN_FP16 0
 #define MEB_SCREEN_FP16_BULK 1
 #define MEB_SCREEN_FP32 2
@@ -270,10 +276,14 @@ int meb_tune_batch(meb_ctx *ctx, int32_t n, const meb_batch_item *items, int32_t
  * with them; requests with m*d >= large_balls take meb_solve's multi-block
  * path on their own workers.  Each request is solved by exactly the steps it
  * would take alone: its results do not depend on the mix.
- * Zero fields of cfg take the defaults: 16 small workers, 1 large worker,
- * large_balls 2^24, groups of at most 32 requests.  The server keeps memory
- * its workers free in this process's stream-ordered pool of the device (up to
- * budget_bytes) for the next requests. */
+ * Zero fields of cfg take the defaults: 64 small workers, 2 large workers,
+ * large_balls 2^24, groups of at most 4 requests.  The workers allocate from
+ * a stream-ordered memory pool of the server's own, which keeps freed memory
+ * (up to budget_bytes) for the next requests and never makes one worker's
+ * allocation wait for another worker's work; they wait for the GPU asleep
+ * (MEB_OPT_BLOCKING_SYNC).  The workers' streams run side by side only on
+ * separate hardware queues: set CUDA_DEVICE_MAX_CONNECTIONS (at most 32)
+ * before the process first uses CUDA. */
 typedef struct {
     int64_t budget_bytes;     /* device memory for admitted requests (required, > 0) */
     int64_t large_balls;      /* m*d at or above which a request is "large"          */

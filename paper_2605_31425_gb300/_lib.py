@@ -18,7 +18,8 @@ MEB_OK, MEB_EINVAL, MEB_ENOMEM, MEB_ECUDA, MEB_ENOTCONV, MEB_ETIMEOUT = 0, -1, -
 MEB_PTR_DEVICE = 1
 # context options and screen modes (include/meb.h)
 MEB_OPT_SCREEN, MEB_OPT_EVAL_SCREEN, MEB_OPT_EVAL_SHADOW_EXP, MEB_OPT_TICK_LOOP, \
-    MEB_OPT_WAIT_CYCLES = 1, 2, 3, 4, 5
+    MEB_OPT_WAIT_CYCLES, MEB_OPT_BATCH_SLOTS, MEB_OPT_RELEASE_SCRATCH, \
+    MEB_OPT_BLOCKING_SYNC = 1, 2, 3, 4, 5, 6, 7, 8
 SCREEN_MODES = {"fp16": 0, "fp16_bulk": 1, "fp32": 2, "fp64": 3}
 TICK_LOOPS = {"graph": 0, "host": 1, "while": 2}
 
@@ -163,7 +164,7 @@ class Context:
     handle (int) or None for a private stream.  Keyword options map to
     meb_set_option: screen ("fp16", "fp16_bulk", "fp32", "fp64"), eval_screen
     (same names), eval_shadow_exp (int), tick_loop ("graph", "host", "while"),
-    wait_cycles (int)."""
+    wait_cycles (int), batch_slots, release_scratch, blocking_sync (0 or 1)."""
 
     def __init__(self, device: int = 0, stream: int | None = None, **options):
         self._lib = load()
@@ -181,7 +182,10 @@ class Context:
                  "eval_screen": (MEB_OPT_EVAL_SCREEN, SCREEN_MODES),
                  "eval_shadow_exp": (MEB_OPT_EVAL_SHADOW_EXP, None),
                  "tick_loop": (MEB_OPT_TICK_LOOP, TICK_LOOPS),
-                 "wait_cycles": (MEB_OPT_WAIT_CYCLES, None)}
+                 "wait_cycles": (MEB_OPT_WAIT_CYCLES, None),
+                 "batch_slots": (MEB_OPT_BATCH_SLOTS, None),
+                 "release_scratch": (MEB_OPT_RELEASE_SCRATCH, None),
+                 "blocking_sync": (MEB_OPT_BLOCKING_SYNC, None)}
         if name not in table:
             raise ValueError(f"unknown option {name!r}")
         opt, names = table[name]

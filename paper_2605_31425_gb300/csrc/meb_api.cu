@@ -35,6 +35,9 @@ struct meb_ctx {
   int buf_d = 0;
   bool batch_per_item = false;  // meb_solve_batch: one scratch slot per instance
   bool release = false;         // free all device scratch at the end of each call
+  cudaMemPool_t mempool = nullptr;   // with release: the pool to allocate from (else the device's)
+  bool blocking = false;        // waits sleep on sync_ev instead of spinning (MEB_OPT_BLOCKING_SYNC)
+  cudaEvent_t sync_ev = nullptr;
   int depth = 0;                // nesting of public calls (a batch falls back to meb_solve)
   void* pool_ptr[32] = {};
   size_t pool_cap[32] = {};
@@ -121,7 +124,9 @@ static int fail(meb_ctx* ctx, int code, const char* fmt, ...) {
 // cudaFreeAsync), so that allocating and freeing on one context never waits
 // for work of another; otherwise plain cudaMalloc / cudaFree.
 static cudaError_t dev_alloc(meb_ctx* ctx, void** p, size_t bytes) {
-  return ctx->release ? cudaMallocAsync(p, bytes, ctx->stream) : cudaMalloc(p, bytes);
+  if (!ctx->release) return cudaMalloc(p, bytes);
+  return ctx->mempool ? cudaMallocFromPoolAsync(p, bytes, ctx->mempool, ctx->stream)
+                      : cudaMallocAsync(p, bytes, ctx->stream);
 }
 static void dev_free(meb_ctx* ctx, void* p) {
   if (!p) return;
@@ -182,6 +187,8 @@ static size_t solve_layout(Buffers* Bp, char* base, int64_t m, int d) {
   take(&B.E32, m_pad);
   take(&B.Hhi, dn);
   take(&B.Hlo, dn);
+  take(&B.Ainv, n1 <= kAinvMaxN ? (size_t)kAinvLen : 0);
+  if (n1 > kAinvMaxN) B.Ainv = nullptr;
   take(&B.R32, m_pad);
   take(&B.slot, m_pad);   // whole tiles are bulk-copied
   for (int k = 0; k < 2; k++) {
@@ -276,6 +283,15 @@ static int ensure_buffers(meb_ctx* ctx, int64_t m, int d) {
 }
 
 // Release every device scratch of the context (buffers, pools, tick graph).
+// Wait for the context's stream: a spin (cudaStreamSynchronize), or with
+// MEB_OPT_BLOCKING_SYNC a sleep on a blocking-sync event, so that many
+// threads waiting on their own contexts do not occupy the host cores.
+static cudaError_t ctx_sync(meb_ctx* ctx) {
+  if (!ctx->blocking || !ctx->sync_ev) return cudaStreamSynchronize(ctx->stream);
+  cudaError_t e = cudaEventRecord(ctx->sync_ev, ctx->stream);
+  return e == cudaSuccess ? cudaEventSynchronize(ctx->sync_ev) : e;
+}
+
 static void release_scratch(meb_ctx* ctx) {
   free_buffers(ctx);
   for (int k = 0; k < 32; k++) {
@@ -295,7 +311,7 @@ struct CallScope {
   }
   ~CallScope() {
     if (--c->depth == 0 && c->release) {
-      cudaStreamSynchronize(c->stream);
+      ctx_sync(c);
       release_scratch(c);
     }
   }
@@ -421,9 +437,9 @@ int meb_create(meb_ctx** out, int device, void* cuda_stream) {
 void meb_destroy(meb_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
-  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->stream) ctx_sync(ctx);
   release_scratch(ctx);
-  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->stream) ctx_sync(ctx);
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
   if (ctx->d_flags) cudaFree(ctx->d_flags);
@@ -435,6 +451,7 @@ void meb_destroy(meb_ctx* ctx) {
   drop_graphs(ctx);
   for (int k = 0; k < 16; k++)
     if (ctx->gev[k]) cudaEventDestroy(ctx->gev[k]);
+  if (ctx->sync_ev) cudaEventDestroy(ctx->sync_ev);
   delete ctx;
 }
 
@@ -469,9 +486,23 @@ int meb_set_option(meb_ctx* ctx, int32_t option, int64_t value) {
       if (value < 0 || value > 1) return fail(ctx, MEB_EINVAL, "release scratch: 0 or 1");
       ctx->release = value == 1;
       return MEB_OK;
+    case MEB_OPT_BLOCKING_SYNC:
+      if (value < 0 || value > 1) return fail(ctx, MEB_EINVAL, "blocking sync: 0 or 1");
+      if (value == 1 && !ctx->sync_ev) {
+        CK(cudaSetDevice(ctx->device));
+        CK(cudaEventCreateWithFlags(&ctx->sync_ev, cudaEventBlockingSync | cudaEventDisableTiming));
+      }
+      ctx->blocking = value == 1;
+      return MEB_OK;
     default:
       return fail(ctx, MEB_EINVAL, "unknown option %d", (int)option);
   }
+}
+
+// Library-internal (the serving loop, meb_serve.cpp): with
+// MEB_OPT_RELEASE_SCRATCH, allocate the context's scratch from `pool`.
+__attribute__((visibility("hidden"))) void meb_ctx_use_pool(meb_ctx* ctx, cudaMemPool_t pool) {
+  if (ctx) ctx->mempool = pool;
 }
 
 int meb_set_profiling(meb_ctx* ctx, int on) {
@@ -527,7 +558,7 @@ static int check_sizes(meb_ctx* ctx, int64_t m, int32_t d) {
 
 static int read_state(meb_ctx* ctx, const Buffers& B) {
   CK(cudaMemcpyAsync(ctx->h_st, B.st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
+  CK(ctx_sync(ctx));
   return MEB_OK;
 }
 
@@ -616,7 +647,7 @@ static int setup_instance(meb_ctx* ctx, Buffers& B, const double* C, const doubl
                       ctx->d_i64 + 1, s));
   CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  CK(ctx_sync(ctx));
   int bad;
   memcpy(&bad, ctx->h_scal + 1, sizeof(int));
   if (bad) return fail(ctx, MEB_EINVAL, "non-finite centre or radius, or negative radius");
@@ -637,6 +668,9 @@ static int init_state(meb_ctx* ctx, Buffers& B, int64_t m, int d, const meb_para
   ctx->h_st->sh_s = sc;
   ctx->h_st->sh_inv_s = 1.0 / sc;
   ctx->h_st->rt_abs = r0;   // initial radius; k_state_init scales it
+  // FP32 rows (the low-precision run): per-ball terms carry about
+  // (d + 16) 2^-24 relative error, of which sums keep about sqrt(d)
+  if (B.lowp) ctx->h_st->rnd = FLT_EPSILON * (2.0 + std::sqrt((double)d));
   CK(cudaMemcpyAsync(B.st, ctx->h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
   CK(launch_state_init(B, d, s));
   return MEB_OK;
@@ -752,13 +786,13 @@ static int finish_solve(meb_ctx* ctx, Buffers& Bx, Buffers& B, const double* C, 
   CK(launch_feas_cert(C, R, m, d, dcout, 0.0, INFINITY, 2, 1, B, ctx->d_scal + 2, ctx->d_i64 + 2,
                       ctx->d_i64 + 3, s));
   CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  CK(ctx_sync(ctx));
   const double r_alm = ctx->h_scal[1];
   const double r_out = ctx->h_scal[2];
   CK(launch_feas_cert(C, R, m, d, dcout, r_out, P.active_theta * r_out, 1, 0, B, nullptr, nullptr,
                       ctx->d_i64 + 5, s, /*reuse_bounds=*/true));
   CK(cudaMemcpyAsync(ctx->h_scal + 8, ctx->d_i64 + 5, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  CK(ctx_sync(ctx));
   memcpy(n_active_out, ctx->h_scal + 8, sizeof(int64_t));
   *r_alm_out = r_alm;
   *r_out_out = r_out;
@@ -842,12 +876,20 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
                        cudaMemcpyDeviceToDevice, s));
     if (!(flags & MEB_PTR_DEVICE))
       CK(cudaMemcpyAsync(c_out, dcout, sizeof(double) * d, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(ctx_sync(ctx));
     const double r = (m == 1) ? r0 : 0.0;
     const int64_t na = m;
-    for (int64_t k = 0; k < active_cap && k < na; k++) {
-      if (flags & MEB_PTR_DEVICE) CK(cudaMemcpy(active_idx + k, &k, sizeof(int64_t), cudaMemcpyHostToDevice));
-      else active_idx[k] = k;
+    const int64_t nw = std::min(active_cap, na);
+    if (flags & MEB_PTR_DEVICE) {
+      if (nw > 0) {
+        std::vector<int64_t> seq(nw);
+        for (int64_t k = 0; k < nw; k++) seq[k] = k;
+        CK(cudaMemcpyAsync(active_idx, seq.data(), sizeof(int64_t) * (size_t)nw,
+                           cudaMemcpyHostToDevice, s));
+        CK(ctx_sync(ctx));
+      }
+    } else {
+      for (int64_t k = 0; k < nw; k++) active_idx[k] = k;
     }
     if (info) {
       info->r = r; info->r_alm = r; info->scale = 1.0; info->n_active = na; info->status = 0;
@@ -893,7 +935,7 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
     rc = copy_out(ctx, active_idx, B.viol, sizeof(int64_t) * (size_t)ncp, flags);
     if (rc) return rc;
   }
-  CK(cudaStreamSynchronize(s));
+  CK(ctx_sync(ctx));
   return S.status == 1 ? MEB_OK : fail(ctx, MEB_ENOTCONV, "iteration cap reached");
 }
 
@@ -1027,7 +1069,7 @@ extern "C" int meb_feas_check(meb_ctx* ctx, const double* centers, const double*
   CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_i64, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(ctx->h_scal + 3, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  CK(ctx_sync(ctx));
   int bad;
   memcpy(&bad, ctx->h_scal + 3, sizeof(int));
   if (bad) return fail(ctx, MEB_EINVAL, "non-finite centre, radius or query, or negative radius");
@@ -1041,7 +1083,7 @@ extern "C" int meb_feas_check(meb_ctx* ctx, const double* centers, const double*
   if (ncp > 0) {
     rc = copy_out(ctx, viol_idx, B.viol, sizeof(int64_t) * (size_t)ncp, flags);
     if (rc) return rc;
-    CK(cudaStreamSynchronize(s));
+    CK(ctx_sync(ctx));
   }
   return MEB_OK;
 }
@@ -1080,7 +1122,7 @@ extern "C" int meb_get_multipliers(meb_ctx* ctx, unsigned flags, int64_t* idx, d
       CK(cudaMemcpyAsync(u, du, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(v, dv, sizeof(double) * (size_t)k * d, cudaMemcpyDeviceToHost, s));
     }
-    CK(cudaStreamSynchronize(s));
+    CK(ctx_sync(ctx));
     return MEB_OK;
   }
   // one ball (u = 1) or every ball the same point (u = 1/m); v = 0
@@ -1094,7 +1136,7 @@ extern "C" int meb_get_multipliers(meb_ctx* ctx, unsigned flags, int64_t* idx, d
     cudaError_t e = cudaMemcpyAsync(idx, hi, sizeof(int64_t) * (size_t)k, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(u, hu, sizeof(double) * (size_t)k, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(double) * (size_t)k * d, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = ctx_sync(ctx);
     cudaFreeHost(hi);
     cudaFreeHost(hu);
     CK(e);
@@ -1248,7 +1290,7 @@ static int batch_run(meb_ctx* ctx, const std::vector<BatchItemDev>& items, const
   if (ms) CK(cudaEventRecord(ctx->ev[1], s));
   std::vector<BatchOut> qo(n);
   CK(cudaMemcpyAsync(qo.data(), dout, sizeof(BatchOut) * n, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  CK(ctx_sync(ctx));
   if (ms) CK(cudaEventElapsedTime(ms, ctx->ev[0], ctx->ev[1]));
   for (int k = 0; k < n; k++) (*outs)[order[k]] = qo[k];
   return MEB_OK;
@@ -1326,7 +1368,7 @@ extern "C" int meb_solve_batch(meb_ctx* ctx, int32_t n, const meb_batch_item* it
         CK(cudaMemcpyAsync(it.active_idx, b.act, sizeof(int64_t) * (size_t)na, cudaMemcpyDeviceToHost, s));
     }
   }
-  CK(cudaStreamSynchronize(s));
+  CK(ctx_sync(ctx));
   ctx->stats.batch_instances += (int64_t)idx.size();
   if (bad) return fail(ctx, MEB_EINVAL, "invalid instance in the batch (its info has status -1)");
   if (notconv) return fail(ctx, MEB_ENOTCONV, "iteration cap reached by an instance");
@@ -1445,7 +1487,7 @@ static int save_warm(meb_ctx* ctx, Buffers& Bs, int d, const DevState& S, const 
   host_idx->resize(n);
   if (n > 0)
     CK(cudaMemcpyAsync(host_idx->data(), widx, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  CK(ctx_sync(ctx));
   *nw = n;
   return MEB_OK;
 }
@@ -1475,14 +1517,14 @@ static int solve_mixed(meb_ctx* ctx, const double* C, const double* R, int64_t m
   //    a multiplier
   CK(launch_final_point(B, d, dcout, ctx->d_scal + 1, s));
   CK(cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  CK(ctx_sync(ctx));
   const double r_hat = ctx->h_scal[1];
   const double fac = P.tol_red > 0 ? P.tol_red : std::max(10.0 * S1.kkt_max, 1e-3);
   CK(launch_feas_cert(C, R, m, d, dcout, r_hat, fac * r_hat, 1, 0, B, nullptr, nullptr,
                       ctx->d_i64 + 6, s));
   int64_t n_scr = 0;
   CK(cudaMemcpyAsync(&n_scr, ctx->d_i64 + 6, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  CK(ctx_sync(ctx));
   std::vector<int64_t> scr(n_scr);
   if (n_scr > 0)
     CK(cudaMemcpyAsync(scr.data(), B.viol, sizeof(int64_t) * (size_t)n_scr, cudaMemcpyDeviceToHost, s));
@@ -1540,17 +1582,17 @@ static int solve_mixed(meb_ctx* ctx, const double* C, const double* R, int64_t m
     // the reduced solution against every ball
     CK(launch_final_point(Br, d, dcout, ctx->d_scal + 1, s));
     CK(cudaMemcpyAsync(ctx->h_scal + 1, ctx->d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(ctx_sync(ctx));
     const double r_bar = ctx->h_scal[1];
     CK(launch_feas_cert(C, R, m, d, dcout, r_bar, eps_feas, 0, 1, B, ctx->d_scal + 2, ctx->d_i64,
                         ctx->d_i64 + 1, s));
     int64_t nv = 0;
     CK(cudaMemcpyAsync(&nv, ctx->d_i64 + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(ctx_sync(ctx));
     std::vector<int64_t> viol(nv), add;
     if (nv > 0) {
       CK(cudaMemcpyAsync(viol.data(), B.viol, sizeof(int64_t) * (size_t)nv, cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+      CK(ctx_sync(ctx));
       std::set_difference(viol.begin(), viol.end(), ired.begin(), ired.end(), std::back_inserter(add));
     }
     if (add.empty() || rounds >= P.max_readd || S2.status != 1) break;

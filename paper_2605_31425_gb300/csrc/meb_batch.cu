@@ -353,6 +353,7 @@ size_t batch_slot_layout(Buffers* Bp, char* base, int64_t m_cap, int d_cap, int6
   take(&B.R32, m_pad);
   take(&B.Hhi, (size_t)nd * nd);
   take(&B.Hlo, (size_t)nd * nd);
+  take(&B.Ainv, (size_t)kAinvLen);
   take(&B.H, (size_t)nd * nd);
   take(&B.slot, m_pad);
   for (int k = 0; k < 2; k++) {

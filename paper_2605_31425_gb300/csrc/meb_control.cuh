@@ -133,7 +133,7 @@ __device__ __forceinline__ void early_body_impl(const Buffers& B, DevState* st, 
     const double pi2_lb = 0.99 * t * st->inv_s * st->inv_s * 0.5;
     const double psi_lb = V.xt[0] + 0.5 * sigma * pi2_lb + 0.5 * tos * dx2;
     const double mag = fabs(V.xt[0]) + 0.5 * sigma * pi2_lb + 0.5 * tos * dx2;
-    const double allow = 64.0 * DBL_EPSILON * fmax(st->psi_mag, mag);
+    const double allow = 64.0 * st->rnd * fmax(st->psi_mag, mag);
     const double thr = st->psi + st->mu * st->eta * st->gdx + allow;
     int rej = 0;
     if (psi_lb > thr && st->bt < st->max_backtrack) {
@@ -242,7 +242,7 @@ __device__ __forceinline__ void control_a_body_impl(const Buffers& B, DevState* 
       st->psi = psi_t - s_last[P_UV2] / (2.0 * sigma);
       st->accept_mode = 0;
     } else if (st->phase == 1) {
-      const double allow = 64.0 * DBL_EPSILON * fmax(st->psi_mag, mag_t);
+      const double allow = 64.0 * st->rnd * fmax(st->psi_mag, mag_t);
       const bool ok = psi_t <= st->psi + st->mu * st->eta * st->gdx + allow;
       if (ok || st->bt >= st->max_backtrack) {
         st->psi = psi_t; st->psi_mag = mag_t;
@@ -381,7 +381,7 @@ __device__ __forceinline__ void control_b_body_impl(const Buffers& B, DevState* 
   const double dk2 = st->dx2_t;   // ||x - xk||^2 with x = xt
   const double lhs = 2.0 * sigma * fabs(la) + sigma * sigma * g2;
   const double rhs = st->rho * (st->last[P_DUV2] + tau * dk2);
-  const bool stop = (lhs <= rhs) || (sqrt(g2) <= 8.0 * DBL_EPSILON * st->gmag);
+  const bool stop = (lhs <= rhs) || (sqrt(g2) <= 8.0 * st->rnd * st->gmag);
   if (stop) {
     do_outer(st, V, d, sh);
     return;

@@ -5,6 +5,7 @@
 // reads back the small action/status fields.
 #pragma once
 #include <cuda_runtime.h>
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 
@@ -15,6 +16,8 @@ namespace meb {
 constexpr int kPassThreads = 256;   // balls per pass block (one per thread)
 constexpr int kPassWarps = kPassThreads / 32;
 constexpr int kMaxDenseN = 225;     // dense Newton solve for d+1 <= 225 (packed FP64 in smem)
+constexpr int kAinvMaxN = 112;      // n = d + 1 of the register Gauss-Jordan solve
+constexpr int kAinvLen = 28 * 256;  // float2 entries of its kept FP32 inverse
 constexpr int kSvecBlocks = 160;    // blocks of the support-row reduction
 constexpr int kSyrkTile = 32;
 constexpr int kSyrkRows = 32;       // support rows per SYRK block
@@ -68,6 +71,7 @@ struct DevState {
   double sh_s, sh_inv_s;  // scale of the FP16 shadow (s in solves; any power of two in evaluations)
   // parameters (scaled problem)
   double tol, rho, sigma_max, sigma_growth, sigma_ratio, tau, mu;
+  double rnd;   // rounding unit of the per-ball rows (FP64, or the FP32 low-precision run)
   int max_outer, max_ssn, max_backtrack, max_cg;
   // iteration state
   double sigma, inv_sigma;
@@ -90,6 +94,9 @@ struct DevState {
   int force_fp64_solve;        // every dense Newton system by the FP64 Cholesky
   int fp64_solves;             // count of FP64 Cholesky fallbacks
   int gj_inverses;             // count of FP32 Gauss-Jordan inverses
+  int gj_reuses;               // Newton systems solved with the kept inverse
+  int inv_valid;               // Buffers::Ainv holds the inverse of an H at sigma = kept_sigma
+  double kept_sigma;
   int early_rejects;           // trials rejected by the certified lower bound
   int reuse_lists;             // next pass: same point, new multipliers (skip the screen)
   int64_t ticks, max_ticks;    // controller ticks of the device-resident loop and their cap
@@ -140,6 +147,8 @@ struct Buffers {
   float* E32;           // [m_pad] per ball: absolute part E_i of the FP32 shadow error
   float* Hhi;           // [n1 x n1] fl32(H)
   float* Hlo;           // [n1 x n1] fl32(H - Hhi)
+  float2* Ainv;         // [kAinvLen] the last FP32 inverse of H (register layout of the
+                        // n <= 112 Gauss-Jordan solve); null: none kept
   bool use_x16;         // host side: the screens read X16
   bool bulk;            // host side: FP16 screens through the bulk-copy pipeline
   bool fp64_all;        // host side: no shadow is read; every ball goes through the FP64 rows
@@ -219,6 +228,7 @@ __host__ __device__ inline void state_defaults(DevState& S, int64_t m, int d, co
   S.sigma_ratio = P.sigma_ratio;
   S.tau = P.tau;
   S.mu = P.armijo_mu;
+  S.rnd = DBL_EPSILON;
   S.max_outer = P.max_outer;
   S.max_ssn = P.max_ssn;
   S.max_backtrack = P.max_backtrack;

@@ -7,10 +7,12 @@
 // within the budget.  Admitted small requests wait in one queue; each small
 // worker owns a context (its own stream, one scratch slot per instance,
 // scratch released and stream-ordered after every call) and, whenever it is
-// free, launches every queued request (up to max_group) as one
+// free, launches the queued requests (up to max_group) as one
 // meb_solve_batch.  A group launched while others are still on the GPU runs
 // beside them: its thread blocks take the SMs the running groups do not use
-// or release.  Large requests (m*d >= large_balls, or d beyond the batch
+// or release.  A group holds its worker until its slowest request ends, so
+// groups are kept small and workers many: the SMs stay busy while a long
+// request finishes.  Large requests (m*d >= large_balls, or d beyond the batch
 // solver's limit) go to large workers, one multi-block meb_solve each.
 // Completion frees the request's budget and admits the next ones.
 //
@@ -32,6 +34,9 @@
 #include <vector>
 
 #include "../../include/meb.h"
+
+// meb_api.cu: scratch of a context from a given pool (library-internal)
+extern "C" void meb_ctx_use_pool(meb_ctx* ctx, cudaMemPool_t pool);
 
 namespace {
 
@@ -72,6 +77,7 @@ struct meb_server {
   int64_t used = 0;
   meb_server_stats st{};
   bool stop = false;
+  cudaMemPool_t pool = nullptr;      // the workers' scratch and staging
   std::vector<std::thread> workers;
 };
 
@@ -122,6 +128,8 @@ void small_worker(meb_server* sv) {
   if (crc == MEB_OK) {
     meb_set_option(ctx, MEB_OPT_BATCH_SLOTS, 1);
     meb_set_option(ctx, MEB_OPT_RELEASE_SCRATCH, 1);
+    meb_set_option(ctx, MEB_OPT_BLOCKING_SYNC, 1);
+    meb_ctx_use_pool(ctx, sv->pool);
   }
   std::vector<Request*> group;
   std::vector<meb_batch_item> items;
@@ -172,7 +180,11 @@ void large_worker(meb_server* sv) {
   cudaSetDevice(sv->device);
   meb_ctx* ctx = nullptr;
   const int crc = meb_create(&ctx, sv->device, nullptr);
-  if (crc == MEB_OK) meb_set_option(ctx, MEB_OPT_RELEASE_SCRATCH, 1);
+  if (crc == MEB_OK) {
+    meb_set_option(ctx, MEB_OPT_RELEASE_SCRATCH, 1);
+    meb_set_option(ctx, MEB_OPT_BLOCKING_SYNC, 1);
+    meb_ctx_use_pool(ctx, sv->pool);
+  }
   for (;;) {
     Request* r = nullptr;
     {
@@ -209,24 +221,37 @@ extern "C" int meb_server_create(meb_server** out, int device, const meb_server_
   if (!sv) return MEB_ENOMEM;
   sv->device = device;
   sv->cfg = *cfg;
-  if (sv->cfg.small_workers <= 0) sv->cfg.small_workers = 16;
-  if (sv->cfg.large_workers <= 0) sv->cfg.large_workers = 1;
+  if (sv->cfg.small_workers <= 0) sv->cfg.small_workers = 64;
+  if (sv->cfg.large_workers <= 0) sv->cfg.large_workers = 2;
   if (sv->cfg.large_balls <= 0) sv->cfg.large_balls = (int64_t)1 << 24;
-  if (sv->cfg.max_group <= 0) sv->cfg.max_group = 32;
+  if (sv->cfg.max_group <= 0) sv->cfg.max_group = 4;
   if (params) sv->P = *params;
   else meb_params_default(&sv->P);
   if (cudaSetDevice(device) != cudaSuccess) {
     delete sv;
     return MEB_ECUDA;
   }
-  // the workers allocate and free stream-ordered from the device's default
-  // pool: keep freed memory in this process's pool (up to the budget) rather
-  // than returning it to the driver at every synchronisation
-  cudaMemPool_t mp;
-  if (cudaDeviceGetDefaultMemPool(&mp, device) == cudaSuccess) {
-    uint64_t keep = (uint64_t)sv->cfg.budget_bytes;
-    cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
+  // The workers allocate and free stream-ordered from a pool of the server's
+  // own.  Freed memory stays in it (up to the budget) instead of going back to
+  // the driver at every synchronisation.  A block freed on one worker's stream
+  // is reused by another only once that free has completed: with the
+  // allocator's internal dependencies a worker's launch would wait for
+  // another worker's batch, and the workers would run one after another.
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  if (cudaMemPoolCreate(&sv->pool, &props) != cudaSuccess) {
+    delete sv;
+    return MEB_ECUDA;
   }
+  uint64_t keep = (uint64_t)sv->cfg.budget_bytes;
+  int no = 0, yes = 1;
+  cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  cudaMemPoolSetAttribute(sv->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+  cudaMemPoolSetAttribute(sv->pool, cudaMemPoolReuseAllowOpportunistic, &yes);
+  cudaMemPoolSetAttribute(sv->pool, cudaMemPoolReuseFollowEventDependencies, &yes);
   for (int k = 0; k < sv->cfg.small_workers; k++) sv->workers.emplace_back(small_worker, sv);
   for (int k = 0; k < sv->cfg.large_workers; k++) sv->workers.emplace_back(large_worker, sv);
   *out = sv;
@@ -308,5 +333,6 @@ extern "C" void meb_server_destroy(meb_server* sv) {
   sv->cv_work.notify_all();
   for (auto& t : sv->workers) t.join();
   for (auto& kv : sv->live) delete kv.second;
+  if (sv->pool) cudaMemPoolDestroy(sv->pool);
   delete sv;
 }

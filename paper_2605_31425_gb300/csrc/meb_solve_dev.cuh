@@ -394,6 +394,13 @@ __device__ __forceinline__ float2 block_sum2f(float a, float b, float2* sh8) {
   return t;
 }
 
+// Kept inverse: while sigma is unchanged, H changes from one Newton step to
+// the next only through the t_k and the support, so the inverse of the last
+// H is tried first.  The refinement below converges with it when it
+// contracts the residual; the iteration count and the required contraction
+// bound the cost of a failed try, after which the inverse is recomputed.
+constexpr int kGjReuseIters = 8;
+
 __device__ __forceinline__ void newton_gj_reg_body(const Buffers& B, int d) {
   DevState* st = B.st;
   extern __shared__ double dyn_Lp[];   // the Cholesky fallback's factor
@@ -401,6 +408,7 @@ __device__ __forceinline__ void newton_gj_reg_body(const Buffers& B, int d) {
     newton_chol_body(B, d, dyn_Lp);
     return;
   }
+  static_assert(4 * kGjTile * 256 == kAinvLen && kGjRegN == kAinvMaxN, "kept inverse layout");
   __shared__ float s_row[2][kGjRegN], s_col[2][kGjRegN];
   __shared__ float s_b[kGjRegN], s_bh[kGjRegN], s_bl[kGjRegN], s_xh[kGjRegN], s_xl[kGjRegN];
   __shared__ float2 s_red[8];
@@ -411,88 +419,117 @@ __device__ __forceinline__ void newton_gj_reg_body(const Buffers& B, int d) {
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   // a[i][q] = (A[ty+16i][tx+32q], A[ty+16i][tx+32q+16]); column tx+112 is a zero dummy
   float2 a[kGjTile][4];
+  bool fresh = !(B.Ainv && st->inv_valid && st->kept_sigma == st->sigma);
+  bool ok = true, solved = false;
+  for (int attempt = 0; attempt < 2 && !solved; attempt++) {
+    if (fresh) {
 #pragma unroll
-  for (int i = 0; i < kGjTile; i++)
+      for (int i = 0; i < kGjTile; i++)
 #pragma unroll
-    for (int j = 0; j < 8; j++) {
-      const int row = ty + 16 * i, col = tx + 16 * j;
-      const float v = (j == 7) ? 0.0f
-                               : (row < n && col < n) ? B.Hhi[(int64_t)row * n + col]
-                                                      : (row == col ? 1.0f : 0.0f);
-      if (j & 1) a[i][j >> 1].y = v; else a[i][j >> 1].x = v;
+        for (int j = 0; j < 8; j++) {
+          const int row = ty + 16 * i, col = tx + 16 * j;
+          const float v = (j == 7) ? 0.0f
+                                   : (row < n && col < n) ? B.Hhi[(int64_t)row * n + col]
+                                                          : (row == col ? 1.0f : 0.0f);
+          if (j & 1) a[i][j >> 1].y = v; else a[i][j >> 1].x = v;
+        }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kGjTile; i++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) a[i][q] = B.Ainv[(i * 4 + q) * 256 + tid];
     }
-  for (int i = tid; i < kGjRegN; i += 256) {
-    const double b = (i < n) ? -V.g[i] : 0.0;   // solve H dx = -g
-    const float bh = __double2float_rn(b);
-    s_bh[i] = bh;
-    s_bl[i] = __double2float_rn(b - (double)bh);
-    s_b[i] = bh;
-    s_xh[i] = 0.0f;
-    s_xl[i] = 0.0f;
-  }
-  bool ok = true;
+    float bn = 0.0f;
+    for (int i = tid; i < kGjRegN; i += 256) {
+      const double b = (i < n) ? -V.g[i] : 0.0;   // solve H dx = -g
+      const float bh = __double2float_rn(b);
+      s_bh[i] = bh;
+      s_bl[i] = __double2float_rn(b - (double)bh);
+      s_b[i] = bh;
+      s_xh[i] = 0.0f;
+      s_xl[i] = 0.0f;
+      bn = fmaf(bh, bh, bn);
+    }
+    if (!fresh) bn = block_sum2f(bn, 0.0f, s_red).x;
+    if (fresh) {
 #pragma unroll
-  for (int kb = 0; kb < kGjTile; kb++) {
-    for (int kk = 0; kk < 16; kk++) {
-      const int k = 16 * kb + kk;
-      if (k < n && ok) {
-        const int bf = k & 1;
-        if (ty == kk) {
+      for (int kb = 0; kb < kGjTile; kb++) {
+        for (int kk = 0; kk < 16; kk++) {
+          const int k = 16 * kb + kk;
+          if (k < n && ok) {
+            const int bf = k & 1;
+            if (ty == kk) {
 #pragma unroll
-          for (int j = 0; j < kGjTile; j++)
-            s_row[bf][tx + 16 * j] = (j & 1) ? a[kb][j >> 1].y : a[kb][j >> 1].x;
-        }
-        if (tx == kk) {
+              for (int j = 0; j < kGjTile; j++)
+                s_row[bf][tx + 16 * j] = (j & 1) ? a[kb][j >> 1].y : a[kb][j >> 1].x;
+            }
+            if (tx == kk) {
 #pragma unroll
-          for (int i = 0; i < kGjTile; i++)
-            s_col[bf][ty + 16 * i] = (kb & 1) ? a[i][kb >> 1].y : a[i][kb >> 1].x;
-        }
-        __syncthreads();
-        const float p = s_row[bf][k];
-        ok = (p > 0.0f) && isfinite(p);   // the same for every thread
-        const float ip = __fdividef(1.0f, p);
-        float2 rc[4];
+              for (int i = 0; i < kGjTile; i++)
+                s_col[bf][ty + 16 * i] = (kb & 1) ? a[i][kb >> 1].y : a[i][kb >> 1].x;
+            }
+            __syncthreads();
+            const float p = s_row[bf][k];
+            ok = (p > 0.0f) && isfinite(p);   // the same for every thread
+            const float ip = __fdividef(1.0f, p);
+            float2 rc[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const float lo = s_row[bf][tx + 32 * q];
-          const float hi = (q < 3) ? s_row[bf][tx + 32 * q + 16] : 0.0f;
-          rc[q] = __fmul2_rn(make_float2(lo, hi), make_float2(ip, ip));
-        }
-        float cr[kGjTile];
+            for (int q = 0; q < 4; q++) {
+              const float lo = s_row[bf][tx + 32 * q];
+              const float hi = (q < 3) ? s_row[bf][tx + 32 * q + 16] : 0.0f;
+              rc[q] = __fmul2_rn(make_float2(lo, hi), make_float2(ip, ip));
+            }
+            float cr[kGjTile];
 #pragma unroll
-        for (int i = 0; i < kGjTile; i++) cr[i] = s_col[bf][ty + 16 * i];
+            for (int i = 0; i < kGjTile; i++) cr[i] = s_col[bf][ty + 16 * i];
 #pragma unroll
-        for (int i = 0; i < kGjTile; i++)
+            for (int i = 0; i < kGjTile; i++)
 #pragma unroll
-          for (int q = 0; q < 4; q++)
-            a[i][q] = __ffma2_rn(make_float2(-cr[i], -cr[i]), rc[q], a[i][q]);
-        if (ty == kk) {   // pivot row: A[k][j] / p, and 1/p on the diagonal
+              for (int q = 0; q < 4; q++)
+                a[i][q] = __ffma2_rn(make_float2(-cr[i], -cr[i]), rc[q], a[i][q]);
+            if (ty == kk) {   // pivot row: A[k][j] / p, and 1/p on the diagonal
 #pragma unroll
-          for (int j = 0; j < kGjTile; j++) {
-            const float rj = (j & 1) ? rc[j >> 1].y : rc[j >> 1].x;
-            const float v = (tx + 16 * j == k) ? ip : rj;
-            if (j & 1) a[kb][j >> 1].y = v; else a[kb][j >> 1].x = v;
-          }
-        }
-        if (tx == kk) {   // pivot column: -A[i][k] / p off the diagonal
+              for (int j = 0; j < kGjTile; j++) {
+                const float rj = (j & 1) ? rc[j >> 1].y : rc[j >> 1].x;
+                const float v = (tx + 16 * j == k) ? ip : rj;
+                if (j & 1) a[kb][j >> 1].y = v; else a[kb][j >> 1].x = v;
+              }
+            }
+            if (tx == kk) {   // pivot column: -A[i][k] / p off the diagonal
 #pragma unroll
-          for (int i = 0; i < kGjTile; i++) {
-            if (ty + 16 * i != k) {
-              const float v = -cr[i] * ip;
-              if (kb & 1) a[i][kb >> 1].y = v; else a[i][kb >> 1].x = v;
+              for (int i = 0; i < kGjTile; i++) {
+                if (ty + 16 * i != k) {
+                  const float v = -cr[i] * ip;
+                  if (kb & 1) a[i][kb >> 1].y = v; else a[i][kb >> 1].x = v;
+                }
+              }
             }
           }
         }
       }
+      if (tid == 0) {
+        st->gj_inverses += 1;
+        st->inv_valid = 0;
+      }
+      if (!ok) break;   // the FP64 Cholesky
+      if (B.Ainv) {
+#pragma unroll
+        for (int i = 0; i < kGjTile; i++)
+#pragma unroll
+          for (int q = 0; q < 4; q++) B.Ainv[(i * 4 + q) * 256 + tid] = a[i][q];
+      }
     }
-  }
-  __syncthreads();
-  if (ok) {
-    // x0 = A (-g) and at most two corrections dx += A r: the Newton direction
-    // needs a small relative error, not FP64 accuracy (the stop test, Armijo
-    // and KKT use the FP64 gradient and Psi)
-    float rn0 = 0.0f;
-    for (int it = 0; it < 3; it++) {
+    __syncthreads();
+    // x0 = A (-g) and corrections dx += A r: the Newton direction needs a
+    // small relative error, not FP64 accuracy (the stop test, Armijo and KKT
+    // use the FP64 gradient and Psi).  A fresh inverse gets two corrections
+    // and must halve the residual.  A kept one gets up to kGjReuseIters; it
+    // must halve the residual at every step, and is given up as soon as its
+    // rate cannot bring the residual to 1e-9 of -g within the steps left.
+    const int max_it = fresh ? 3 : kGjReuseIters;
+    float rn_prev = bn, rn0 = 0.0f;
+    bool conv = false;
+    for (int it = 0; it < max_it; it++) {
       // t = A s_b : partial rows over this thread's columns, reduced over tx
       float tv[kGjTile];
 #pragma unroll
@@ -528,7 +565,9 @@ __device__ __forceinline__ void newton_gj_reg_body(const Buffers& B, int d) {
         }
       }
       const float2 dx2 = block_sum2f(dn, xn, s_red);   // (barriers: s_xh, s_xl visible)
-      if (dx2.x <= 1e-16f * dx2.y || it == 2) break;
+      if (dx2.x <= 1e-16f * dx2.y) { conv = true; break; }
+      if (fresh && it == max_it - 1) { conv = true; break; }
+      if (it == max_it - 1) break;
       // r = -g - H x in double-float, rows reduced over tx
       float sa[kGjTile], la[kGjTile];
 #pragma unroll
@@ -570,13 +609,37 @@ __device__ __forceinline__ void newton_gj_reg_body(const Buffers& B, int d) {
         }
       }
       const float rr = block_sum2f(rn, 0.0f, s_red).x;   // (barriers: s_b visible)
-      if (it == 0) rn0 = rr;
-      else if (!(rr <= 0.25f * rn0)) { ok = false; break; }   // not contracting
+      if (fresh) {
+        // the second residual at most a quarter of the first (squared norms)
+        if (it == 0) rn0 = rr;
+        else if (!(rr <= 0.25f * rn0)) break;
+      } else {
+        if (!isfinite(rr)) break;
+        const float rel = rr / bn, q = rr / rn_prev;
+        if (!(rel > 1e-18f)) { conv = true; break; }
+        if (!(q <= 0.25f)) break;
+        const int left = max_it - 1 - it;
+        if ((float)left * __logf(q) > __logf(1e-18f / rel)) break;
+        rn_prev = rr;
+      }
     }
+    if (conv) {
+      solved = true;
+      if (tid == 0) {
+        if (!fresh) st->gj_reuses += 1;
+        st->inv_valid = B.Ainv ? 1 : 0;
+        st->kept_sigma = st->sigma;
+      }
+    } else if (fresh) {
+      ok = false;   // the FP64 Cholesky
+    } else {
+      fresh = true;   // the kept inverse did not contract: a new one
+    }
+    __syncthreads();
   }
-  if (tid == 0) st->gj_inverses += 1;
-  if (!ok) {
+  if (!ok || !solved) {
     // the FP64 Cholesky in the same launch (dynamic shared memory n(n+1)/2 doubles)
+    if (tid == 0) st->inv_valid = 0;
     __syncthreads();
     newton_chol_body(B, d, dyn_Lp);
     return;

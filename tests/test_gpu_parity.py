@@ -261,11 +261,15 @@ def test_tick_loops_agree():
     assert ctx.stats()["pass_launches"] > 0
     g2 = meb.solve(C, R, ctx=ctx)    # graph reused
     assert g2["r"] == g["r"] and np.array_equal(g2["c"], g["c"])
+    # waits that sleep, scratch freed after the call: same results
+    q = meb.solve(C, R, ctx=meb.Context(0, blocking_sync=1, release_scratch=1))
+    assert q["r"] == g["r"] and np.array_equal(q["c"], g["c"])
+    assert np.array_equal(q["active"], g["active"])
 
 
 def test_options_rejected():
     ctx = meb.Context(0)
     for name, val in (("screen", 7), ("tick_loop", 3), ("wait_cycles", -1),
-                      ("eval_shadow_exp", 100)):
+                      ("eval_shadow_exp", 100), ("blocking_sync", 2), ("batch_slots", -1)):
         with pytest.raises(meb.MebError):
             ctx.set_option(name, val)
