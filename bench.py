@@ -247,9 +247,18 @@ def sphere_workload(meb, torch, local, stream, workloads, out):
     ctx.reset_stats()
     lat, res, radii = timed_solves(meb, torch, ctx, dC, dR, 3, 1, stream)
     st = ctx.stats()
+    # one more solve with per-phase events (a sync per tick: not timed above)
+    ctx.set_profiling(True)
+    ctx.reset_stats()
+    meb.solve(dC, dR, ctx=ctx)
+    torch.cuda.synchronize()
+    ph = ctx.stats()["phase_ms"]
+    ctx.set_profiling(False)
     rel = [abs(r - 1.0) for r in radii]
     ok = sum(e <= 1e-8 for e in rel)
     out["sphere_m2e5_d2000"] = {
+        "phase_ms_profiled_solve": {"pass": ph[0], "support_rows_control": ph[1],
+                                    "newton_cg": ph[2], "multipliers": ph[3]},
         "value": ok / (sum(lat) / 1e3), "unit": UNIT, "steps": len(lat),
         "p50_ms": statistics.median(lat), "max_relerr": max(rel),
         "reference": "closed form r* = 1", "ssn_per_solve": res["ssn_iters"],
@@ -369,7 +378,7 @@ def paper_sweep(meb, torch, local, stream):
 
 
 def serving(meb, workloads, seconds, rate=2000.0, n_pool=256, small_workers=0, max_group=0,
-            large_balls=0):
+            large_balls=0, **server_flags):
     """Poisson arrivals at `rate` requests/s for `seconds`, instances drawn from
     a pool of ragged instances (1% large: m = 5e5, d = 128), under an 80 GB
     device-memory budget; every request's latency from submission to result.
@@ -381,7 +390,7 @@ def serving(meb, workloads, seconds, rate=2000.0, n_pool=256, small_workers=0, m
            for k in range(2)]
     t_arr, pick = workloads.poisson_arrivals(rate, seconds, n_pool, 1005, 0.01, len(big))
     sv = meb.Server(budget_bytes=80 * 10 ** 9, small_workers=small_workers, max_group=max_group,
-                    large_balls=large_balls)
+                    large_balls=large_balls, **server_flags)
     tickets = [None] * len(t_arr)
     t0 = time.perf_counter()
     for k, (ta, p) in enumerate(zip(t_arr, pick)):
@@ -401,6 +410,7 @@ def serving(meb, workloads, seconds, rate=2000.0, n_pool=256, small_workers=0, m
             "p99_ms": float(np.percentile(lat, 99)), "p50_small_ms": float(np.percentile(small_lat, 50)),
             "p99_small_ms": float(np.percentile(small_lat, 99)),
             "large_requests": int(np.sum(pick < 0)), "launches": st["launches"],
+            "failed": int(len(res) - ok),
             "peak_device_gb": st["peak_bytes"] / 1e9, "budget_gb": 80,
             "pool": f"{n_pool} ragged instances (seed 1005) + 2 large (m=5e5, d=128), pinned host memory",
             "small_workers": small_workers or "default", "max_group": max_group or "default",

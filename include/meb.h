@@ -115,6 +115,13 @@ typedef struct {
                                 (radius) + 4 (multiplier slot)             */
     int64_t batch_instances; /* instances solved by meb_solve_batch      */
     int64_t batch_fallbacks; /* of those, re-solved by the multi-block path */
+    double phase_ms[4];      /* with profiling, ticks driven by the host (the
+                                matrix-free Newton path, or MEB_OPT_TICK_LOOP
+                                1): elapsed device time of the pass (screen
+                                and FP64 rows), the support rows and
+                                controller, the Newton system (with the host's
+                                turnarounds between CG rounds) and the
+                                multiplier update, milliseconds            */
 } meb_stats;
 
 /* Create a context on `device`, issuing work on `cuda_stream` (a cudaStream_t;
@@ -277,7 +284,7 @@ int meb_tune_batch(meb_ctx *ctx, int32_t n, const meb_batch_item *items, int32_t
  * path on their own workers.  Each request is solved by exactly the steps it
  * would take alone: its results do not depend on the mix.
  * Zero fields of cfg take the defaults: 64 small workers, 2 large workers,
- * large_balls 2^24, groups of at most 4 requests.  The workers allocate from
+ * large_balls 2^27, groups of at most 4 requests.  The workers allocate from
  * a stream-ordered memory pool of the server's own, which keeps freed memory
  * (up to budget_bytes) for the next requests and never makes one worker's
  * allocation wait for another worker's work; they wait for the GPU asleep
@@ -290,8 +297,13 @@ typedef struct {
     int32_t small_workers;
     int32_t large_workers;
     int32_t max_group;
-    int32_t reserved;
+    int32_t flags;            /* MEB_SERVER_SPIN_WAITS, MEB_SERVER_DEVICE_POOL, or 0 */
 } meb_server_config;
+/* workers spin while they wait for the GPU (default: they sleep) */
+#define MEB_SERVER_SPIN_WAITS 1u
+/* workers allocate from the device's default stream-ordered pool (default: a
+   pool of the server's own) */
+#define MEB_SERVER_DEVICE_POOL 2u
 
 typedef struct {
     int64_t submitted, completed, failed;

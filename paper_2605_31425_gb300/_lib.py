@@ -21,6 +21,7 @@ MEB_OPT_SCREEN, MEB_OPT_EVAL_SCREEN, MEB_OPT_EVAL_SHADOW_EXP, MEB_OPT_TICK_LOOP,
     MEB_OPT_WAIT_CYCLES, MEB_OPT_BATCH_SLOTS, MEB_OPT_RELEASE_SCRATCH, \
     MEB_OPT_BLOCKING_SYNC = 1, 2, 3, 4, 5, 6, 7, 8
 SCREEN_MODES = {"fp16": 0, "fp16_bulk": 1, "fp32": 2, "fp64": 3}
+MEB_SERVER_SPIN_WAITS, MEB_SERVER_DEVICE_POOL = 1, 2
 TICK_LOOPS = {"graph": 0, "host": 1, "while": 2}
 
 _D = ct.POINTER(ct.c_double)
@@ -61,7 +62,7 @@ class MebBatchItem(ct.Structure):
 class MebServerConfig(ct.Structure):
     _fields_ = [
         ("budget_bytes", ct.c_int64), ("large_balls", ct.c_int64), ("small_workers", ct.c_int32),
-        ("large_workers", ct.c_int32), ("max_group", ct.c_int32), ("reserved", ct.c_int32),
+        ("large_workers", ct.c_int32), ("max_group", ct.c_int32), ("flags", ct.c_int32),
     ]
 
 
@@ -78,6 +79,7 @@ class MebStats(ct.Structure):
         ("kernel_launches", ct.c_int64), ("pass_launches", ct.c_int64), ("pass_ms", ct.c_double),
         ("pass_balls", ct.c_int64), ("pass_fp64_rows", ct.c_int64), ("pass_bytes", ct.c_int64),
         ("batch_instances", ct.c_int64), ("batch_fallbacks", ct.c_int64),
+        ("phase_ms", ct.c_double * 4),
     ]
 
 
@@ -227,7 +229,9 @@ class Context:
     def stats(self) -> dict:
         st = MebStats()
         self._check(self._lib.meb_get_stats(self._h, ct.byref(st)))
-        return {k: getattr(st, k) for k, _ in MebStats._fields_}
+        out = {k: getattr(st, k) for k, _ in MebStats._fields_}
+        out["phase_ms"] = list(st.phase_ms)
+        return out
 
     def _check(self, rc: int, ok=(MEB_OK,)):
         if rc not in ok:
@@ -563,10 +567,13 @@ class Server:
 
     def __init__(self, budget_bytes: int, device: int = 0, small_workers: int = 0,
                  large_workers: int = 0, large_balls: int = 0, max_group: int = 0,
-                 params: MebParams | None = None):
+                 params: MebParams | None = None, spin_waits: bool = False,
+                 device_pool: bool = False):
         self._lib = load()
+        flags = (MEB_SERVER_SPIN_WAITS if spin_waits else 0) | \
+            (MEB_SERVER_DEVICE_POOL if device_pool else 0)
         cfg = MebServerConfig(int(budget_bytes), int(large_balls), int(small_workers),
-                              int(large_workers), int(max_group), 0)
+                              int(large_workers), int(max_group), flags)
         h = ct.c_void_p()
         rc = self._lib.meb_server_create(ct.byref(h), int(device), ct.byref(cfg),
                                          ct.byref(params) if params is not None else None)

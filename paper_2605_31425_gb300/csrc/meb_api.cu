@@ -734,12 +734,26 @@ static int run_ticks(meb_ctx* ctx, Buffers& B, const double* C, const double* R,
     }
   } else {
     int64_t ticks = 0;
+    const bool prof = ctx->profiling != 0;
+    cudaEvent_t* pe = ctx->gev;   // phase marks (the graph loop's events are unused here)
+    if (prof && !pe[0])
+      for (int k = 0; k < 16; k++) CK(cudaEventCreate(&ctx->gev[k]));
+    auto phase = [&](int k, int a, int b) -> int {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, pe[a], pe[b]));
+      ctx->stats.phase_ms[k] += ms;
+      return MEB_OK;
+    };
     for (;;) {
+      if (prof) CK(cudaEventRecord(pe[10], s));
       CK(launch_pass(C, R, B, m, d, s, ctx->profiling ? ctx->ev[0] : nullptr,
                      ctx->profiling ? ctx->ev[1] : nullptr));
+      if (prof) CK(cudaEventRecord(pe[11], s));
       CK(launch_tick_control(B, m, d, s));
+      if (prof) CK(cudaEventRecord(pe[12], s));
       rc = read_state(ctx, B);
       if (rc) return rc;
+      if (prof && ((rc = phase(0, 10, 11)) || (rc = phase(1, 11, 12)))) return rc;
       if (ctx->profiling && ctx->h_st->screens > ctx->prof_screens) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
@@ -751,6 +765,7 @@ static int run_ticks(meb_ctx* ctx, Buffers& B, const double* C, const double* R,
       }
       ctx->prof_screens = ctx->h_st->screens;
       if (ctx->h_st->status != 0) break;
+      if (prof) CK(cudaEventRecord(pe[13], s));
       if (ctx->h_st->action == ACT_NEWTON) {
         if (dense) {
           CK(launch_newton_dense(B, d, s));
@@ -765,7 +780,13 @@ static int run_ticks(meb_ctx* ctx, Buffers& B, const double* C, const double* R,
           CK(launch_cg_finish(B, d, s));
         }
       }
+      if (prof) CK(cudaEventRecord(pe[14], s));
       CK(launch_mult_update(C, B, m, d, s));
+      if (prof) {
+        CK(cudaEventRecord(pe[15], s));
+        CK(ctx_sync(ctx));
+        if ((rc = phase(2, 13, 14)) || (rc = phase(3, 14, 15))) return rc;
+      }
       if (++ticks > max_ticks) return fail(ctx, MEB_ECUDA, "controller did not terminate");
     }
   }

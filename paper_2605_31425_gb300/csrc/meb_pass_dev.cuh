@@ -469,27 +469,58 @@ __device__ __forceinline__ void rows_block(const PassArgs& A, int bid) {
       const int sl = __shfl_sync(MEB_FULLMASK, mysl, q);
       const double* crow = A.C + ii * (int64_t)d;
       T nn = 0, pp = 0, dv = 0, vv = 0;
-      if (sl >= 0) {
-        const double* vrow = sv + (int64_t)sl * d;
-        for (int j = lane; j < d; j += 32) {
-          const T dl = LOWP ? (T)((x32_at(A.X32, A.m_pad, ii, j) - s_yf[j]) * (float)inv_s)
-                            : (T)((crow[j] - s_ct[j]) * (double)inv_s);
-          const T v = (T)vrow[j];
-          const T b = fma(v, inv_sigma, dl);
-          nn = fma(b, b, nn);
-          pp = fma(dl, dl, pp);
-          dv = fma(dl, v, dv);
-          vv = fma(v, v, vv);
+      if (LOWP) {
+        if (sl >= 0) {
+          const double* vrow = sv + (int64_t)sl * d;
+          for (int j = lane; j < d; j += 32) {
+            const T dl = (T)((x32_at(A.X32, A.m_pad, ii, j) - s_yf[j]) * (float)inv_s);
+            const T v = (T)vrow[j];
+            const T b = fma(v, inv_sigma, dl);
+            nn = fma(b, b, nn);
+            pp = fma(dl, dl, pp);
+            dv = fma(dl, v, dv);
+            vv = fma(v, v, vv);
+          }
+          nn = warp_sum_t(nn); pp = warp_sum_t(pp); dv = warp_sum_t(dv); vv = warp_sum_t(vv);
+        } else {
+          for (int j = lane; j < d; j += 32) {
+            const T dl = (T)((x32_at(A.X32, A.m_pad, ii, j) - s_yf[j]) * (float)inv_s);
+            nn = fma(dl, dl, nn);
+          }
+          nn = warp_sum_t(nn);
+          pp = nn;
         }
-        nn = warp_sum_t(nn); pp = warp_sum_t(pp); dv = warp_sum_t(dv); vv = warp_sum_t(vv);
       } else {
-        for (int j = lane; j < d; j += 32) {
-          const T dl = LOWP ? (T)((x32_at(A.X32, A.m_pad, ii, j) - s_yf[j]) * (float)inv_s)
-                            : (T)((crow[j] - s_ct[j]) * (double)inv_s);
-          nn = fma(dl, dl, nn);
+        // in units of s: e = c_i - c (rounded once), dl = e / s and b = dl + v / sigma
+        // are exact power-of-two scalings of e and b' = e + v (s / sigma), and so are
+        // the sums: one multiplication per coordinate fewer, the same results
+        const double s_is = (double)inv_sigma * st->s;
+        double nn2 = 0.0, pp2 = 0.0, dv2 = 0.0, vv2 = 0.0;
+        if (sl >= 0) {
+          const double* vrow = sv + (int64_t)sl * d;
+          for (int j = lane; j < d; j += 32) {
+            const double e = crow[j] - s_ct[j];
+            const double v = vrow[j];
+            const double b2 = fma(v, s_is, e);
+            nn2 = fma(b2, b2, nn2);
+            pp2 = fma(e, e, pp2);
+            dv2 = fma(e, v, dv2);
+            vv2 = fma(v, v, vv2);
+          }
+          nn2 = warp_sum_t(nn2); pp2 = warp_sum_t(pp2); dv2 = warp_sum_t(dv2); vv2 = warp_sum_t(vv2);
+        } else {
+          for (int j = lane; j < d; j += 32) {
+            const double e = crow[j] - s_ct[j];
+            nn2 = fma(e, e, nn2);
+          }
+          nn2 = warp_sum_t(nn2);
+          pp2 = nn2;
         }
-        nn = warp_sum_t(nn);
-        pp = nn;
+        const double is = (double)inv_s;
+        nn = (T)((nn2 * is) * is);
+        pp = (T)((pp2 * is) * is);
+        dv = (T)(dv2 * is);
+        vv = (T)vv2;
       }
       if (lane == q) { mnn = nn; mpp = pp; mdv = dv; mvv = vv; }
     }
@@ -666,6 +697,7 @@ __device__ __forceinline__ void svec_block(const double* __restrict__ C, const B
   __shared__ int s_off[kMaxPassBlocks + 1];   // candidate segment starts of the pass blocks
   __shared__ unsigned char s_cs[kSvecStage];
   __shared__ double s_sf[kSvecStage], s_in[kSvecStage], s_t[kSvecStage];
+  __shared__ float s_t32[kSvecStage];
   __shared__ double s_red[3 * 256];
   __shared__ double sh[32];
   const int k0 = bid * rpb, k1 = min(nS, k0 + rpb);
@@ -687,6 +719,7 @@ __device__ __forceinline__ void svec_block(const double* __restrict__ C, const B
     const int j = j0 + jl;
     const bool act = grp < G && j < d;
     double av = 0.0, aw = 0.0, atw = 0.0;
+    float atw32 = 0.0f;
     for (int r0 = k0; r0 < k1; r0 += kSvecStage) {
       const int nr = min(kSvecStage, k1 - r0);
       __syncthreads();
@@ -722,6 +755,7 @@ __device__ __forceinline__ void svec_block(const double* __restrict__ C, const B
           const double t = a * in;
           s_in[threadIdx.x] = in;
           s_t[threadIdx.x] = t;
+          s_t32[threadIdx.x] = (float)t;
           s_sf[threadIdx.x] = sigma * (0.5 * (a + n) * in);
           if (j0 == 0) {
             B.S_t[k] = t;
@@ -730,18 +764,17 @@ __device__ __forceinline__ void svec_block(const double* __restrict__ C, const B
         } else {
           s_in[threadIdx.x] = 1.0;
           s_t[threadIdx.x] = 0.0;
+          s_t32[threadIdx.x] = 0.0f;
           s_sf[threadIdx.x] = sigma;
           if (j0 == 0) B.S_t[k] = 0.0;
         }
       }
       __syncthreads();
-      if (act) {
+      if (act && LOWP) {
         for (int r = grp; r < nr; r += G) {
           const int64_t idx = s_idx[r];
           const int sl = s_sl[r];
-          double b = LOWP ? (double)((x32_at(B.X32, st->m_pad, idx, j) - B.vec.y32[j]) *
-                                     (float)inv_s)
-                          : (C[idx * d + j] - ct[j]) * inv_s;
+          double b = (double)((x32_at(B.X32, st->m_pad, idx, j) - B.vec.y32[j]) * (float)inv_s);
           if (sl >= 0) b = fma(sv[(int64_t)sl * d + j], inv_sigma, b);
           av = fma(s_sf[r], b, av);
           const int64_t k = r0 + r;
@@ -756,8 +789,43 @@ __device__ __forceinline__ void svec_block(const double* __restrict__ C, const B
             if (B.W32) B.W32[k * d + j] = (float)b;
           }
         }
+      } else if (act) {
+        // in units of s (as in the rows): b' = (c_k - c) + v (s / sigma) = s b
+        // exactly, so w = b / n = b' (1 / (n s)) and sum sf b = (sum sf b') / s
+        // are the same numbers with one multiplication per coordinate fewer
+        // With FP32 rows for the matrix-free products, those rows and the
+        // Jacobi preconditioner's sum t w^2 (both only shape the Newton
+        // direction) are formed off the FP64 pipe: the rows by integer
+        // truncation, the sum in FP32.
+        const double s_is = inv_sigma * st->s;
+        float* W32 = B.W32;
+        for (int r = grp; r < nr; r += G) {
+          const int64_t idx = s_idx[r];
+          const int sl = s_sl[r];
+          double b2 = C[idx * d + j] - ct[j];
+          if (sl >= 0) b2 = fma(sv[(int64_t)sl * d + j], s_is, b2);
+          av = fma(s_sf[r], b2, av);
+          const int64_t k = r0 + r;
+          if (s_cs[r] == CASE_M) {
+            const double wv = b2 * (s_in[r] * inv_s);
+            aw += wv;
+            B.W[k * d + j] = wv;
+            if (W32) {
+              const float w32 = f64_to_f32_trunc(wv);
+              atw32 = fmaf(s_t32[r] * w32, w32, atw32);
+              W32[k * d + j] = w32;
+            } else {
+              atw = fma(s_t[r] * wv, wv, atw);
+            }
+          } else {
+            const double b = b2 * inv_s;
+            B.W[k * d + j] = b;
+            if (W32) W32[k * d + j] = f64_to_f32_trunc(b);
+          }
+        }
       }
     }
+    if (!LOWP && B.W32) atw = (double)atw32;
     // the groups' sums, in group order
     __syncthreads();
     if (act) {
@@ -774,7 +842,7 @@ __device__ __forceinline__ void svec_block(const double* __restrict__ C, const B
         aw += s_red[3 * tt + 1];
         atw += s_red[3 * tt + 2];
       }
-      out[j] = av;
+      out[j] = LOWP ? av : av * inv_s;
       out[d + j] = aw;
       out[2 * d + j] = atw;
     }

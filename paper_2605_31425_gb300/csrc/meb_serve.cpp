@@ -13,7 +13,11 @@
 // or release.  A group holds its worker until its slowest request ends, so
 // groups are kept small and workers many: the SMs stay busy while a long
 // request finishes.  Large requests (m*d >= large_balls, or d beyond the batch
-// solver's limit) go to large workers, one multi-block meb_solve each.
+// solver's limit) go to large workers, one multi-block meb_solve each.  The
+// multi-block kernels need many SMs at once while every batch block holds an
+// SM for a whole solve, so each side waits for the other: the threshold is
+// high (2^27 coordinates, 1 GB of FP64 centres) and everything below it is
+// solved one thread block per request.
 // Completion frees the request's budget and admits the next ones.
 //
 // Each request is solved by the same steps whatever else is queued (one
@@ -128,7 +132,7 @@ void small_worker(meb_server* sv) {
   if (crc == MEB_OK) {
     meb_set_option(ctx, MEB_OPT_BATCH_SLOTS, 1);
     meb_set_option(ctx, MEB_OPT_RELEASE_SCRATCH, 1);
-    meb_set_option(ctx, MEB_OPT_BLOCKING_SYNC, 1);
+    if (!(sv->cfg.flags & MEB_SERVER_SPIN_WAITS)) meb_set_option(ctx, MEB_OPT_BLOCKING_SYNC, 1);
     meb_ctx_use_pool(ctx, sv->pool);
   }
   std::vector<Request*> group;
@@ -182,7 +186,7 @@ void large_worker(meb_server* sv) {
   const int crc = meb_create(&ctx, sv->device, nullptr);
   if (crc == MEB_OK) {
     meb_set_option(ctx, MEB_OPT_RELEASE_SCRATCH, 1);
-    meb_set_option(ctx, MEB_OPT_BLOCKING_SYNC, 1);
+    if (!(sv->cfg.flags & MEB_SERVER_SPIN_WAITS)) meb_set_option(ctx, MEB_OPT_BLOCKING_SYNC, 1);
     meb_ctx_use_pool(ctx, sv->pool);
   }
   for (;;) {
@@ -223,7 +227,7 @@ extern "C" int meb_server_create(meb_server** out, int device, const meb_server_
   sv->cfg = *cfg;
   if (sv->cfg.small_workers <= 0) sv->cfg.small_workers = 64;
   if (sv->cfg.large_workers <= 0) sv->cfg.large_workers = 2;
-  if (sv->cfg.large_balls <= 0) sv->cfg.large_balls = (int64_t)1 << 24;
+  if (sv->cfg.large_balls <= 0) sv->cfg.large_balls = (int64_t)1 << 27;
   if (sv->cfg.max_group <= 0) sv->cfg.max_group = 4;
   if (params) sv->P = *params;
   else meb_params_default(&sv->P);
@@ -237,21 +241,23 @@ extern "C" int meb_server_create(meb_server** out, int device, const meb_server_
   // is reused by another only once that free has completed: with the
   // allocator's internal dependencies a worker's launch would wait for
   // another worker's batch, and the workers would run one after another.
-  cudaMemPoolProps props;
-  memset(&props, 0, sizeof(props));
-  props.allocType = cudaMemAllocationTypePinned;
-  props.location.type = cudaMemLocationTypeDevice;
-  props.location.id = device;
-  if (cudaMemPoolCreate(&sv->pool, &props) != cudaSuccess) {
-    delete sv;
-    return MEB_ECUDA;
+  if (!(sv->cfg.flags & MEB_SERVER_DEVICE_POOL)) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&sv->pool, &props) != cudaSuccess) {
+      delete sv;
+      return MEB_ECUDA;
+    }
+    uint64_t keep = (uint64_t)sv->cfg.budget_bytes;
+    int no = 0, yes = 1;
+    cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaMemPoolSetAttribute(sv->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+    cudaMemPoolSetAttribute(sv->pool, cudaMemPoolReuseAllowOpportunistic, &yes);
+    cudaMemPoolSetAttribute(sv->pool, cudaMemPoolReuseFollowEventDependencies, &yes);
   }
-  uint64_t keep = (uint64_t)sv->cfg.budget_bytes;
-  int no = 0, yes = 1;
-  cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
-  cudaMemPoolSetAttribute(sv->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
-  cudaMemPoolSetAttribute(sv->pool, cudaMemPoolReuseAllowOpportunistic, &yes);
-  cudaMemPoolSetAttribute(sv->pool, cudaMemPoolReuseFollowEventDependencies, &yes);
   for (int k = 0; k < sv->cfg.small_workers; k++) sv->workers.emplace_back(small_worker, sv);
   for (int k = 0; k < sv->cfg.large_workers; k++) sv->workers.emplace_back(large_worker, sv);
   *out = sv;

@@ -90,8 +90,9 @@ cudaError_t launch_newton_dense(Buffers& B, int d, cudaStream_t s) {
 
 __global__ void __launch_bounds__(256) k_hvp_dot(Buffers B, int d, const double* __restrict__ q,
                                                   double* __restrict__ wq, int force) {
+  extern __shared__ float dyn_q32[];   // d floats with FP32 rows
   if (!force && !cg_gate(B.st)) return;
-  if (B.W32 && !force) hvp_dot_block<true>(B, d, q, wq, blockIdx.x, gridDim.x);
+  if (B.W32 && !force) hvp_dot_block<true>(B, d, q, wq, blockIdx.x, gridDim.x, dyn_q32);
   else hvp_dot_block<false>(B, d, q, wq, blockIdx.x, gridDim.x);
 }
 
@@ -125,7 +126,10 @@ cudaError_t launch_cg_setup(Buffers& B, int d, cudaStream_t s) {
 }
 
 cudaError_t launch_cg_iter(Buffers& B, int d, cudaStream_t s) {
-  k_hvp_dot<<<kHvpBlocks * 4, 256, 0, s>>>(B, d, B.vec.cg_p, B.wq, 0);
+  const size_t qsm = B.W32 ? sizeof(float) * (size_t)d : 0;
+  cudaError_t e = raise_smem_limit((const void*)k_hvp_dot, qsm);
+  if (e != cudaSuccess) return e;
+  k_hvp_dot<<<kHvpBlocks * 4, 256, qsm, s>>>(B, d, B.vec.cg_p, B.wq, 0);
   if (B.W32) {   // FP32 products: row groups x column chunks
     k_hvp_acc<<<dim3(kHvpGroups32, (d + 255) / 256), 256, 0, s>>>(B, d, B.vec.cg_p, B.wq, B.hpart, 0);
     k_cg_update<<<1, 256, 0, s>>>(B, d, kHvpGroups32);

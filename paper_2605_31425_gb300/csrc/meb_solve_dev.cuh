@@ -661,17 +661,25 @@ __device__ __forceinline__ void newton_gj_reg_body(const Buffers& B, int d) {
 // use the FP64 gradient and Psi).
 template <bool F32 = false>
 __device__ __forceinline__ void hvp_dot_block(const Buffers& B, int d, const double* __restrict__ q,
-                                              double* __restrict__ wq, int bid, int nb) {
+                                              double* __restrict__ wq, int bid, int nb,
+                                              float* s_q32 = nullptr) {
   const DevState* st = B.st;
   const int nS = st->nS;
   const int lane = threadIdx.x & 31;
+  if (F32 && s_q32) {   // q1 in FP32 once per block, not once per row
+    for (int j = threadIdx.x; j < d; j += blockDim.x) s_q32[j] = (float)q[1 + j];
+    __syncthreads();
+  }
   for (int k = (bid * 256 + threadIdx.x) >> 5; k < nS; k += (nb * 256) >> 5) {
     double t = 0.0;
     if (B.S_case[k] == CASE_M) {
       if (F32) {
         const float* w = B.W32 + (int64_t)k * d;
         float tf = 0.0f;
-        for (int j = lane; j < d; j += 32) tf = fmaf(w[j], (float)q[1 + j], tf);
+        if (s_q32)
+          for (int j = lane; j < d; j += 32) tf = fmaf(w[j], s_q32[j], tf);
+        else
+          for (int j = lane; j < d; j += 32) tf = fmaf(w[j], (float)q[1 + j], tf);
         t = (double)warp_sum_t(tf);
       } else {
         const double* w = B.W + (int64_t)k * d;
@@ -877,12 +885,21 @@ __device__ __forceinline__ void mult_rows_block(const double* __restrict__ C, co
     const int sl = ((unsigned)sl0 < (unsigned)nsup && sidx[sl0] == idx) ? sl0 : -1;
     const double a = B.S_a[k], n = B.S_n[k];
     const double f = (B.S_case[k] == CASE_I) ? 1.0 : 0.5 * (a + n) / n;
-    for (int j = lane; j < d; j += 32) {
-      double b = LOWP ? (double)((x32_at(B.X32, st->m_pad, idx, j) - B.vec.y32[j]) *
-                                 (float)inv_s)
-                      : (C[(int64_t)idx * d + j] - ct[j]) * inv_s;
-      if (sl >= 0) b = fma(sv[(int64_t)sl * d + j], inv_sigma, b);
-      nv[(int64_t)k * d + j] = sigma * f * b;
+    if (LOWP) {
+      for (int j = lane; j < d; j += 32) {
+        double b = (double)((x32_at(B.X32, st->m_pad, idx, j) - B.vec.y32[j]) * (float)inv_s);
+        if (sl >= 0) b = fma(sv[(int64_t)sl * d + j], inv_sigma, b);
+        nv[(int64_t)k * d + j] = sigma * f * b;
+      }
+    } else {
+      // in units of s: b' = (c_i - c) + v (s / sigma) = s b exactly, and
+      // sigma f b = b' (sigma f / s): the same numbers, one multiplication fewer
+      const double s_is = inv_sigma * st->s, sfs = (sigma * f) * inv_s;
+      for (int j = lane; j < d; j += 32) {
+        double b2 = C[(int64_t)idx * d + j] - ct[j];
+        if (sl >= 0) b2 = fma(sv[(int64_t)sl * d + j], s_is, b2);
+        nv[(int64_t)k * d + j] = b2 * sfs;
+      }
     }
     __syncwarp();   // every lane has read the old slot of ball idx
     if (lane == 0) {
