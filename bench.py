@@ -428,7 +428,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="headline only (no FP64 arm, no other workloads)")
-    ap.add_argument("--batch-instances", type=int, default=1024)
+    ap.add_argument("--batch-instances", type=int, default=4096)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--only", choices=["ragged", "sphere", "serving"], default=None,
                     help="run one extra line alone and print it (for profiling)")

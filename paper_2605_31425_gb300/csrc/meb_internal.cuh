@@ -18,7 +18,7 @@ constexpr int kPassWarps = kPassThreads / 32;
 constexpr int kMaxDenseN = 225;     // dense Newton solve for d+1 <= 225 (packed FP64 in smem)
 constexpr int kAinvMaxN = 112;      // n = d + 1 of the register Gauss-Jordan solve
 constexpr int kAinvLen = 28 * 256;  // float2 entries of its kept FP32 inverse
-constexpr int kSvecBlocks = 160;    // blocks of the support-row reduction
+constexpr int kSvecBlocks = 152;    // blocks of the support-row reduction (one per SM)
 constexpr int kSyrkTile = 32;
 constexpr int kSyrkRows = 32;       // support rows per SYRK block
 

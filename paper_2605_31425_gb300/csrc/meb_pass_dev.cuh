@@ -715,6 +715,125 @@ __device__ __forceinline__ void svec_block(const double* __restrict__ C, const B
   const int jl = (int)threadIdx.x - grp * (span >= 256 ? 256 : span);
   for (int b = threadIdx.x; b <= npb; b += 256) s_off[b] = B.cand_off[b];
   double s1t = 0.0;
+  // stage rows r0 .. r0+nr-1: index, slot (checked), case and the row scalars.
+  // Row k of S is entry k - s_off[b] of pass block b's candidate segment
+  // (b the last block with s_off[b] <= k); the first column round also writes
+  // the ordered support list S for the Newton and multiplier kernels.
+  auto stage = [&](int r0, int nr, bool first) {
+    if ((int)threadIdx.x < nr) {
+      const int k = r0 + threadIdx.x;
+      int lo = 0, hi = npb;   // s_off[lo] <= k < s_off[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[mid] <= k) lo = mid; else hi = mid;
+      }
+      const int64_t src = (int64_t)lo * seg + (k - s_off[lo]);
+      const int idx = B.cand_idx[src];
+      const int cs = B.cand_case[src];
+      const double a = B.cand_a[src], n = B.cand_n[src];
+      if (first) {
+        B.S_idx[k] = idx;
+        B.S_case[k] = (unsigned char)cs;
+        B.S_a[k] = a;
+        B.S_n[k] = n;
+        B.S_u[k] = B.cand_u[src];
+      }
+      const int sl0 = B.slot[idx];
+      const int sl = ((unsigned)sl0 < (unsigned)nsup && sidx[sl0] == idx) ? sl0 : -1;
+      s_idx[threadIdx.x] = idx;
+      s_sl[threadIdx.x] = sl;
+      s_cs[threadIdx.x] = (unsigned char)cs;
+      if (cs == CASE_M) {
+        const double in = 1.0 / n;
+        const double t = a * in;
+        s_in[threadIdx.x] = in;
+        s_t[threadIdx.x] = t;
+        s_t32[threadIdx.x] = (float)t;
+        s_sf[threadIdx.x] = sigma * (0.5 * (a + n) * in);
+        if (first) {
+          B.S_t[k] = t;
+          s1t += 1.0 + t;
+        }
+      } else {
+        s_in[threadIdx.x] = 1.0;
+        s_t[threadIdx.x] = 0.0;
+        s_t32[threadIdx.x] = 0.0f;
+        s_sf[threadIdx.x] = sigma;
+        if (first) B.S_t[k] = 0.0;
+      }
+    }
+  };
+  if (!LOWP && G == 1 && d >= 512) {
+    // wide rows: each thread takes NC columns 256 apart (more loads in flight
+    // per thread, the rows staged once for NC columns); every column's sums
+    // run over the rows in the same order as with one column per thread
+    auto cols = [&](auto ncv) {
+      constexpr int NC = decltype(ncv)::value;
+      const double s_is = inv_sigma * st->s;
+      float* W32 = B.W32;
+      for (int j0 = 0; j0 < d; j0 += 256 * NC) {
+        double av[NC], aw[NC], atw[NC];
+        float atw32[NC];
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+          av[c] = 0.0; aw[c] = 0.0; atw[c] = 0.0; atw32[c] = 0.0f;
+        }
+        for (int r0 = k0; r0 < k1; r0 += kSvecStage) {
+          const int nr = min(kSvecStage, k1 - r0);
+          __syncthreads();
+          stage(r0, nr, j0 == 0);
+          __syncthreads();
+          for (int r = 0; r < nr; r++) {
+            const int64_t idx = s_idx[r];
+            const int sl = s_sl[r];
+            const int64_t k = r0 + r;
+            const bool isM = s_cs[r] == CASE_M;
+            const double sf = s_sf[r], ins = s_in[r] * inv_s, tt = s_t[r];
+            const float t32 = s_t32[r];
+#pragma unroll
+            for (int c = 0; c < NC; c++) {
+              const int j = j0 + 256 * c + jl;
+              if (j < d) {
+                double b2 = C[idx * d + j] - ct[j];
+                if (sl >= 0) b2 = fma(sv[(int64_t)sl * d + j], s_is, b2);
+                av[c] = fma(sf, b2, av[c]);
+                if (isM) {
+                  const double wv = b2 * ins;
+                  aw[c] += wv;
+                  B.W[k * d + j] = wv;
+                  if (W32) {
+                    const float w32 = f64_to_f32_trunc(wv);
+                    atw32[c] = fmaf(t32 * w32, w32, atw32[c]);
+                    W32[k * d + j] = w32;
+                  } else {
+                    atw[c] = fma(tt * wv, wv, atw[c]);
+                  }
+                } else {
+                  const double b = b2 * inv_s;
+                  B.W[k * d + j] = b;
+                  if (W32) W32[k * d + j] = f64_to_f32_trunc(b);
+                }
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+          const int j = j0 + 256 * c + jl;
+          if (j < d) {
+            out[j] = av[c] * inv_s;
+            out[d + j] = aw[c];
+            out[2 * d + j] = W32 ? (double)atw32[c] : atw[c];
+          }
+        }
+      }
+    };
+    if (d >= 1024) cols(std::integral_constant<int, 4>());
+    else cols(std::integral_constant<int, 2>());
+    s1t = block_sum<256>(s1t, sh);
+    if (threadIdx.x == 0) out[3 * d] = s1t;
+    return;
+  }
   for (int j0 = 0; j0 < d; j0 += 256) {
     const int j = j0 + jl;
     const bool act = grp < G && j < d;
@@ -727,48 +846,7 @@ __device__ __forceinline__ void svec_block(const double* __restrict__ C, const B
       // Row k of S is entry k - s_off[b] of pass block b's candidate segment
       // (b the last block with s_off[b] <= k); the first j-round also writes
       // the ordered support list S for the Newton and multiplier kernels.
-      if ((int)threadIdx.x < nr) {
-        const int k = r0 + threadIdx.x;
-        int lo = 0, hi = npb;   // s_off[lo] <= k < s_off[hi]
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (s_off[mid] <= k) lo = mid; else hi = mid;
-        }
-        const int64_t src = (int64_t)lo * seg + (k - s_off[lo]);
-        const int idx = B.cand_idx[src];
-        const int cs = B.cand_case[src];
-        const double a = B.cand_a[src], n = B.cand_n[src];
-        if (j0 == 0) {
-          B.S_idx[k] = idx;
-          B.S_case[k] = (unsigned char)cs;
-          B.S_a[k] = a;
-          B.S_n[k] = n;
-          B.S_u[k] = B.cand_u[src];
-        }
-        const int sl0 = B.slot[idx];
-        const int sl = ((unsigned)sl0 < (unsigned)nsup && sidx[sl0] == idx) ? sl0 : -1;
-        s_idx[threadIdx.x] = idx;
-        s_sl[threadIdx.x] = sl;
-        s_cs[threadIdx.x] = (unsigned char)cs;
-        if (cs == CASE_M) {
-          const double in = 1.0 / n;
-          const double t = a * in;
-          s_in[threadIdx.x] = in;
-          s_t[threadIdx.x] = t;
-          s_t32[threadIdx.x] = (float)t;
-          s_sf[threadIdx.x] = sigma * (0.5 * (a + n) * in);
-          if (j0 == 0) {
-            B.S_t[k] = t;
-            s1t += 1.0 + t;
-          }
-        } else {
-          s_in[threadIdx.x] = 1.0;
-          s_t[threadIdx.x] = 0.0;
-          s_t32[threadIdx.x] = 0.0f;
-          s_sf[threadIdx.x] = sigma;
-          if (j0 == 0) B.S_t[k] = 0.0;
-        }
-      }
+      stage(r0, nr, j0 == 0);
       __syncthreads();
       if (act && LOWP) {
         for (int r = grp; r < nr; r += G) {

@@ -7,6 +7,8 @@
 // The iterate lives on the scaled problem (data divided by the power of two
 // s); the streaming kernels read the unscaled input.  The controller kernels
 // run on one block; their vector work (length d + 1) is spread over it.
+#include <algorithm>
+
 #include "meb_solve_dev.cuh"
 
 namespace meb {
@@ -130,9 +132,11 @@ cudaError_t launch_cg_iter(Buffers& B, int d, cudaStream_t s) {
   cudaError_t e = raise_smem_limit((const void*)k_hvp_dot, qsm);
   if (e != cudaSuccess) return e;
   k_hvp_dot<<<kHvpBlocks * 4, 256, qsm, s>>>(B, d, B.vec.cg_p, B.wq, 0);
-  if (B.W32) {   // FP32 products: row groups x column chunks
-    k_hvp_acc<<<dim3(kHvpGroups32, (d + 255) / 256), 256, 0, s>>>(B, d, B.vec.cg_p, B.wq, B.hpart, 0);
-    k_cg_update<<<1, 256, 0, s>>>(B, d, kHvpGroups32);
+  if (B.W32) {   // FP32 products: row groups x column chunks, two blocks per SM
+    const int chunks = (d + 255) / 256;
+    const int groups = std::max(1, std::min(kHvpGroups32, (2 * 152 + chunks - 1) / chunks));
+    k_hvp_acc<<<dim3(groups, chunks), 256, 0, s>>>(B, d, B.vec.cg_p, B.wq, B.hpart, 0);
+    k_cg_update<<<1, 256, 0, s>>>(B, d, groups);
   } else {
     k_hvp_acc<<<kHvpBlocks, 256, 0, s>>>(B, d, B.vec.cg_p, B.wq, B.hpart, 0);
     k_cg_update<<<1, 256, 0, s>>>(B, d, kHvpBlocks);

@@ -746,9 +746,9 @@ __device__ __forceinline__ void hvp_acc_block(const Buffers& B, int d, const dou
   if (threadIdx.x == 0 && jb == 0) out[0] = s0;
 }
 
-// Row groups of the FP32 products in the multi-block CG (partials per entry
-// summed by the CG update).
-constexpr int kHvpGroups32 = 32;
+// At most this many row groups in the FP32 products of the multi-block CG
+// (partials per entry summed by the CG update; the partial buffer holds 152).
+constexpr int kHvpGroups32 = 152;
 
 // y = tau/sigma q + sigma (n_I q + 1/2 [n_M q0 + S0 ; q0 sum w + sum(1+t) q1] + acc)
 __device__ inline void hvp_finish(DevState* st, const DevVecs& V, int d, const double* q,
