@@ -247,13 +247,16 @@ def sphere_workload(meb, torch, local, stream, workloads, out):
     ctx.reset_stats()
     lat, res, radii = timed_solves(meb, torch, ctx, dC, dR, 3, 1, stream)
     st = ctx.stats()
-    # one more solve with per-phase events (a sync per tick: not timed above)
+    # one more solve, driven from the host with per-phase events (a sync per
+    # tick: not timed above)
+    ctx.set_option("tick_loop", "host")
     ctx.set_profiling(True)
     ctx.reset_stats()
     meb.solve(dC, dR, ctx=ctx)
     torch.cuda.synchronize()
     ph = ctx.stats()["phase_ms"]
     ctx.set_profiling(False)
+    ctx.set_option("tick_loop", "graph")
     rel = [abs(r - 1.0) for r in radii]
     ok = sum(e <= 1e-8 for e in rel)
     out["sphere_m2e5_d2000"] = {
@@ -415,6 +418,27 @@ def serving(meb, workloads, seconds, rate=2000.0, n_pool=256, small_workers=0, m
             "pool": f"{n_pool} ragged instances (seed 1005) + 2 large (m=5e5, d=128), pinned host memory",
             "small_workers": small_workers or "default", "max_group": max_group or "default",
             "large_balls": large_balls or "default"}
+
+
+def serving_in_own_process(seconds, local):
+    """The serving line, from a process of its own on the same GPU (one server
+    per process is the supported use: a server created in a process whose
+    earlier server served requests ran slower); this process's cached device
+    memory is released first."""
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("RANK", "LOCAL_RANK", "WORLD_SIZE", "LOCAL_WORLD_SIZE", "GROUP_RANK")}
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    env["CUDA_VISIBLE_DEVICES"] = vis.split(",")[local] if vis else str(local)
+    cmd = [sys.executable, os.path.abspath(__file__), "--only", "serving",
+           "--serve-seconds", str(seconds)]
+    p = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    for ln in reversed(p.stdout.strip().splitlines()):
+        if ln.startswith("{"):
+            out = json.loads(ln)
+            out.pop("only", None)
+            out["process"] = "its own (bench.py --only serving)"
+            return out
+    return {"error": f"exit {p.returncode}: {p.stderr.strip()[-300:]}"}
 
 
 def main():
@@ -590,7 +614,9 @@ def main():
             extra["ragged_batch"] = ragged_batch(meb, torch, local, stream, workloads,
                                                  args.batch_instances)
         if args.serve_seconds > 0:
-            extra["serving"] = serving(meb, workloads, args.serve_seconds)
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            extra["serving"] = serving_in_own_process(args.serve_seconds, local)
         extra["paper_sweep"] = paper_sweep(meb, torch, local, stream)
 
     cpu = None

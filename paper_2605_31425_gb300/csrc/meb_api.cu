@@ -55,9 +55,10 @@ struct meb_ctx {
     cudaGraphExec_t gexec = nullptr;
     const void* key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int64_t m = 0;
-    int d = 0, mode = -1, var = -1, prof = -1, lowp = -1;
+    int d = 0, mode = -1, var = -1, prof = -1, lowp = -1, dense = -1;
     long long wait = -1;
   } tg[2];
+  cudaStream_t stream2 = nullptr;   // captures the CG loop bodies of tick graphs
   int tg_next = 0;
   cudaEvent_t gev[2 * 8] = {};
   // the reduced instance of the mixed-precision pipeline
@@ -446,6 +447,7 @@ void meb_destroy(meb_ctx* ctx) {
   if (ctx->d_scal) cudaFree(ctx->d_scal);
   if (ctx->d_i64) cudaFree(ctx->d_i64);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
   for (int k = 0; k < 2; k++)
     if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
   drop_graphs(ctx);
@@ -562,20 +564,61 @@ static int read_state(meb_ctx* ctx, const Buffers& B) {
   return MEB_OK;
 }
 
+// During the capture of a tick graph on s: append a conditional while node
+// (its handle defaults to 1 at every launch, so the body runs at least once)
+// whose body, captured on the context's second stream, is one CG iteration
+// and k_cg_cond; then continue the capture after the node.
+static cudaError_t cg_loop_node(meb_ctx* ctx, Buffers& B, int d, cudaStream_t s) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &graph, &deps, nullptr, &ndeps);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive || !graph) return cudaErrorStreamCaptureInvalidated;
+  std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+  memset(npbuf, 0, sizeof(npbuf));
+  cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(npbuf);
+  np->type = cudaGraphNodeTypeConditional;
+  np->conditional.handle = h;
+  np->conditional.type = cudaGraphCondTypeWhile;
+  np->conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, graph, dv.empty() ? nullptr : dv.data(), nullptr, dv.size(), np);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = np->conditional.phGraph_out[0];
+  cudaStream_t s2 = ctx->stream2;
+  e = cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return e;
+  e = launch_cg_iter(B, d, s2);
+  if (e == cudaSuccess) e = launch_cg_cond(B, h, s2);
+  cudaGraph_t got = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(s2, &got);
+  if (e != cudaSuccess) return e;
+  if (e2 != cudaSuccess) return e2;
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
 // Build (or reuse) the tick graph of buffer set B: kUnrollTicks ticks of
-// { pass; controller; Newton (dense); multiplier update } (mode 0), or a
-// while-node running ticks until the controller stops (mode 2).  Every kernel
-// of the tick is gated on the controller's action, so the tick is a fixed
-// sequence.  *out: the cached entry.
+// { pass; controller; Newton; multiplier update } (mode 0; the matrix-free
+// Newton system as CG setup, a while node of CG iterations and the finish),
+// or a while-node running ticks until the controller stops (mode 2, dense).
+// Every kernel of the tick is gated on the controller's action, so the tick
+// is a fixed sequence.  *out: the cached entry.
 static int solve_graph(meb_ctx* ctx, Buffers& B, const double* C, const double* R, int64_t m,
-                       int d, meb_ctx::TickGraph** out) {
+                       int d, bool dense, meb_ctx::TickGraph** out) {
   const int mode = ctx->loop_mode;
   const int prof = ctx->profiling;
   const void* xs = B.use_x16 ? (const void*)B.X16 : (const void*)B.X32;
   for (auto& g : ctx->tg) {
     if (g.gexec && g.key[0] == C && g.key[1] == R && g.key[2] == B.st && g.key[3] == xs &&
         g.key[4] == B.W && g.var == screen_variant(B, d) && g.wait == B.wait_cycles &&
-        g.m == m && g.d == d && g.mode == mode && g.prof == prof && g.lowp == (int)B.lowp) {
+        g.m == m && g.d == d && g.mode == mode && g.prof == prof && g.lowp == (int)B.lowp &&
+        g.dense == (int)dense) {
       *out = &g;
       return MEB_OK;
     }
@@ -614,13 +657,24 @@ static int solve_graph(meb_ctx* ctx, Buffers& B, const double* C, const double* 
     if (e != cudaSuccess) return fail(ctx, MEB_ECUDA, "graph capture: %s", cudaGetErrorString(e));
     CK(e2);
   } else {
+    if (!dense && !ctx->stream2)
+      CK(cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking));
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
     for (int t = 0; t < kUnrollTicks && e == cudaSuccess; t++) {
       // profiling: CUDA events around every k_screen of the batch (event nodes)
       e = prof ? launch_pass(C, R, B, m, d, s, ctx->gev[2 * t], ctx->gev[2 * t + 1], t)
                : launch_pass(C, R, B, m, d, s);
       if (e == cudaSuccess) e = launch_tick_control(B, m, d, s);
-      if (e == cudaSuccess) e = launch_newton_dense(B, d, s);
+      if (dense) {
+        if (e == cudaSuccess) e = launch_newton_dense(B, d, s);
+      } else {
+        // matrix-free Newton system: CG setup, then a conditional while node
+        // whose body is one CG iteration and the loop condition, then the
+        // finish (each kernel gated on the controller's action)
+        if (e == cudaSuccess) e = launch_cg_setup(B, d, s);
+        if (e == cudaSuccess) e = cg_loop_node(ctx, B, d, s);
+        if (e == cudaSuccess) e = launch_cg_finish(B, d, s);
+      }
       if (e == cudaSuccess) e = launch_mult_update(C, B, m, d, s);
     }
     cudaError_t e2 = cudaStreamEndCapture(s, &g.graph);
@@ -631,7 +685,7 @@ static int solve_graph(meb_ctx* ctx, Buffers& B, const double* C, const double* 
   g.key[0] = C; g.key[1] = R; g.key[2] = B.st; g.key[3] = xs; g.key[4] = B.W;
   g.var = screen_variant(B, d);
   g.wait = B.wait_cycles;
-  g.m = m; g.d = d; g.mode = mode; g.prof = prof; g.lowp = (int)B.lowp;
+  g.m = m; g.d = d; g.mode = mode; g.prof = prof; g.lowp = (int)B.lowp; g.dense = (int)dense;
   *out = &g;
   return MEB_OK;
 }
@@ -677,8 +731,9 @@ static int init_state(meb_ctx* ctx, Buffers& B, int64_t m, int d, const meb_para
 }
 
 // The controller ticks on buffer set B until the controller stops (status in
-// ctx->h_st afterwards): graph batches, a while-node graph, or host launches
-// (the CG path and MEB_OPT_TICK_LOOP = 1).
+// ctx->h_st afterwards): graph batches, a while-node graph (dense Newton path),
+// or host launches (MEB_OPT_TICK_LOOP = 1, and the while mode on the
+// matrix-free path or with profiling).
 static int run_ticks(meb_ctx* ctx, Buffers& B, const double* C, const double* R, int64_t m,
                      int d, const meb_params& P) {
   cudaStream_t s = ctx->stream;
@@ -691,10 +746,14 @@ static int run_ticks(meb_ctx* ctx, Buffers& B, const double* C, const double* R,
                                          : m * (B.use_x16 ? 16 * ((d4 + 1) / 2) + 12 : 16 * d4 + 12);
   const int64_t max_ticks = tick_cap(P);
   int rc;
-  if (dense && ctx->loop_mode != 1 && !(ctx->profiling && ctx->loop_mode == 2)) {
+  // graph ticks: batches of kUnrollTicks (both Newton paths), or the while
+  // node (dense path, without profiling); otherwise host launches
+  const bool graph_ticks =
+      ctx->loop_mode == 0 || (ctx->loop_mode == 2 && dense && !ctx->profiling);
+  if (graph_ticks) {
     // device-resident ticks: graph launches, one status read per kUnrollTicks ticks
     meb_ctx::TickGraph* g = nullptr;
-    rc = solve_graph(ctx, B, C, R, m, d, &g);
+    rc = solve_graph(ctx, B, C, R, m, d, dense, &g);
     if (rc) return rc;
     const int64_t before = B.launches;
     if (ctx->loop_mode == 2) {
@@ -730,7 +789,10 @@ static int run_ticks(meb_ctx* ctx, Buffers& B, const double* C, const double* R,
         if (ctx->h_st->status != 0) break;
         if (ticks > max_ticks) return fail(ctx, MEB_ECUDA, "controller did not terminate");
       }
-      B.launches = before + ticks * tick_launches(d);
+      // dense: a fixed count per tick; matrix-free: pass, controller, CG
+      // setup and finish, multipliers, plus 4 per run of the CG loop body
+      B.launches = before + (dense ? ticks * tick_launches(d)
+                                   : ticks * 6 + 4 * ctx->h_st->cg_bodies);
     }
   } else {
     int64_t ticks = 0;

@@ -100,6 +100,7 @@ struct DevState {
   int early_rejects;           // trials rejected by the certified lower bound
   int reuse_lists;             // next pass: same point, new multipliers (skip the screen)
   int64_t ticks, max_ticks;    // controller ticks of the device-resident loop and their cap
+  int64_t cg_bodies;           // runs of the CG loop body in the tick graph (launch count)
   int screen_log[8];           // profiling: tick t of a graph batch ran a full screen
   unsigned int ctr_screen, ctr_rows, ctr_svec, ctr_slots;   // last-block-done tickets
   int screens;                 // full FP32 screens run
@@ -370,5 +371,6 @@ cudaError_t launch_warm_start(Buffers& B, int d, const double* wx, double sigma,
                               const int64_t* ired, int64_t nred, cudaStream_t s);
 cudaError_t launch_map_idx(int64_t* idx, int64_t n, const int64_t* map, cudaStream_t s);
 cudaError_t launch_loop_cond(Buffers& B, cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_cg_cond(Buffers& B, cudaGraphConditionalHandle h, cudaStream_t s);
 
 }  // namespace meb

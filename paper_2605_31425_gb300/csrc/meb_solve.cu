@@ -57,9 +57,11 @@ __global__ void __launch_bounds__(256, 1) k_newton_gj_reg(Buffers B, int d) {
 int newton_dense_launches(int d) { return d + 1 <= kGjRegN ? 3 : 4; }
 
 // Host set-up outside any stream capture: dynamic shared memory limits.
+static cudaError_t prepare_hvp(int d);
+
 cudaError_t prepare_newton(int d) {
   const int n = d + 1;
-  if (n > kMaxDenseN) return cudaSuccess;   // matrix-free path
+  if (n > kMaxDenseN) return prepare_hvp(d);   // matrix-free path
   const size_t shc = sizeof(double) * (size_t)n * (n + 1) / 2;
   cudaError_t e = cudaSuccess;
   if (n <= kGjRegN) return raise_smem_limit((const void*)k_newton_gj_reg, shc);
@@ -125,6 +127,11 @@ cudaError_t launch_cg_setup(Buffers& B, int d, cudaStream_t s) {
   k_cg_setup<<<1, 256, 0, s>>>(B, d);
   B.launches += 1;
   return cudaGetLastError();
+}
+
+// the FP32 query of the products in shared memory (set before any capture)
+static cudaError_t prepare_hvp(int d) {
+  return raise_smem_limit((const void*)k_hvp_dot, sizeof(float) * (size_t)d);
 }
 
 cudaError_t launch_cg_iter(Buffers& B, int d, cudaStream_t s) {
@@ -259,6 +266,20 @@ __global__ void k_loop_cond(Buffers B, cudaGraphConditionalHandle h) {
 cudaError_t launch_loop_cond(Buffers& B, cudaGraphConditionalHandle h, cudaStream_t s) {
   k_loop_cond<<<1, 1, 0, s>>>(B, h);
   B.launches += 1;
+  return cudaGetLastError();
+}
+
+// The condition of the CG loop node of a tick graph: another CG iteration
+// while the conjugate gradients of this Newton system run (cg_update ends them
+// at convergence or at max_cg, so the loop ends).
+__global__ void k_cg_cond(Buffers B, cudaGraphConditionalHandle h) {
+  DevState* st = B.st;
+  st->cg_bodies += 1;
+  cudaGraphSetConditional(h, cg_gate(st) ? 1u : 0u);
+}
+
+cudaError_t launch_cg_cond(Buffers& B, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_cg_cond<<<1, 1, 0, s>>>(B, h);
   return cudaGetLastError();
 }
 

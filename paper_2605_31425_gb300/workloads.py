@@ -180,4 +180,7 @@ def workload(name: str):
     if name == "sphere_m2e5_d2000":
         C, R, _ = sphere(200_000, 2000, 1003)
         return C, R
+    if name == "sphere_m5e4_d2000":   # quarter-size sphere instance for counter captures
+        C, R, _ = sphere(50_000, 2000, 1013)
+        return C, R
     raise KeyError(name)

@@ -267,6 +267,23 @@ def test_tick_loops_agree():
     assert np.array_equal(q["active"], g["active"])
 
 
+def test_tick_loops_agree_matrix_free():
+    """d + 1 > 225: the CG loop runs inside the tick graph (a conditional
+    while node per tick) or from the host: the same kernels in the same
+    order, bit-identical."""
+    C, R = workloads.cube(6000, 300, 23, 0.05)
+    res = {k: meb.solve(C, R, ctx=meb.Context(0, tick_loop=k)) for k in ("graph", "host", "while")}
+    g = res["graph"]
+    assert g["cg_iters"] > 0
+    for k in ("host", "while"):
+        h = res[k]
+        assert g["r"] == h["r"] and np.array_equal(g["c"], h["c"]), k
+        assert g["passes"] == h["passes"] and g["cg_iters"] == h["cg_iters"], k
+        assert np.array_equal(g["active"], h["active"]), k
+    o = oracle.solve(C, R, tol=1e-12)
+    assert abs(g["r"] - o["r"]) <= 1e-8 * o["r"]
+
+
 def test_options_rejected():
     ctx = meb.Context(0)
     for name, val in (("screen", 7), ("tick_loop", 3), ("wait_cycles", -1),
