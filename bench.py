@@ -66,7 +66,7 @@ ROOFLINE_SOLVES = 3
 # screen per ball, by d, from an ncu capture at m = 1e6 (traffic grows with
 # the balls streamed; scaled to a launch by m).  Valid only for the screen
 # kernel as captured: empty while the kernel has changed since.
-SCREEN_TRAFFIC_PER_BALL: dict = {}
+SCREEN_TRAFFIC_PER_BALL: dict = {100: 223.7}
 
 
 def _peaks():
@@ -194,6 +194,16 @@ def run_reference(args, C, R, m, rank):
     print(json.dumps(line), flush=True)
 
 
+# the contexts' tick loop (--tick-loop): "graph" (default), or "host" for
+# profiling the matrix-free path kernel by kernel (a profiler does not see the
+# kernels of a graph with conditional nodes)
+TICK_LOOP = "graph"
+
+
+def new_ctx(meb, local, stream):
+    return meb.Context(local, stream.cuda_stream, tick_loop=TICK_LOOP)
+
+
 def timed_solves(meb, torch, ctx, dC, dR, steps, warmup, stream):
     """Warm-up, then `steps` solves each bracketed by CUDA events on the solve
     stream; returns (per-solve ms, the last result, radii)."""
@@ -222,7 +232,7 @@ def extra_workloads(meb, torch, local, stream, workloads, sphere_only=False):
     C, R = workloads.workload("gaussian_m1e4_d10")
     gold = _golden("gaussian_m1e4_d10")
     r_ref = gold["r"] if gold and gold.get("input_sha256") == workloads.digest(C, R) else None
-    ctx = meb.Context(local, stream.cuda_stream)
+    ctx = new_ctx(meb, local, stream)
     dC, dR = torch.from_numpy(C).cuda(), torch.from_numpy(R).cuda()
     lat, res, radii = timed_solves(meb, torch, ctx, dC, dR, 30, 5, stream)
     rel = [abs(r - r_ref) / r_ref for r in radii] if r_ref else None
@@ -241,7 +251,7 @@ def extra_workloads(meb, torch, local, stream, workloads, sphere_only=False):
 def sphere_workload(meb, torch, local, stream, workloads, out):
     # m = 2e5, d = 2000 (sphere, seed 1003): closed form r* = 1
     C, R, _ctr = workloads.sphere(200_000, 2000, 1003)
-    ctx = meb.Context(local, stream.cuda_stream)
+    ctx = new_ctx(meb, local, stream)
     dC, dR = torch.from_numpy(C).cuda(), torch.from_numpy(R).cuda()
     del C
     ctx.reset_stats()
@@ -256,7 +266,7 @@ def sphere_workload(meb, torch, local, stream, workloads, out):
     torch.cuda.synchronize()
     ph = ctx.stats()["phase_ms"]
     ctx.set_profiling(False)
-    ctx.set_option("tick_loop", "graph")
+    ctx.set_option("tick_loop", TICK_LOOP)
     rel = [abs(r - 1.0) for r in radii]
     ok = sum(e <= 1e-8 for e in rel)
     out["sphere_m2e5_d2000"] = {
@@ -285,7 +295,7 @@ def ragged_batch(meb, torch, local, stream, workloads, n_inst):
     balls = sum(C.shape[0] for C, _ in inst)
     in_bytes = sum(C.nbytes + R.nbytes for C, R in inst)
     del inst
-    ctx = meb.Context(local, stream.cuda_stream)
+    ctx = new_ctx(meb, local, stream)
     table = meb.tune_batch(dinst, per_class=8, ctx=ctx)
     res = meb.solve_batch(dinst, ctx=ctx, allow_notconv=True)  # warm-up
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -343,7 +353,7 @@ def paper_sweep(meb, torch, local, stream):
         return None
     mp = meb.params_default()
     mp.mixed = 1
-    ctx = meb.Context(local, stream.cuda_stream)
+    ctx = new_ctx(meb, local, stream)
     rows = []
     for g in gold["instances"]:
         m, d = g["m"], g["d"]
@@ -362,7 +372,7 @@ def paper_sweep(meb, torch, local, stream):
                     ts.append(time.perf_counter() - t0)
             except meb.MebError as e:   # reported, not hidden
                 row[tag + "_error"] = str(e)
-                ctx = meb.Context(local, stream.cuda_stream)
+                ctx = new_ctx(meb, local, stream)
                 continue
             row[tag + "_ms"] = 1e3 * statistics.median(ts)
             row[tag + "_relerr"] = abs(res["r"] - g["r"]) / g["r"]
@@ -456,7 +466,11 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--only", choices=["ragged", "sphere", "serving"], default=None,
                     help="run one extra line alone and print it (for profiling)")
+    ap.add_argument("--tick-loop", choices=["graph", "host", "while"], default="graph",
+                    help="the contexts' tick loop (host: kernel-by-kernel profiling)")
     args = ap.parse_args()
+    global TICK_LOOP
+    TICK_LOOP = args.tick_loop
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -490,7 +504,7 @@ def main():
                                   sphere_only=True)["sphere_m2e5_d2000"]
         print(json.dumps({"only": args.only, **out}), flush=True)
         return
-    ctx = meb.Context(local, stream.cuda_stream)
+    ctx = new_ctx(meb, local, stream)
     dC = torch.from_numpy(C).cuda()
     dR = torch.from_numpy(R).cuda()
     torch.cuda.synchronize()
@@ -551,7 +565,7 @@ def main():
     # end to end: host (pinned) inputs through the public API, result back to host
     pC = torch.from_numpy(C).pin_memory()
     pR = torch.from_numpy(R).pin_memory()
-    hctx = meb.Context(local, stream.cuda_stream)
+    hctx = new_ctx(meb, local, stream)
     res_h = meb.solve(pC, pR, ctx=hctx)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -585,7 +599,7 @@ def main():
         # the mixed-precision reduction pipeline (Sec. 4.2) on the same inputs
         mp = meb.params_default()
         mp.mixed = 1
-        mctx = meb.Context(local, stream.cuda_stream)
+        mctx = new_ctx(meb, local, stream)
         for _ in range(2):
             meb.solve(dC, dR, params=mp, ctx=mctx)
         mev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
