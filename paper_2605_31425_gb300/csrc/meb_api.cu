@@ -196,6 +196,7 @@ static size_t solve_layout(Buffers* Bp, char* base, int64_t m, int d) {
     take(&B.sup_idx[k], m);
     take(&B.sup_u[k], m);
     take(&B.sup_v[k], md);
+    take(&B.sup_vv[k], m);
   }
   // segments of 256 per tile and block: at most (tiles + blocks) * 256 for any grid
   const int64_t ncand = (nblk + kMaxPassBlocks) * 256;
@@ -221,7 +222,7 @@ static size_t solve_layout(Buffers* Bp, char* base, int64_t m, int d) {
   take(&B.S_t, m);
   take(&B.W, md);
   if (d + 1 > kMaxDenseN) take(&B.W32, md);   // the matrix-free path for sure: FP32 rows
-  take(&B.svec_part, (size_t)kSvecBlocks * (3 * d + 1));
+  take(&B.svec_part, (size_t)(d >= 512 ? kSvecBlocksWide : kSvecBlocks) * (3 * d + 1));
   take(&B.hpart, hp);
   take(&B.H, dn);
   take(&B.hq, n1);
@@ -239,6 +240,7 @@ static size_t solve_layout(Buffers* Bp, char* base, int64_t m, int d) {
   take(&B.count64, 8);
   take(&B.scal, 8);
   take(&B.wq, m);
+  take(&B.cf32, m);
   take(&B.st, 1);
   // vectors of length n1 (x, xt, xk, ab, g, gt, dx, ct, o, sv, sw, st1, cg_*) and y32;
   // each starts on a 16-byte boundary (y32 is read as float4)
@@ -792,7 +794,8 @@ static int run_ticks(meb_ctx* ctx, Buffers& B, const double* C, const double* R,
       // dense: a fixed count per tick; matrix-free: pass, controller, CG
       // setup and finish, multipliers, plus 4 per run of the CG loop body
       B.launches = before + (dense ? ticks * tick_launches(d)
-                                   : ticks * 6 + 4 * ctx->h_st->cg_bodies);
+                                   : ticks * (support_rows_wide(B, d) ? 7 : 6) +
+                                         4 * ctx->h_st->cg_bodies);
     }
   } else {
     int64_t ticks = 0;

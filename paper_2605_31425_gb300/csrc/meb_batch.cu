@@ -171,6 +171,7 @@ __device__ void batch_solve_one(const BatchArgs& G, int j, const Buffers& B,
     A.sup_idx0 = B.sup_idx[0]; A.sup_idx1 = B.sup_idx[1];
     A.sup_u0 = B.sup_u[0]; A.sup_u1 = B.sup_u[1];
     A.sup_v0 = B.sup_v[0]; A.sup_v1 = B.sup_v[1];
+    A.sup_vv0 = B.sup_vv[0]; A.sup_vv1 = B.sup_vv[1];
     A.st = B.st; A.ct = B.vec.ct; A.y32 = B.vec.y32;
     A.unc_cnt = B.unc_cnt; A.unc_idx = B.unc_idx; A.unc_slot = B.unc_slot;
     A.vlb_part = B.vlb_part;
@@ -360,6 +361,7 @@ size_t batch_slot_layout(Buffers* Bp, char* base, int64_t m_cap, int d_cap, int6
     take(&B.sup_idx[k], sup_cap);
     take(&B.sup_u[k], sup_cap);
     take(&B.sup_v[k], (size_t)sup_cap * d_cap);
+    take(&B.sup_vv[k], sup_cap);
   }
   take(&B.part_flag, kMaxPassBlocks);
   take(&B.part, (size_t)kMaxPassBlocks * P_NREC);
@@ -398,6 +400,7 @@ size_t batch_slot_layout(Buffers* Bp, char* base, int64_t m_cap, int d_cap, int6
   take(&B.count64, 8);
   take(&B.scal, 8);
   take(&B.wq, sup_cap);
+  take(&B.cf32, sup_cap);
   take(&B.st, 1);
   const size_t stride = (size_t)((n1 + 8 + 1) / 2) * 2;
   take(&B.vec_store, 20 * stride + (size_t)(d4 * 4 + 8));

@@ -323,24 +323,30 @@ __device__ __forceinline__ void control_a_body(const Buffers& B, int d, int nb) 
   state_out(B.st, st);
 }
 
-// Controller, part B (the last block of k_svec, after the support rows were
-// reduced): the gradient at the accepted point, then the relative-type stopping condition
-// (Algorithm 1) and the next action.
-__device__ __forceinline__ void control_b_body_impl(const Buffers& B, DevState* st, int d) {
+// Entry e of the 3d + 1 sums over the support blocks' partials (in block
+// order): sum v^+ (d), sum w (d), sum t w^2 (d), sum (1 + t).
+__device__ __forceinline__ void svec_sum_entry(const Buffers& B, int d, int e, int snb) {
+  const DevVecs& V = B.vec;
+  const int nsum = 3 * d + 1;
+  double a = 0.0;
+  for (int k = 0; k < snb; k++) a += B.svec_part[(int64_t)k * nsum + e];
+  if (e < d) V.sv[e] = a;
+  else if (e < 2 * d) V.sw[e - d] = a;
+  else if (e < 3 * d) V.cg_diag[1 + e - 2 * d] = a;   // sum_M t w_j^2 (Jacobi preconditioner)
+  else V.st1[0] = a;
+}
+
+// Controller, part B (the last block of k_svec, or of k_svec_reduce when that
+// kernel summed the partials: `reduced`): the gradient at the accepted point,
+// then the relative-type stopping condition (Algorithm 1) and the next action.
+__device__ __forceinline__ void control_b_body_impl(const Buffers& B, DevState* st, int d,
+                                                    bool reduced = false) {
   const DevVecs& V = B.vec;
   const int n1 = d + 1;
   __shared__ double sh[32];
-  const int snb = st->svec_nb;
-  // the 3d + 1 sums over the support blocks' partials, one per thread (each
-  // in block order): sum v^+ (d), sum w (d), sum t w^2 (d), sum (1 + t)
-  const int nsum = 3 * d + 1;
-  for (int e = threadIdx.x; e < nsum; e += 256) {
-    double a = 0.0;
-    for (int k = 0; k < snb; k++) a += B.svec_part[(int64_t)k * nsum + e];
-    if (e < d) V.sv[e] = a;
-    else if (e < 2 * d) V.sw[e - d] = a;
-    else if (e < 3 * d) V.cg_diag[1 + e - 2 * d] = a;   // sum_M t w_j^2 (Jacobi preconditioner)
-    else V.st1[0] = a;
+  if (!reduced) {
+    const int snb = st->svec_nb;
+    for (int e = threadIdx.x; e < 3 * d + 1; e += 256) svec_sum_entry(B, d, e, snb);
   }
   __syncthreads();
   const double sigma = st->sigma, tau = st->tau, tos = st->tos;
@@ -392,10 +398,10 @@ __device__ __forceinline__ void control_b_body_impl(const Buffers& B, DevState* 
   }
 }
 
-__device__ __forceinline__ void control_b_body(const Buffers& B, int d) {
+__device__ __forceinline__ void control_b_body(const Buffers& B, int d, bool reduced = false) {
   __shared__ DevState s_st;
   DevState* st = state_in(B.st, &s_st);
-  control_b_body_impl(B, st, d);
+  control_b_body_impl(B, st, d, reduced);
   state_out(B.st, st);
 }
 

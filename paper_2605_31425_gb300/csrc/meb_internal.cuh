@@ -19,6 +19,7 @@ constexpr int kMaxDenseN = 225;     // dense Newton solve for d+1 <= 225 (packed
 constexpr int kAinvMaxN = 112;      // n = d + 1 of the register Gauss-Jordan solve
 constexpr int kAinvLen = 28 * 256;  // float2 entries of its kept FP32 inverse
 constexpr int kSvecBlocks = 152;    // blocks of the support-row reduction (one per SM)
+constexpr int kSvecBlocksWide = 456;   // the same for rows of d >= 512 (three per SM)
 constexpr int kSyrkTile = 32;
 constexpr int kSyrkRows = 32;       // support rows per SYRK block
 
@@ -102,7 +103,7 @@ struct DevState {
   int64_t ticks, max_ticks;    // controller ticks of the device-resident loop and their cap
   int64_t cg_bodies;           // runs of the CG loop body in the tick graph (launch count)
   int screen_log[8];           // profiling: tick t of a graph batch ran a full screen
-  unsigned int ctr_screen, ctr_rows, ctr_svec, ctr_slots;   // last-block-done tickets
+  unsigned int ctr_screen, ctr_rows, ctr_svec, ctr_slots, ctr_svecr;   // last-block-done tickets
   int screens;                 // full FP32 screens run
   double dx2_t;                // ||xt - xk||^2 of the trial (set with the trial)
   double kkt[5], kkt_max;
@@ -162,6 +163,7 @@ struct Buffers {
   int* sup_idx[2];      // [m]
   double* sup_u[2];     // [m]
   double* sup_v[2];     // [m*d]
+  double* sup_vv[2];    // [m] ||v_k||^2, lane-strided FMAs then a warp tree (as the rows sum it)
   // pass outputs
   int* part_flag;       // [nblk]
   int* part_cnt;        // [nblk][P_NCNT]
@@ -179,7 +181,7 @@ struct Buffers {
   int* S_idx; unsigned char* S_case; double* S_a; double* S_n; double* S_u; double* S_t;
   double* W;            // [m*d] w rows (case M) / b rows (case I)
   float* W32;           // [m*d] the same in FP32 for the CG products (matrix-free path), or null
-  double* svec_part;    // [kSvecBlocks][2d+1]
+  double* svec_part;    // [kSvecBlocks or kSvecBlocksWide][3d+1]
   double* hpart;        // SYRK partials
   int64_t hpart_cap;
   double* H;            // [n1*n1] assembled Hessian (eval entry / CG diag)
@@ -197,6 +199,7 @@ struct Buffers {
   int64_t* list_tmp;    // [m_pad] per-tile lists before compaction
   int64_t* count64;     // [4] device counters
   double* wq;           // [m] w_k . q of the Hessian-vector product
+  float* cf32;          // [m] FP32 products: -t_k (w_k . q) / 2 for case M, else 0
   double* scal;         // [8] scalars of the batched solver (r0, r_out, r_alm)
   DevState* st;
   DevVecs vec;
@@ -372,5 +375,6 @@ cudaError_t launch_warm_start(Buffers& B, int d, const double* wx, double sigma,
 cudaError_t launch_map_idx(int64_t* idx, int64_t n, const int64_t* map, cudaStream_t s);
 cudaError_t launch_loop_cond(Buffers& B, cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_cg_cond(Buffers& B, cudaGraphConditionalHandle h, cudaStream_t s);
+bool support_rows_wide(const Buffers& B, int d);   // support rows over kSvecBlocksWide blocks
 
 }  // namespace meb

@@ -316,6 +316,7 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
   A.sup_idx0 = B.sup_idx[0]; A.sup_idx1 = B.sup_idx[1];
   A.sup_u0 = B.sup_u[0]; A.sup_u1 = B.sup_u[1];
   A.sup_v0 = B.sup_v[0]; A.sup_v1 = B.sup_v[1];
+  A.sup_vv0 = B.sup_vv[0]; A.sup_vv1 = B.sup_vv[1];
   A.st = B.st; A.ct = B.vec.ct; A.y32 = B.vec.y32;
   A.unc_cnt = B.unc_cnt; A.unc_idx = B.unc_idx; A.unc_slot = B.unc_slot;
   A.vlb_part = B.vlb_part;
@@ -368,25 +369,49 @@ cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m,
   return cudaGetLastError();
 }
 
+// ctl: controller B in the last block (else k_svec_reduce follows)
 template <bool LOWP>
 __global__ void __launch_bounds__(256) k_svec(const double* __restrict__ C, Buffers B, int d,
-                                              int npb, int64_t seg) {
+                                              int npb, int64_t seg, int nsvb, int ctl) {
   pdl_wait_and_release();
   DevState* st = B.st;
   if (st->status != 0 || st->action != ACT_GRAD) return;
-  svec_block<LOWP>(C, B, d, npb, seg, blockIdx.x, kSvecBlocks);
-  if (last_block_ticket(&st->ctr_svec)) control_b_body(B, d);
+  svec_block<LOWP>(C, B, d, npb, seg, blockIdx.x, nsvb);
+  if (ctl && last_block_ticket(&st->ctr_svec)) control_b_body(B, d);
 }
+
+// Rows of d >= 512: the 3d + 1 sums over the support blocks' partials, one
+// entry per thread over the grid (the same order as in controller B), then
+// controller B in the last block.
+__global__ void __launch_bounds__(256) k_svec_reduce(Buffers B, int d) {
+  pdl_wait_and_release();
+  DevState* st = B.st;
+  if (st->status != 0 || st->action != ACT_GRAD) return;
+  const int e = blockIdx.x * 256 + threadIdx.x;
+  if (e < 3 * d + 1) svec_sum_entry(B, d, e, st->svec_nb);
+  if (last_block_ticket(&st->ctr_svecr)) control_b_body(B, d, true);
+}
+
+bool support_rows_wide(const Buffers& B, int d) { return !B.lowp && d >= 512; }
 
 cudaError_t launch_support_rows(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s) {
   int tpb;
   const int nb = pass_blocks(m, d, screen_variant(B, d), &tpb);
-  cudaError_t e = B.lowp ? launch_pdl(k_svec<true>, dim3(kSvecBlocks), dim3(256), 0, s, C, B, d,
-                                      nb, (int64_t)tpb * kPassThreads)
-                        : launch_pdl(k_svec<false>, dim3(kSvecBlocks), dim3(256), 0, s, C, B, d,
-                                      nb, (int64_t)tpb * kPassThreads);
+  // wide rows: three blocks per SM for the FP64 work, the partial sums spread
+  // over a grid of their own
+  const bool wide = support_rows_wide(B, d);
+  const int nsvb = wide ? kSvecBlocksWide : kSvecBlocks;
+  cudaError_t e = B.lowp ? launch_pdl(k_svec<true>, dim3(nsvb), dim3(256), 0, s, C, B, d,
+                                      nb, (int64_t)tpb * kPassThreads, nsvb, 1)
+                        : launch_pdl(k_svec<false>, dim3(nsvb), dim3(256), 0, s, C, B, d,
+                                      nb, (int64_t)tpb * kPassThreads, nsvb, wide ? 0 : 1);
   if (e != cudaSuccess) return e;
   B.launches += 1;
+  if (wide) {
+    e = launch_pdl(k_svec_reduce, dim3((3 * d + 1 + 255) / 256), dim3(256), 0, s, B, d);
+    if (e != cudaSuccess) return e;
+    B.launches += 1;
+  }
   return cudaGetLastError();
 }
 
@@ -512,8 +537,15 @@ __global__ void k_dense_support(const double* __restrict__ U, const double* __re
   for (int64_t k = ((int64_t)blockIdx.x * 256 + threadIdx.x) >> 5; k < ns;
        k += ((int64_t)gridDim.x * 256) >> 5) {
     const int64_t i = list[k];
-    for (int j = lane; j < d; j += 32) B.sup_v[0][k * d + j] = V[i * (int64_t)d + j];
+    double vv = 0.0;
+    for (int j = lane; j < d; j += 32) {
+      const double v = V[i * (int64_t)d + j];
+      B.sup_v[0][k * d + j] = v;
+      vv = fma(v, v, vv);
+    }
+    vv = warp_sum_t(vv);
     if (lane == 0) {
+      B.sup_vv[0][k] = vv;
       B.sup_idx[0][k] = (int)i;
       B.sup_u[0][k] = U[i];
       B.slot[i] = (int)k;

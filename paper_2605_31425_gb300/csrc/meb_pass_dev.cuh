@@ -207,6 +207,7 @@ struct PassArgs {
   const int* sup_idx0; const int* sup_idx1;
   const double* sup_u0; const double* sup_u1;
   const double* sup_v0; const double* sup_v1;
+  const double* sup_vv0; const double* sup_vv1;
   DevState* st;
   const double* ct;
   const float* y32;
@@ -440,6 +441,7 @@ __device__ __forceinline__ void rows_block(const PassArgs& A, int bid) {
   const int* sidx = cur ? A.sup_idx1 : A.sup_idx0;
   const double* su = cur ? A.sup_u1 : A.sup_u0;
   const double* sv = cur ? A.sup_v1 : A.sup_v0;
+  const double* svv = cur ? A.sup_vv1 : A.sup_vv0;
   const T inv_s = (T)st->inv_s, sigma = (T)st->sigma, inv_sigma = (T)st->inv_sigma;
   const T rt = LOWP ? (T)st->rq32 : (T)st->rt_abs;
   const float* R32 = A.R32;
@@ -495,6 +497,8 @@ __device__ __forceinline__ void rows_block(const PassArgs& A, int bid) {
         // are exact power-of-two scalings of e and b' = e + v (s / sigma), and so are
         // the sums: one multiplication per coordinate fewer, the same results
         const double s_is = (double)inv_sigma * st->s;
+        // ||v||^2 of a support row was summed, in the same order, when the
+        // multiplier was written
         double nn2 = 0.0, pp2 = 0.0, dv2 = 0.0, vv2 = 0.0;
         if (sl >= 0) {
           const double* vrow = sv + (int64_t)sl * d;
@@ -505,9 +509,9 @@ __device__ __forceinline__ void rows_block(const PassArgs& A, int bid) {
             nn2 = fma(b2, b2, nn2);
             pp2 = fma(e, e, pp2);
             dv2 = fma(e, v, dv2);
-            vv2 = fma(v, v, vv2);
           }
-          nn2 = warp_sum_t(nn2); pp2 = warp_sum_t(pp2); dv2 = warp_sum_t(dv2); vv2 = warp_sum_t(vv2);
+          nn2 = warp_sum_t(nn2); pp2 = warp_sum_t(pp2); dv2 = warp_sum_t(dv2);
+          vv2 = svv[sl];
         } else {
           for (int j = lane; j < d; j += 32) {
             const double e = crow[j] - s_ct[j];

@@ -139,9 +139,9 @@ cudaError_t launch_cg_iter(Buffers& B, int d, cudaStream_t s) {
   cudaError_t e = raise_smem_limit((const void*)k_hvp_dot, qsm);
   if (e != cudaSuccess) return e;
   k_hvp_dot<<<kHvpBlocks * 4, 256, qsm, s>>>(B, d, B.vec.cg_p, B.wq, 0);
-  if (B.W32) {   // FP32 products: row groups x column chunks, two blocks per SM
+  if (B.W32) {   // FP32 products: row groups x column chunks, four blocks per SM
     const int chunks = (d + 255) / 256;
-    const int groups = std::max(1, std::min(kHvpGroups32, (2 * 152 + chunks - 1) / chunks));
+    const int groups = std::max(1, std::min(kHvpGroups32, (4 * 152 + chunks - 1) / chunks));
     k_hvp_acc<<<dim3(groups, chunks), 256, 0, s>>>(B, d, B.vec.cg_p, B.wq, B.hpart, 0);
     k_cg_update<<<1, 256, 0, s>>>(B, d, groups);
   } else {
@@ -361,6 +361,17 @@ __global__ void k_warm_start(Buffers B, int d, const double* __restrict__ wx, do
     B.slot[lo] = (int)k;
   }
   for (int64_t e = threadIdx.x; e < nw * d; e += blockDim.x) B.sup_v[0][e] = wv[e];
+  // ||v_k||^2 as the rows sum it (lane-strided FMAs, warp tree)
+  const int lane = threadIdx.x & 31;
+  for (int64_t k = threadIdx.x >> 5; k < nw; k += blockDim.x >> 5) {
+    double vv = 0.0;
+    for (int j = lane; j < d; j += 32) {
+      const double v = wv[k * d + j];
+      vv = fma(v, v, vv);
+    }
+    vv = warp_sum_t(vv);
+    if (lane == 0) B.sup_vv[0][k] = vv;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     st->sigma = sigma;

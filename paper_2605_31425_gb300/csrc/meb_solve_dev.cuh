@@ -672,6 +672,7 @@ __device__ __forceinline__ void hvp_dot_block(const Buffers& B, int d, const dou
   }
   for (int k = (bid * 256 + threadIdx.x) >> 5; k < nS; k += (nb * 256) >> 5) {
     double t = 0.0;
+    float cf = 0.0f;
     if (B.S_case[k] == CASE_M) {
       if (F32) {
         const float* w = B.W32 + (int64_t)k * d;
@@ -680,19 +681,33 @@ __device__ __forceinline__ void hvp_dot_block(const Buffers& B, int d, const dou
           for (int j = lane; j < d; j += 32) tf = fmaf(w[j], s_q32[j], tf);
         else
           for (int j = lane; j < d; j += 32) tf = fmaf(w[j], (float)q[1 + j], tf);
-        t = (double)warp_sum_t(tf);
+        tf = warp_sum_t(tf);
+        t = (double)tf;
+        // the row's coefficient in the accumulation, once per row (its
+        // conversions run on the FP64 pipe)
+        cf = -0.5f * (float)B.S_t[k] * tf;
       } else {
         const double* w = B.W + (int64_t)k * d;
         for (int j = lane; j < d; j += 32) t = fma(w[j], q[1 + j], t);
         t = warp_sum(t);
       }
     }
-    if (lane == 0) wq[k] = t;
+    if (lane == 0) {
+      wq[k] = t;
+      if (F32) B.cf32[k] = cf;
+    }
   }
 }
 
 __device__ __forceinline__ bool cg_gate(const DevState* st) {
   return st->status == 0 && st->action == ACT_NEWTON && !st->cg_done;
+}
+
+// Row groups of the multi-block FP32 products used for nS rows out of nb
+// launched: at least 256 rows per group.
+__device__ __forceinline__ int hvp_groups_used(int nS, int nb) {
+  const int g = (nS + 255) / 256;
+  return g < 1 ? 1 : (g < nb ? g : nb);
 }
 
 // Row group bid of nb; F32: column chunk `chunk` of 256 only (chunks < 0:
@@ -704,6 +719,12 @@ __device__ __forceinline__ void hvp_acc_block(const Buffers& B, int d, const dou
                                               int chunk = -1) {
   const DevState* st = B.st;
   const int nS = st->nS;
+  // FP32 products over a grid of row groups: groups of at least 256 rows
+  // (the update sums one partial per group used)
+  if (F32 && chunk >= 0) {
+    nb = hvp_groups_used(nS, nb);
+    if (bid >= nb) return;
+  }
   const int rpb = (nS + nb - 1) / nb;
   const int k0 = bid * rpb, k1 = min(nS, k0 + rpb);
   double* out = part + (int64_t)bid * (d + 1);
@@ -713,25 +734,29 @@ __device__ __forceinline__ void hvp_acc_block(const Buffers& B, int d, const dou
   for (int j0 = jb; j0 < je; j0 += 256) {
     const int j = j0 + threadIdx.x;
     if (F32) {
-      // four independent accumulators (more loads in flight), summed in order
-      float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      // eight independent accumulators (eight rows' loads in flight), summed
+      // in a fixed tree; the row coefficients come from the dot kernel
+      const float* cf32 = B.cf32;
+      float a[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
       int k = k0;
-      for (; k + 3 < k1; k += 4) {
+      if (j < d) {
+        for (; k + 7 < k1; k += 8) {
+          float wv[8];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-          const int kk = k + u;
-          const float coef = (B.S_case[kk] == CASE_M) ? -0.5f * (float)B.S_t[kk] * (float)wq[kk] : 0.0f;
-          if (j < d) a[u] = fmaf(coef, B.W32[(int64_t)kk * d + j], a[u]);
+          for (int u = 0; u < 8; u++) wv[u] = B.W32[(int64_t)(k + u) * d + j];
+#pragma unroll
+          for (int u = 0; u < 8; u++) a[u] = fmaf(cf32[k + u], wv[u], a[u]);
         }
+        for (; k < k1; k++) a[0] = fmaf(cf32[k], B.W32[(int64_t)k * d + j], a[0]);
+        out[1 + j] = (double)(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
       }
-      for (; k < k1; k++) {
-        const float coef = (B.S_case[k] == CASE_M) ? -0.5f * (float)B.S_t[k] * (float)wq[k] : 0.0f;
-        if (j < d) a[0] = fmaf(coef, B.W32[(int64_t)k * d + j], a[0]);
+      if (j0 == 0) {   // 1/2 sum_M wq over the group's rows, all threads, then in a tree
+        __shared__ double sh_s0[32];
+        double p0 = 0.0;
+        for (int kk = k0 + (int)threadIdx.x; kk < k1; kk += 256)
+          if (B.S_case[kk] == CASE_M) p0 += 0.5 * wq[kk];
+        s0 = block_sum<256>(p0, sh_s0);
       }
-      if (j < d) out[1 + j] = (double)((a[0] + a[1]) + (a[2] + a[3]));
-      if (j0 == 0 && threadIdx.x == 0)
-        for (int kk = k0; kk < k1; kk++)
-          if (B.S_case[kk] == CASE_M) s0 += 0.5 * wq[kk];
     } else {
       double acc = 0.0;
       for (int k = k0; k < k1; k++) {
@@ -810,7 +835,9 @@ __device__ __forceinline__ void cg_update_body(const Buffers& B, int d, int nblk
   __shared__ double sh[32];
   const DevVecs& V = B.vec;
   const int n1 = d + 1;
-  hvp_finish(st, V, d, V.cg_p, B.hpart, nblk, V.cg_ap);
+  // FP32 products of the multi-block CG: the row groups used
+  hvp_finish(st, V, d, V.cg_p, B.hpart, (B.W32 && nblk > 1) ? hvp_groups_used(st->nS, nblk) : nblk,
+             V.cg_ap);
   __syncthreads();
   double pap = 0.0;
   for (int k = threadIdx.x; k < n1; k += 256) pap += V.cg_p[k] * V.cg_ap[k];
@@ -885,11 +912,15 @@ __device__ __forceinline__ void mult_rows_block(const double* __restrict__ C, co
     const int sl = ((unsigned)sl0 < (unsigned)nsup && sidx[sl0] == idx) ? sl0 : -1;
     const double a = B.S_a[k], n = B.S_n[k];
     const double f = (B.S_case[k] == CASE_I) ? 1.0 : 0.5 * (a + n) / n;
+    // with ||v^+||^2 summed as the rows will sum it (lane-strided FMAs, warp tree)
+    double vv = 0.0;
     if (LOWP) {
       for (int j = lane; j < d; j += 32) {
         double b = (double)((x32_at(B.X32, st->m_pad, idx, j) - B.vec.y32[j]) * (float)inv_s);
         if (sl >= 0) b = fma(sv[(int64_t)sl * d + j], inv_sigma, b);
-        nv[(int64_t)k * d + j] = sigma * f * b;
+        const double v = sigma * f * b;
+        nv[(int64_t)k * d + j] = v;
+        vv = fma(v, v, vv);
       }
     } else {
       // in units of s: b' = (c_i - c) + v (s / sigma) = s b exactly, and
@@ -898,11 +929,15 @@ __device__ __forceinline__ void mult_rows_block(const double* __restrict__ C, co
       for (int j = lane; j < d; j += 32) {
         double b2 = C[(int64_t)idx * d + j] - ct[j];
         if (sl >= 0) b2 = fma(sv[(int64_t)sl * d + j], s_is, b2);
-        nv[(int64_t)k * d + j] = b2 * sfs;
+        const double v = b2 * sfs;
+        nv[(int64_t)k * d + j] = v;
+        vv = fma(v, v, vv);
       }
     }
+    vv = warp_sum_t(vv);
     __syncwarp();   // every lane has read the old slot of ball idx
     if (lane == 0) {
+      B.sup_vv[nxt][k] = vv;
       B.sup_idx[nxt][k] = idx;
       B.sup_u[nxt][k] = B.S_u[k];
       // the new slot: each ball is in S once, so no other warp reads or

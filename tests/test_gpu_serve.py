@@ -56,6 +56,19 @@ def test_results_same_alone_and_in_the_mix():
         assert np.linalg.norm(mix[k]["c"] - o["c"]) <= 1e-7 * o["r"]
 
 
+def test_server_flags_same_results():
+    """Spinning waits and the device's default pool change how the workers
+    wait and allocate, not what they compute."""
+    inst = pool(12, 321)
+    ref = meb.solve_batch(inst)
+    for kw in (dict(spin_waits=True), dict(device_pool=True), dict(spin_waits=True, device_pool=True)):
+        sv = meb.Server(budget_bytes=4 << 30, small_workers=4, max_group=2, **kw)
+        res = [sv.wait(t) for t in [sv.submit(C, R) for C, R in inst]]
+        sv.close()
+        for g, a in zip(res, ref):
+            assert g["rc"] == 0 and g["r"] == a["r"] and np.array_equal(g["c"], a["c"]), kw
+
+
 def test_budget_admission():
     inst = pool(30, 7)
     fps = [meb.footprint(C.shape[0], C.shape[1], True) + 8 * C.size + 8 * len(R) for C, R in inst]
