@@ -570,7 +570,7 @@ static int read_state(meb_ctx* ctx, const Buffers& B) {
 // (its handle defaults to 1 at every launch, so the body runs at least once)
 // whose body, captured on the context's second stream, is one CG iteration
 // and k_cg_cond; then continue the capture after the node.
-static cudaError_t cg_loop_node(meb_ctx* ctx, Buffers& B, int d, cudaStream_t s) {
+static cudaError_t cg_loop_node(meb_ctx* ctx, Buffers& B, int64_t m, int d, cudaStream_t s) {
   cudaStreamCaptureStatus cs;
   cudaGraph_t graph = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -596,7 +596,7 @@ static cudaError_t cg_loop_node(meb_ctx* ctx, Buffers& B, int d, cudaStream_t s)
   cudaStream_t s2 = ctx->stream2;
   e = cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return e;
-  e = launch_cg_iter(B, d, s2);
+  e = launch_cg_iter(B, m, d, s2);
   if (e == cudaSuccess) e = launch_cg_cond(B, h, s2);
   cudaGraph_t got = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(s2, &got);
@@ -674,7 +674,7 @@ static int solve_graph(meb_ctx* ctx, Buffers& B, const double* C, const double* 
         // whose body is one CG iteration and the loop condition, then the
         // finish (each kernel gated on the controller's action)
         if (e == cudaSuccess) e = launch_cg_setup(B, d, s);
-        if (e == cudaSuccess) e = cg_loop_node(ctx, B, d, s);
+        if (e == cudaSuccess) e = cg_loop_node(ctx, B, m, d, s);
         if (e == cudaSuccess) e = launch_cg_finish(B, d, s);
       }
       if (e == cudaSuccess) e = launch_mult_update(C, B, m, d, s);
@@ -837,7 +837,7 @@ static int run_ticks(meb_ctx* ctx, Buffers& B, const double* C, const double* R,
         } else {
           CK(launch_cg_setup(B, d, s));
           for (int round = 0; round <= P.max_cg / 4 + 1; round++) {
-            for (int k = 0; k < 4; k++) CK(launch_cg_iter(B, d, s));
+            for (int k = 0; k < 4; k++) CK(launch_cg_iter(B, m, d, s));
             rc = read_state(ctx, B);
             if (rc) return rc;
             if (ctx->h_st->cg_done || ctx->h_st->status != 0 || ctx->h_st->action != ACT_NEWTON) break;

@@ -355,7 +355,7 @@ cudaError_t launch_newton_dense(Buffers& B, int d, cudaStream_t s);
 int newton_dense_launches(int d);
 cudaError_t prepare_newton(int d);
 cudaError_t launch_cg_setup(Buffers& B, int d, cudaStream_t s);
-cudaError_t launch_cg_iter(Buffers& B, int d, cudaStream_t s);
+cudaError_t launch_cg_iter(Buffers& B, int64_t m, int d, cudaStream_t s);
 cudaError_t launch_cg_finish(Buffers& B, int d, cudaStream_t s);
 cudaError_t launch_mult_update(const double* C, Buffers& B, int64_t m, int d, cudaStream_t s);
 cudaError_t launch_state_init(Buffers& B, int d, cudaStream_t s);

@@ -134,14 +134,19 @@ static cudaError_t prepare_hvp(int d) {
   return raise_smem_limit((const void*)k_hvp_dot, sizeof(float) * (size_t)d);
 }
 
-cudaError_t launch_cg_iter(Buffers& B, int d, cudaStream_t s) {
+cudaError_t launch_cg_iter(Buffers& B, int64_t m, int d, cudaStream_t s) {
   const size_t qsm = B.W32 ? sizeof(float) * (size_t)d : 0;
   cudaError_t e = raise_smem_limit((const void*)k_hvp_dot, qsm);
   if (e != cudaSuccess) return e;
   k_hvp_dot<<<kHvpBlocks * 4, 256, qsm, s>>>(B, d, B.vec.cg_p, B.wq, 0);
   if (B.W32) {   // FP32 products: row groups x column chunks, four blocks per SM
     const int chunks = (d + 255) / 256;
-    const int groups = std::max(1, std::min(kHvpGroups32, (4 * 152 + chunks - 1) / chunks));
+    // four blocks per SM, and groups of at least 256 of the instance's balls
+    // (the support is at most m rows; a fixed count per instance, so the
+    // order of the sums does not depend on the iteration)
+    const int64_t by_m = (m + 255) / 256;
+    const int groups = (int)std::max<int64_t>(
+        1, std::min<int64_t>({(int64_t)kHvpGroups32, (int64_t)(4 * 152 + chunks - 1) / chunks, by_m}));
     k_hvp_acc<<<dim3(groups, chunks), 256, 0, s>>>(B, d, B.vec.cg_p, B.wq, B.hpart, 0);
     k_cg_update<<<1, 256, 0, s>>>(B, d, groups);
   } else {

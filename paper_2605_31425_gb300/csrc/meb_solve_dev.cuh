@@ -703,13 +703,6 @@ __device__ __forceinline__ bool cg_gate(const DevState* st) {
   return st->status == 0 && st->action == ACT_NEWTON && !st->cg_done;
 }
 
-// Row groups of the multi-block FP32 products used for nS rows out of nb
-// launched: at least 256 rows per group.
-__device__ __forceinline__ int hvp_groups_used(int nS, int nb) {
-  const int g = (nS + 255) / 256;
-  return g < 1 ? 1 : (g < nb ? g : nb);
-}
-
 // Row group bid of nb; F32: column chunk `chunk` of 256 only (chunks < 0:
 // every chunk), FP64: every chunk.
 template <bool F32 = false>
@@ -719,12 +712,6 @@ __device__ __forceinline__ void hvp_acc_block(const Buffers& B, int d, const dou
                                               int chunk = -1) {
   const DevState* st = B.st;
   const int nS = st->nS;
-  // FP32 products over a grid of row groups: groups of at least 256 rows
-  // (the update sums one partial per group used)
-  if (F32 && chunk >= 0) {
-    nb = hvp_groups_used(nS, nb);
-    if (bid >= nb) return;
-  }
   const int rpb = (nS + nb - 1) / nb;
   const int k0 = bid * rpb, k1 = min(nS, k0 + rpb);
   double* out = part + (int64_t)bid * (d + 1);
@@ -835,9 +822,7 @@ __device__ __forceinline__ void cg_update_body(const Buffers& B, int d, int nblk
   __shared__ double sh[32];
   const DevVecs& V = B.vec;
   const int n1 = d + 1;
-  // FP32 products of the multi-block CG: the row groups used
-  hvp_finish(st, V, d, V.cg_p, B.hpart, (B.W32 && nblk > 1) ? hvp_groups_used(st->nS, nblk) : nblk,
-             V.cg_ap);
+  hvp_finish(st, V, d, V.cg_p, B.hpart, nblk, V.cg_ap);
   __syncthreads();
   double pap = 0.0;
   for (int k = threadIdx.x; k < n1; k += 256) pap += V.cg_p[k] * V.cg_ap[k];
