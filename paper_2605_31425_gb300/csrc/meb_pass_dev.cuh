@@ -638,7 +638,7 @@ __device__ __forceinline__ bool rows_gate(const DevState* st) {
 }
 
 // ---------------------------------------------------------------------------
-// FP16 screen through a bulk-copy pipeline (MEB_SCREEN=bulk).  One block per
+// FP16 screen through a bulk-copy pipeline (MEB_OPT_SCREEN = MEB_SCREEN_FP16_BULK).  One block per
 // SM keeps `nst` tiles in flight: a tile's shadow rows (16 B per ball and row), error
 // bounds, FP32 radii and slots are copied by the TMA engine into a shared
 // memory stage and signal its mbarrier; the block sums each ball from shared
