@@ -230,7 +230,7 @@ __device__ void batch_solve_one(const BatchArgs& G, int j, const Buffers& B,
         }
         syrk_reduce_block(B, d, 0, 1, 1);
         __syncthreads();
-        newton_gj_reg_body(B, d);
+        newton_gj_small_body(B, d);
         __syncthreads();
       } else {
         cg_setup_body(B, d);

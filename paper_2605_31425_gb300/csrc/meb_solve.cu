@@ -51,6 +51,13 @@ __global__ void __launch_bounds__(256, 1) k_newton_gj_reg(Buffers B, int d) {
   newton_gj_reg_body(B, d);
 }
 
+// n <= 32: the single-warp sweep (with the same Cholesky fallback)
+__global__ void __launch_bounds__(256, 1) k_newton_gj_warp(Buffers B, int d) {
+  pdl_wait_and_release();
+  if (!newton_gate(B.st)) return;
+  newton_gj_small_body(B, d);
+}
+
 // Launches per Newton step of the dense path: SYRK, its reduction and the
 // solve (n <= kGjRegN: Gauss-Jordan with the Cholesky fallback inside), or
 // SYRK, reduction, shared-memory Gauss-Jordan and a separate Cholesky.
@@ -64,6 +71,7 @@ cudaError_t prepare_newton(int d) {
   if (n > kMaxDenseN) return prepare_hvp(d);   // matrix-free path
   const size_t shc = sizeof(double) * (size_t)n * (n + 1) / 2;
   cudaError_t e = cudaSuccess;
+  if (n <= kGjWarpN) return raise_smem_limit((const void*)k_newton_gj_warp, shc);
   if (n <= kGjRegN) return raise_smem_limit((const void*)k_newton_gj_reg, shc);
   const size_t shg = sizeof(float) * (size_t)n * n;
   e = raise_smem_limit((const void*)k_newton_gj, shg);
@@ -80,7 +88,9 @@ cudaError_t launch_newton_dense(Buffers& B, int d, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   const int n = d + 1;
   const size_t shc = sizeof(double) * (size_t)n * (n + 1) / 2;
-  if (n <= kGjRegN) {
+  if (n <= kGjWarpN) {
+    e = launch_pdl(k_newton_gj_warp, dim3(1), dim3(256), shc, s, B, d);
+  } else if (n <= kGjRegN) {
     e = launch_pdl(k_newton_gj_reg, dim3(1), dim3(256), shc, s, B, d);
   } else {
     e = launch_pdl(k_newton_gj, dim3(1), dim3(256), sizeof(float) * (size_t)n * n, s, B, d);

@@ -394,6 +394,94 @@ __device__ __forceinline__ float2 block_sum2f(float a, float b, float2* sh8) {
   return t;
 }
 
+// Small systems, n = d + 1 <= 32: one warp.  Lane i holds row i of the matrix
+// in registers; each pivot's row comes by shuffles, so the sweep needs no block
+// barrier.  The same FP32 Gauss-Jordan sweep and double-float refinement as the
+// 256-thread solve (at most two corrections; the second residual must be at
+// most half the first, else the FP64 Cholesky).  Warp 0 computes; the block
+// then sets up the trial.  No inverse is kept (a fresh one costs little here).
+constexpr int kGjWarpN = 32;
+
+__device__ __forceinline__ void newton_gj_warp_body(const Buffers& B, int d) {
+  DevState* st = B.st;
+  extern __shared__ double dyn_Lp[];   // the Cholesky fallback's factor
+  __shared__ double s_x[kGjWarpN];
+  __shared__ double sh[32];
+  __shared__ int s_ok;
+  const DevVecs& V = B.vec;
+  const int n = d + 1;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < 32) {
+    float a[kGjWarpN];   // a[j] = A[lane][j]; rows and columns past n: identity
+#pragma unroll
+    for (int j = 0; j < kGjWarpN; j++)
+      a[j] = (lane < n && j < n) ? B.Hhi[(int64_t)lane * n + j] : (lane == j ? 1.0f : 0.0f);
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < kGjWarpN; k++) {
+      if (k < n && ok) {   // the same for every lane
+        const float p = __shfl_sync(MEB_FULLMASK, a[k], k);
+        ok = (p > 0.0f) && isfinite(p);
+        const float ip = __fdividef(1.0f, p);
+        const float cik = a[k];   // A[lane][k] before the sweep
+#pragma unroll
+        for (int j = 0; j < kGjWarpN; j++) {
+          const float rkj = __shfl_sync(MEB_FULLMASK, a[j], k);   // A[k][j] before the sweep
+          if (lane == k) a[j] = (j == k) ? ip : rkj * ip;
+          else a[j] = (j == k) ? -cik * ip : fmaf(-cik, rkj * ip, a[j]);
+        }
+      }
+    }
+    // x0 = A (-g) and corrections x += A r, r = -g - H x in double-float
+    const double b = (lane < n) ? -V.g[lane] : 0.0;
+    const float bh = __double2float_rn(b);
+    const float bl = __double2float_rn(b - (double)bh);
+    float sb = bh, xh = 0.0f, xl = 0.0f, rn0 = 0.0f;
+    bool conv = false;
+    for (int it = 0; ok && it < 3; it++) {
+      float t = 0.0f;
+#pragma unroll
+      for (int j = 0; j < kGjWarpN; j++) t = fmaf(a[j], __shfl_sync(MEB_FULLMASK, sb, j), t);
+      if (lane >= n) t = 0.0f;
+      float h, e;
+      two_sum(xh, t, h, e);
+      const float l = xl + e;
+      const float h2 = h + l;
+      xl = l - (h2 - h);
+      xh = h2;
+      const float dn = warp_sum_t(t * t), xn = warp_sum_t(xh * xh);
+      if (dn <= 1e-16f * xn || it == 2) { conv = true; break; }
+      float sa = 0.0f, la = 0.0f;
+      for (int j = 0; j < n; j++) {
+        const float xj = __shfl_sync(MEB_FULLMASK, xh, j), xlj = __shfl_sync(MEB_FULLMASK, xl, j);
+        if (lane < n) df_mac(B.Hhi[(int64_t)lane * n + j], B.Hlo[(int64_t)lane * n + j], xj, xlj, sa, la);
+      }
+      float r = 0.0f;
+      if (lane < n) {
+        float hh, ee;
+        two_sum(bh, -sa, hh, ee);   // exact leading difference
+        r = hh + ((ee + bl) - la);
+      }
+      const float rr = warp_sum_t(r * r);
+      if (it == 0) rn0 = rr;
+      else if (!(rr <= 0.25f * rn0)) { ok = false; break; }
+      sb = r;
+    }
+    if (lane < n) s_x[lane] = (double)xh + (double)xl;
+    if (lane == 0) {
+      s_ok = ok && conv;
+      st->gj_inverses += 1;
+      st->inv_valid = 0;
+    }
+  }
+  __syncthreads();
+  if (!s_ok) {
+    newton_chol_body(B, d, dyn_Lp);   // the FP64 Cholesky in the same launch
+    return;
+  }
+  newton_accept(st, V, d, s_x, sh);
+}
+
 // Kept inverse: while sigma is unchanged, H changes from one Newton step to
 // the next only through the t_k and the support, so the inverse of the last
 // H is tried first.  The refinement below converges with it when it
@@ -647,6 +735,13 @@ __device__ __forceinline__ void newton_gj_reg_body(const Buffers& B, int d) {
   for (int i = tid; i < kGjRegN; i += 256) s_x[i] = (double)s_xh[i] + (double)s_xl[i];
   __syncthreads();
   newton_accept(st, V, d, s_x, sh);
+}
+
+// The dense Newton solve for n = d + 1 <= 112 (one thread block): one warp for
+// n <= 32, the 256-thread register sweep otherwise.
+__device__ __forceinline__ void newton_gj_small_body(const Buffers& B, int d) {
+  if (d + 1 <= kGjWarpN && !B.st->force_fp64_solve) newton_gj_warp_body(B, d);
+  else newton_gj_reg_body(B, d);
 }
 
 // ===========================================================================
