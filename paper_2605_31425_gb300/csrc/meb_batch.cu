@@ -224,12 +224,14 @@ __device__ void batch_solve_one(const BatchArgs& G, int j, const Buffers& B,
     }
     if (newton_gate(st)) {
       if (dense) {
-        for (int t = 0; t < ntri; t++) {
-          syrk_block(B, d, t, 0, 1);
+        if (!syrk_in_solve(st, d)) {   // else the solve assembles H itself
+          for (int t = 0; t < ntri; t++) {
+            syrk_block(B, d, t, 0, 1);
+            __syncthreads();
+          }
+          syrk_reduce_block(B, d, 0, 1, 1);
           __syncthreads();
         }
-        syrk_reduce_block(B, d, 0, 1, 1);
-        __syncthreads();
         newton_gj_small_body(B, d);
         __syncthreads();
       } else {

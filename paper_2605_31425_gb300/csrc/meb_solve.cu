@@ -21,13 +21,13 @@ cudaError_t launch_tick_control(Buffers& B, int64_t m, int d, cudaStream_t s) {
 
 __global__ void __launch_bounds__(256) k_syrk(Buffers B, int d, int force) {
   pdl_wait_and_release();
-  if (!force && !newton_gate(B.st)) return;
+  if (!force && (!newton_gate(B.st) || syrk_in_solve(B.st, d))) return;
   syrk_block(B, d, blockIdx.x, blockIdx.y);
 }
 
 __global__ void k_syrk_reduce(Buffers B, int d, int force) {
   pdl_wait_and_release();
-  if (!force && !newton_gate(B.st)) return;
+  if (!force && (!newton_gate(B.st) || syrk_in_solve(B.st, d))) return;
   syrk_reduce_block(B, d, blockIdx.x, gridDim.x);
 }
 

@@ -737,11 +737,67 @@ __device__ __forceinline__ void newton_gj_reg_body(const Buffers& B, int d) {
   newton_accept(st, V, d, s_x, sh);
 }
 
+// Small dense systems (n <= 32, at most 32 support rows): the block of the
+// solve assembles H itself, so the SYRK launches are skipped.  Each entry sums
+// the support rows in order, as the one-group SYRK does (the batched solver's
+// H is the same either way); one thread per entry, so the support is kept
+// short.
+constexpr int kFusedSyrkRows = 32;
+__device__ __forceinline__ bool syrk_in_solve(const DevState* st, int d) {
+  return d + 1 <= kGjWarpN && !st->force_fp64_solve && st->nS <= kFusedSyrkRows;
+}
+
+// H = tau/sigma I + sigma (n_I I + 1/2 [[n_M, sum w^T], [sum w, sum(1+t) I - SY]])
+// with SY = sum_M t w w^T summed over the support rows in order (block-wide).
+__device__ __forceinline__ void h_assemble_block(const Buffers& B, int d) {
+  const DevState* st = B.st;
+  const DevVecs& V = B.vec;
+  const int n1 = d + 1, nS = st->nS;
+  const double sigma = st->sigma, tos = st->tos;
+  const double nI = st->last[P_NI], nM = st->last[P_NM], s1t = V.st1[0];
+  for (int e = threadIdx.x; e < n1 * n1; e += blockDim.x) {
+    const int i = e / n1, l = e % n1;
+    if (l > i) continue;   // the thread of (i, l) writes (i, l) and (l, i)
+    double h;
+    if (i == 0) {
+      h = tos + sigma * (nI + 0.5 * nM);
+    } else if (l == 0) {
+      h = sigma * 0.5 * V.sw[i - 1];
+    } else {
+      const int j = i - 1, k = l - 1;
+      double sy = 0.0;
+      for (int r = 0; r < nS; r++) {
+        if (B.S_case[r] != CASE_M) continue;
+        const double bv = B.W[(int64_t)r * d + k] * B.S_t[r];
+        sy = fma(B.W[(int64_t)r * d + j], bv, sy);
+      }
+      h = -0.5 * sigma * sy;
+      if (i == l) h += tos + sigma * (nI + 0.5 * s1t);
+    }
+    B.H[(int64_t)i * n1 + l] = h;
+    B.H[(int64_t)l * n1 + i] = h;
+    const float hi = __double2float_rn(h);
+    const float lo = __double2float_rn(h - (double)hi);
+    B.Hhi[(int64_t)i * n1 + l] = hi;
+    B.Hhi[(int64_t)l * n1 + i] = hi;
+    B.Hlo[(int64_t)i * n1 + l] = lo;
+    B.Hlo[(int64_t)l * n1 + i] = lo;
+  }
+}
+
 // The dense Newton solve for n = d + 1 <= 112 (one thread block): one warp for
-// n <= 32, the 256-thread register sweep otherwise.
+// n <= 32 (with H assembled here when the support is small), the 256-thread
+// register sweep otherwise.
 __device__ __forceinline__ void newton_gj_small_body(const Buffers& B, int d) {
-  if (d + 1 <= kGjWarpN && !B.st->force_fp64_solve) newton_gj_warp_body(B, d);
-  else newton_gj_reg_body(B, d);
+  if (d + 1 <= kGjWarpN && !B.st->force_fp64_solve) {
+    if (syrk_in_solve(B.st, d)) {
+      h_assemble_block(B, d);
+      __syncthreads();
+    }
+    newton_gj_warp_body(B, d);
+  } else {
+    newton_gj_reg_body(B, d);
+  }
 }
 
 // ===========================================================================
