@@ -62,7 +62,8 @@ typedef struct {
     int32_t max_ssn;     /* 50  */
     int32_t max_backtrack; /* 40 */
     int32_t dense_max_d; /* dense Cholesky Newton solve when d <= this (<= 224); 224    */
-    int32_t max_cg;      /* CG iterations per Newton system (d > dense_max_d); 500     */
+    int32_t max_cg;      /* CG iterations per Newton system (d > dense_max_d); 500,
+                            at most 20,000 (the device-side CG loop's bound)        */
     int32_t newton_fp64; /* 1: solve every dense Newton system by the FP64 Cholesky   */
                          /* (the reference path; default 0: FP32 Gauss-Jordan with   */
                          /* refinement, FP64 Cholesky only as the fallback)          */

@@ -542,7 +542,7 @@ static int resolve_params(meb_ctx* ctx, const meb_params* params, double tol, me
   if (tol > 0) P.tol = tol;
   if (!(P.tol > 0) || !(P.rho >= 0 && P.rho < 1) || !(P.sigma0 > 0) || !(P.tau > 0) ||
       !(P.sigma_max >= P.sigma0) || !(P.sigma_growth >= 1) || P.max_outer < 1 || P.max_ssn < 1 ||
-      P.max_backtrack < 0 || P.max_cg < 1 || !(P.active_theta >= 0) ||
+      P.max_backtrack < 0 || P.max_cg < 1 || P.max_cg > 20000 || !(P.active_theta >= 0) ||
       (P.mixed && (!(P.tol_lp > 0) || !(P.tol_red >= 0) || P.max_readd < 0)))
     return fail(ctx, MEB_EINVAL, "invalid parameters");
   *out = P;

@@ -199,6 +199,11 @@ def test_invalid_inputs():
         meb.solve(Cn, R)
     with pytest.raises(meb.MebError):
         meb.solve(np.zeros((0, 2)), np.zeros(0))
+    P = meb.params_default()
+    P.max_cg = 20001                     # past the device-side CG loop's bound
+    with pytest.raises(meb.MebError) as e:
+        meb.solve(workloads.cube(100, 3, 1, 0.05)[0], np.zeros(100), params=P)
+    assert e.value.code == -1
 
 
 def test_device_pointer_path():
