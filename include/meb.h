@@ -286,9 +286,12 @@ int meb_tune_batch(meb_ctx *ctx, int32_t n, const meb_batch_item *items, int32_t
  * would take alone: its results do not depend on the mix.
  * Zero fields of cfg take the defaults: 64 small workers, 2 large workers,
  * large_balls 2^27, groups of at most 4 requests.  The workers allocate from
- * a stream-ordered memory pool of the server's own, which keeps freed memory
- * (up to budget_bytes) for the next requests and never makes one worker's
- * allocation wait for another worker's work; they wait for the GPU asleep
+ * a stream-ordered memory pool that the process's servers share (one per
+ * device), which keeps freed memory (up to the largest budget_bytes) for the
+ * next requests and servers and never makes one worker's allocation wait for
+ * another worker's work; each worker runs on a stream the process keeps for
+ * its index (streams are not created and destroyed per server: that churn
+ * halved a later server's throughput); they wait for the GPU asleep
  * (MEB_OPT_BLOCKING_SYNC).  The workers' streams run side by side only on
  * separate hardware queues: set CUDA_DEVICE_MAX_CONNECTIONS (at most 32)
  * before the process first uses CUDA. */
@@ -302,8 +305,8 @@ typedef struct {
 } meb_server_config;
 /* workers spin while they wait for the GPU (default: they sleep) */
 #define MEB_SERVER_SPIN_WAITS 1u
-/* workers allocate from the device's default stream-ordered pool (default: a
-   pool of the server's own) */
+/* workers allocate from the device's default stream-ordered pool (default:
+   the pool the process's servers share) */
 #define MEB_SERVER_DEVICE_POOL 2u
 
 typedef struct {

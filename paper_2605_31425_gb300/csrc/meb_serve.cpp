@@ -65,6 +65,61 @@ struct Request {
 
 constexpr int kBatchMaxD = 4096;   // the batch solver's largest d
 
+// The workers allocate and free stream-ordered from a pool of the servers'
+// own, one per device for the process.  Freed memory stays in it (up to the
+// largest budget of the servers created) instead of going back to the driver
+// at every synchronisation, and a later server reuses what an earlier one
+// mapped: a server created after another had served (and returned its memory)
+// ran at about half the throughput while mapping memory anew.  A block freed
+// on one worker's stream is reused by another only once that free has
+// completed: with the allocator's internal dependencies a worker's launch
+// would wait for another worker's batch, and the workers would run one after
+// another.
+// The k-th worker stream of the process on `device` (created once, kept for
+// later servers): each server's workers reuse the same streams instead of
+// creating and destroying their own.
+cudaStream_t server_stream(int device, int k) {
+  static std::mutex mu;
+  static std::unordered_map<int, std::vector<cudaStream_t>> streams;
+  std::lock_guard<std::mutex> lk(mu);
+  std::vector<cudaStream_t>& v = streams[device];
+  while ((int)v.size() <= k) {
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    v.push_back(s);
+  }
+  return v[k];
+}
+
+cudaMemPool_t server_pool(int device, int64_t budget) {
+  static std::mutex mu;
+  static std::unordered_map<int, cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> lk(mu);
+  cudaMemPool_t& p = pools[device];
+  if (!p) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      p = nullptr;
+      return nullptr;
+    }
+    int no = 0, yes = 1;
+    cudaMemPoolSetAttribute(p, cudaMemPoolReuseAllowInternalDependencies, &no);
+    cudaMemPoolSetAttribute(p, cudaMemPoolReuseAllowOpportunistic, &yes);
+    cudaMemPoolSetAttribute(p, cudaMemPoolReuseFollowEventDependencies, &yes);
+  }
+  uint64_t keep = 0;
+  cudaMemPoolGetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+  if ((uint64_t)budget > keep) {
+    keep = (uint64_t)budget;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  return p;
+}
+
 }  // namespace
 
 struct meb_server {
@@ -81,7 +136,7 @@ struct meb_server {
   int64_t used = 0;
   meb_server_stats st{};
   bool stop = false;
-  cudaMemPool_t pool = nullptr;      // the workers' scratch and staging
+  cudaMemPool_t pool = nullptr;      // the workers' scratch and staging (shared per device)
   std::vector<std::thread> workers;
 };
 
@@ -125,10 +180,11 @@ int rc_of(const meb_info& info) {
   return info.status == -1 ? MEB_EINVAL : info.status == 0 ? MEB_OK : MEB_ENOTCONV;
 }
 
-void small_worker(meb_server* sv) {
+void small_worker(meb_server* sv, int k) {
   cudaSetDevice(sv->device);
   meb_ctx* ctx = nullptr;
-  const int crc = meb_create(&ctx, sv->device, nullptr);
+  cudaStream_t ws = server_stream(sv->device, k);
+  const int crc = ws ? meb_create(&ctx, sv->device, ws) : MEB_ECUDA;
   if (crc == MEB_OK) {
     meb_set_option(ctx, MEB_OPT_BATCH_SLOTS, 1);
     meb_set_option(ctx, MEB_OPT_RELEASE_SCRATCH, 1);
@@ -180,10 +236,11 @@ void small_worker(meb_server* sv) {
   if (ctx) meb_destroy(ctx);
 }
 
-void large_worker(meb_server* sv) {
+void large_worker(meb_server* sv, int k) {
   cudaSetDevice(sv->device);
   meb_ctx* ctx = nullptr;
-  const int crc = meb_create(&ctx, sv->device, nullptr);
+  cudaStream_t ws = server_stream(sv->device, k);
+  const int crc = ws ? meb_create(&ctx, sv->device, ws) : MEB_ECUDA;
   if (crc == MEB_OK) {
     meb_set_option(ctx, MEB_OPT_RELEASE_SCRATCH, 1);
     if (!(sv->cfg.flags & MEB_SERVER_SPIN_WAITS)) meb_set_option(ctx, MEB_OPT_BLOCKING_SYNC, 1);
@@ -235,31 +292,16 @@ extern "C" int meb_server_create(meb_server** out, int device, const meb_server_
     delete sv;
     return MEB_ECUDA;
   }
-  // The workers allocate and free stream-ordered from a pool of the server's
-  // own.  Freed memory stays in it (up to the budget) instead of going back to
-  // the driver at every synchronisation.  A block freed on one worker's stream
-  // is reused by another only once that free has completed: with the
-  // allocator's internal dependencies a worker's launch would wait for
-  // another worker's batch, and the workers would run one after another.
   if (!(sv->cfg.flags & MEB_SERVER_DEVICE_POOL)) {
-    cudaMemPoolProps props;
-    memset(&props, 0, sizeof(props));
-    props.allocType = cudaMemAllocationTypePinned;
-    props.location.type = cudaMemLocationTypeDevice;
-    props.location.id = device;
-    if (cudaMemPoolCreate(&sv->pool, &props) != cudaSuccess) {
+    sv->pool = server_pool(device, sv->cfg.budget_bytes);
+    if (!sv->pool) {
       delete sv;
       return MEB_ECUDA;
     }
-    uint64_t keep = (uint64_t)sv->cfg.budget_bytes;
-    int no = 0, yes = 1;
-    cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    cudaMemPoolSetAttribute(sv->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
-    cudaMemPoolSetAttribute(sv->pool, cudaMemPoolReuseAllowOpportunistic, &yes);
-    cudaMemPoolSetAttribute(sv->pool, cudaMemPoolReuseFollowEventDependencies, &yes);
   }
-  for (int k = 0; k < sv->cfg.small_workers; k++) sv->workers.emplace_back(small_worker, sv);
-  for (int k = 0; k < sv->cfg.large_workers; k++) sv->workers.emplace_back(large_worker, sv);
+  for (int k = 0; k < sv->cfg.small_workers; k++) sv->workers.emplace_back(small_worker, sv, k);
+  for (int k = 0; k < sv->cfg.large_workers; k++)
+    sv->workers.emplace_back(large_worker, sv, sv->cfg.small_workers + k);
   *out = sv;
   return MEB_OK;
 }
@@ -339,6 +381,5 @@ extern "C" void meb_server_destroy(meb_server* sv) {
   sv->cv_work.notify_all();
   for (auto& t : sv->workers) t.join();
   for (auto& kv : sv->live) delete kv.second;
-  if (sv->pool) cudaMemPoolDestroy(sv->pool);
   delete sv;
 }
