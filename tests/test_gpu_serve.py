@@ -69,6 +69,28 @@ def test_server_flags_same_results():
             assert g["rc"] == 0 and g["r"] == a["r"] and np.array_equal(g["c"], a["c"]), kw
 
 
+def test_two_servers_share_streams_and_pool():
+    """Servers of one process share their workers' streams and memory pool:
+    two alive at once, and one after another, still give every request its
+    result alone."""
+    inst = pool(10, 555)
+    ref = meb.solve_batch(inst)
+    a = meb.Server(budget_bytes=4 << 30, small_workers=3, max_group=2)
+    b = meb.Server(budget_bytes=2 << 30, small_workers=5, max_group=4)
+    ta = [a.submit(C, R) for C, R in inst]
+    tb = [b.submit(C, R) for C, R in inst]
+    ra = [a.wait(t) for t in ta]
+    rb = [b.wait(t) for t in tb]
+    a.close()
+    b.close()
+    c = meb.Server(budget_bytes=4 << 30)
+    rc = [c.wait(t) for t in [c.submit(C, R) for C, R in inst]]
+    c.close()
+    for res in (ra, rb, rc):
+        for g, r in zip(res, ref):
+            assert g["rc"] == 0 and g["r"] == r["r"] and np.array_equal(g["c"], r["c"])
+
+
 def test_budget_admission():
     inst = pool(30, 7)
     fps = [meb.footprint(C.shape[0], C.shape[1], True) + 8 * C.size + 8 * len(R) for C, R in inst]
