@@ -205,7 +205,11 @@ int meb_get_stats(meb_ctx *ctx, meb_stats *out);
  * centers m x d, radii m; tol > 0 overrides params->tol (params may be NULL).
  * Outputs: c_out[d]; active_idx[active_cap] ascending indices of
  * {i : r - r_i - ||c - c_i|| <= theta r} (truncated at active_cap, which may be
- * 0 with active_idx NULL); info (may be NULL).  m = 1 returns the ball itself. */
+ * 0 with active_idx NULL); info (may be NULL).  m = 1 returns the ball itself.
+ * Host centres of more than 128 MB are copied in chunks of about 64 MB on the
+ * context's second stream, the FP32 shadow of each chunk computed on the
+ * context's stream under the copy of the next (same results as device
+ * inputs); the call returns when both streams are done with the inputs. */
 int meb_solve(meb_ctx *ctx, const double *centers, const double *radii, int64_t m, int32_t d,
               double tol, const meb_params *params, unsigned flags, double *c_out,
               int64_t *active_idx, int64_t active_cap, meb_info *info);

@@ -58,7 +58,8 @@ struct meb_ctx {
     int d = 0, mode = -1, var = -1, prof = -1, lowp = -1, dense = -1;
     long long wait = -1;
   } tg[2];
-  cudaStream_t stream2 = nullptr;   // captures the CG loop bodies of tick graphs
+  cudaStream_t stream2 = nullptr;   // captures the CG loop bodies of tick graphs; chunked copy-in
+  cudaEvent_t stage_ev[2] = {};     // chunked copy-in: buffers free, chunk landed
   int tg_next = 0;
   cudaEvent_t gev[2 * 8] = {};
   // the reduced instance of the mixed-precision pipeline
@@ -347,6 +348,54 @@ static int stage_in(meb_ctx* ctx, int id, const void* src, size_t bytes, unsigne
   return MEB_OK;
 }
 
+// Host centres of a large instance: copied in chunks of about 64 MB on the
+// second stream; the shadow sweep of each chunk (whole 64-ball shadow blocks)
+// runs on the solve's stream as soon as that chunk has landed, under the copy
+// of the next one.  The radii and the first centre (the shadow origin) land
+// with the first chunk.  Leaves the shadow blocks done and the input flag set;
+// the mean centre is left to the caller.
+constexpr size_t kStageChunkBytes = size_t(64) << 20;
+
+static bool stage_chunked(unsigned flags, int64_t m, int d) {
+  return !(flags & MEB_PTR_DEVICE) && sizeof(double) * (size_t)m * d > 2 * kStageChunkBytes;
+}
+
+static int stage_in_shadowed(meb_ctx* ctx, Buffers& B, const double* centers, const double* radii,
+                             int64_t m, int d, const double** Cp, const double** Rp) {
+  cudaStream_t s = ctx->stream;
+  double* dC = nullptr;
+  double* dR = nullptr;
+  int rc = pool(ctx, POOL_C, sizeof(double) * (size_t)m * d, (void**)&dC);
+  if (rc) return rc;
+  if ((rc = pool(ctx, POOL_R, sizeof(double) * (size_t)m, (void**)&dR))) return rc;
+  if (!ctx->stream2) CK(cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking));
+  for (int k = 0; k < 2; k++)
+    if (!ctx->stage_ev[k]) CK(cudaEventCreateWithFlags(&ctx->stage_ev[k], cudaEventDisableTiming));
+  cudaStream_t s2 = ctx->stream2;
+  // the copies wait for earlier work of this context on the same buffers
+  CK(cudaEventRecord(ctx->stage_ev[0], s));
+  CK(cudaStreamWaitEvent(s2, ctx->stage_ev[0], 0));
+  CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
+  CK(cudaMemcpyAsync(dR, radii, sizeof(double) * (size_t)m, cudaMemcpyHostToDevice, s2));
+  const int64_t nb = (m + kShadowBallsPerBlock - 1) / kShadowBallsPerBlock;
+  const int64_t per = std::max<int64_t>(
+      1, (int64_t)(kStageChunkBytes / (sizeof(double) * (size_t)kShadowBallsPerBlock * d)));
+  for (int64_t b0 = 0; b0 < nb; b0 += per) {
+    const int64_t b1 = std::min(nb, b0 + per);
+    const int64_t i0 = b0 * kShadowBallsPerBlock;
+    const int64_t i1 = std::min(m, b1 * kShadowBallsPerBlock);
+    CK(cudaMemcpyAsync(dC + i0 * d, centers + i0 * d, sizeof(double) * (size_t)(i1 - i0) * d,
+                       cudaMemcpyHostToDevice, s2));
+    // a wait takes the event's latest record at the time of the call
+    CK(cudaEventRecord(ctx->stage_ev[1], s2));
+    CK(cudaStreamWaitEvent(s, ctx->stage_ev[1], 0));
+    CK(launch_shadow_blocks(dC, dR, m, d, B, b0, b1, ctx->d_flags, s));
+  }
+  *Cp = dC;
+  *Rp = dR;
+  return MEB_OK;
+}
+
 static int copy_out(meb_ctx* ctx, void* dst, const void* dsrc, size_t bytes, unsigned flags) {
   if (!bytes) return MEB_OK;
   CK(cudaMemcpyAsync(dst, dsrc, bytes,
@@ -456,6 +505,8 @@ void meb_destroy(meb_ctx* ctx) {
   for (int k = 0; k < 16; k++)
     if (ctx->gev[k]) cudaEventDestroy(ctx->gev[k]);
   if (ctx->sync_ev) cudaEventDestroy(ctx->sync_ev);
+  for (int k = 0; k < 2; k++)
+    if (ctx->stage_ev[k]) cudaEventDestroy(ctx->stage_ev[k]);
   delete ctx;
 }
 
@@ -694,11 +745,16 @@ static int solve_graph(meb_ctx* ctx, Buffers& B, const double* C, const double* 
 
 // The input check, the FP32 shadow (origin c_0), the mean centre c0 and
 // r0 = max_i ||c0 - c_i|| + r_i (certified feasibility pass at c0).
+// With swept = true the shadow blocks have run already (stage_in_shadowed).
 static int setup_instance(meb_ctx* ctx, Buffers& B, const double* C, const double* R, int64_t m,
-                          int d, double* r0) {
+                          int d, double* r0, bool swept = false) {
   cudaStream_t s = ctx->stream;
-  CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
-  CK(launch_shadow(C, R, m, d, B, B.vec.o, B.vec.c0, ctx->d_flags, s));
+  if (swept) {
+    CK(launch_shadow_mean(C, m, d, B, B.vec.o, B.vec.c0, s));
+  } else {
+    CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
+    CK(launch_shadow(C, R, m, d, B, B.vec.o, B.vec.c0, ctx->d_flags, s));
+  }
   CK(launch_feas_cert(C, R, m, d, B.vec.c0, 0.0, INFINITY, 2, 1, B, ctx->d_scal, ctx->d_i64,
                       ctx->d_i64 + 1, s));
   CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -935,10 +991,16 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
   Buffers& B = ctx->B;
   const double* C;
   const double* R;
-  rc = stage_in(ctx, POOL_C, centers, sizeof(double) * (size_t)m * d, flags, (const void**)&C);
-  if (rc) return rc;
-  rc = stage_in(ctx, POOL_R, radii, sizeof(double) * (size_t)m, flags, (const void**)&R);
-  if (rc) return rc;
+  const bool swept = stage_chunked(flags, m, d);
+  if (swept) {
+    rc = stage_in_shadowed(ctx, B, centers, radii, m, d, &C, &R);
+    if (rc) return rc;
+  } else {
+    rc = stage_in(ctx, POOL_C, centers, sizeof(double) * (size_t)m * d, flags, (const void**)&C);
+    if (rc) return rc;
+    rc = stage_in(ctx, POOL_R, radii, sizeof(double) * (size_t)m, flags, (const void**)&R);
+    if (rc) return rc;
+  }
   B.C_in = C;
   ctx->mult_kind = 0;
   B.use_x16 = ctx->screen_mode == MEB_SCREEN_FP16 || ctx->screen_mode == MEB_SCREEN_FP16_BULK;
@@ -950,7 +1012,7 @@ extern "C" int meb_solve(meb_ctx* ctx, const double* centers, const double* radi
 
   // the input check, the FP32 shadow and r0 at the mean centre
   double r0 = 0.0;
-  rc = setup_instance(ctx, B, C, R, m, d, &r0);
+  rc = setup_instance(ctx, B, C, R, m, d, &r0, swept);
   if (rc) return rc;
   void* dcout = nullptr;
   if (flags & MEB_PTR_DEVICE) dcout = c_out;

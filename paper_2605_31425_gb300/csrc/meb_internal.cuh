@@ -338,6 +338,14 @@ int pass_blocks(int64_t m, int d, int variant, int* tiles_per_block);
 cudaError_t prepare_pass(const Buffers& B, int d);
 cudaError_t launch_shadow(const double* C, const double* R, int64_t m, int d, Buffers& B,
                           double* o, double* c0, int* bad, cudaStream_t s);
+// The two halves of launch_shadow: the sweep over the shadow blocks
+// [b0, b1) (64 balls each; rows of those balls only are read) and the mean
+// centre once every block has run.
+constexpr int kShadowBallsPerBlock = 64;
+cudaError_t launch_shadow_blocks(const double* C, const double* R, int64_t m, int d, Buffers& B,
+                                 int64_t b0, int64_t b1, int* bad, cudaStream_t s);
+cudaError_t launch_shadow_mean(const double* C, int64_t m, int d, Buffers& B, double* o,
+                               double* c0, cudaStream_t s);
 cudaError_t launch_shadow16(Buffers& B, int64_t m, int d, double inv_s, cudaStream_t s);
 cudaError_t launch_pass(const double* C, const double* R, Buffers& B, int64_t m, int d,
                         cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,

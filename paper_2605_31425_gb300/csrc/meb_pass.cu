@@ -28,8 +28,8 @@ __global__ void __launch_bounds__(kShadowNT, 4) k_shadow(const double* __restric
                                                       float* __restrict__ R32,
                                                       float* __restrict__ E32,
                                                       double* __restrict__ colpart,
-                                                      int* __restrict__ bad) {
-  shadow_block(blockIdx.x, C, R, m, d, m_pad, X32, R32, E32, colpart, bad);
+                                                      int* __restrict__ bad, int64_t b0) {
+  shadow_block((int)(b0 + blockIdx.x), C, R, m, d, m_pad, X32, R32, E32, colpart, bad);
 }
 
 __global__ void k_shadow_mean(const double* __restrict__ C, const double* __restrict__ colpart,
@@ -38,16 +38,33 @@ __global__ void k_shadow_mean(const double* __restrict__ C, const double* __rest
   shadow_mean_block(blockIdx.x, C, colpart, nb, d, m, o, c0);
 }
 
+static_assert(kShadowBallsPerBlock == kShadowBalls, "shadow block size");
+
+cudaError_t launch_shadow_blocks(const double* C, const double* R, int64_t m, int d, Buffers& B,
+                                 int64_t b0, int64_t b1, int* bad, cudaStream_t s) {
+  const int64_t m_pad = ((m + 255) / 256) * 256;
+  const int64_t nb = (m + kShadowBalls - 1) / kShadowBalls;
+  if (b0 < 0 || b1 > nb || b0 >= b1) return cudaErrorInvalidValue;
+  k_shadow<<<(unsigned)(b1 - b0), kShadowNT, 0, s>>>(C, R, m, d, m_pad, B.X32, B.R32, B.E32,
+                                                     B.colsum_part, bad, b0);
+  B.launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shadow_mean(const double* C, int64_t m, int d, Buffers& B, double* o,
+                               double* c0, cudaStream_t s) {
+  const int nb = (int)((m + kShadowBalls - 1) / kShadowBalls);
+  k_shadow_mean<<<d, 256, 0, s>>>(C, B.colsum_part, nb, d, m, o, c0);
+  B.launches += 1;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_shadow(const double* C, const double* R, int64_t m, int d, Buffers& B,
                           double* o, double* c0, int* bad, cudaStream_t s) {
-  const int64_t m_pad = ((m + 255) / 256) * 256;
-  const int nb = (int)((m + kShadowBalls - 1) / kShadowBalls);
-  k_shadow<<<nb, kShadowNT, 0, s>>>(C, R, m, d, m_pad, B.X32, B.R32, B.E32, B.colsum_part, bad);
-  cudaError_t e = cudaGetLastError();
+  const int64_t nb = (m + kShadowBalls - 1) / kShadowBalls;
+  cudaError_t e = launch_shadow_blocks(C, R, m, d, B, 0, nb, bad, s);
   if (e != cudaSuccess) return e;
-  k_shadow_mean<<<d, 256, 0, s>>>(C, B.colsum_part, nb, d, m, o, c0);
-  B.launches += 2;
-  return cudaGetLastError();
+  return launch_shadow_mean(C, m, d, B, o, c0, s);
 }
 
 __global__ void k_shadow16(const float4* __restrict__ X32, const float* __restrict__ E32,
