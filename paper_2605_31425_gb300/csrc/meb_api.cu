@@ -380,16 +380,25 @@ static int stage_in_shadowed(meb_ctx* ctx, Buffers& B, const double* centers, co
   const int64_t nb = (m + kShadowBallsPerBlock - 1) / kShadowBallsPerBlock;
   const int64_t per = std::max<int64_t>(
       1, (int64_t)(kStageChunkBytes / (sizeof(double) * (size_t)kShadowBallsPerBlock * d)));
-  for (int64_t b0 = 0; b0 < nb; b0 += per) {
+  cudaError_t e = cudaSuccess;
+  for (int64_t b0 = 0; b0 < nb && e == cudaSuccess; b0 += per) {
     const int64_t b1 = std::min(nb, b0 + per);
     const int64_t i0 = b0 * kShadowBallsPerBlock;
     const int64_t i1 = std::min(m, b1 * kShadowBallsPerBlock);
-    CK(cudaMemcpyAsync(dC + i0 * d, centers + i0 * d, sizeof(double) * (size_t)(i1 - i0) * d,
-                       cudaMemcpyHostToDevice, s2));
+    e = cudaMemcpyAsync(dC + i0 * d, centers + i0 * d, sizeof(double) * (size_t)(i1 - i0) * d,
+                        cudaMemcpyHostToDevice, s2);
     // a wait takes the event's latest record at the time of the call
-    CK(cudaEventRecord(ctx->stage_ev[1], s2));
-    CK(cudaStreamWaitEvent(s, ctx->stage_ev[1], 0));
-    CK(launch_shadow_blocks(dC, dR, m, d, B, b0, b1, ctx->d_flags, s));
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->stage_ev[1], s2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->stage_ev[1], 0);
+    if (e == cudaSuccess) e = launch_shadow_blocks(dC, dR, m, d, B, b0, b1, ctx->d_flags, s);
+  }
+  if (e != cudaSuccess) {
+    // whatever was issued on the second stream finishes before the solve's
+    // stream goes on (and before the buffers can be freed on it)
+    const cudaError_t e2 = cudaEventRecord(ctx->stage_ev[1], s2);
+    if (e2 == cudaSuccess) cudaStreamWaitEvent(s, ctx->stage_ev[1], 0);
+    else cudaStreamSynchronize(s2);
+    return fail(ctx, MEB_ECUDA, "chunked copy-in: %s", cudaGetErrorString(e));
   }
   *Cp = dC;
   *Rp = dR;
